@@ -1,0 +1,175 @@
+/* aspot.h — C-ABI of the GB300 (sm_103a) entropic Partial Optimal Transport
+ * library: Accelerated Sinkhorn for POT (ASPOT, arXiv 2601.17196,
+ * Algorithm 2), the feasible Sinkhorn baseline it improves on (Algorithm 3
+ * with the setup of Algorithm 2, Section 4.1), the rounding of an entropic
+ * plan to a feasible plan of mass s, and the transport cost <C, X>.
+ *
+ * Problem (Section 2.1):  POT(r, c, s) = min <C, X> over
+ *   U(r, c, s) = { X >= 0 : X 1 <= r, X^T 1 <= c, 1^T X 1 = s },
+ * with r in R^n_+, c in R^m_+ of possibly different total mass and
+ * 0 < s <= min(|r|_1, |c|_1).  The entropic dual (Eq. dual) is
+ *   phi(u, v, w) = |B|_1 + sum e^{u_i} + sum e^{v_j} - <u, r> - <v, c> - w s,
+ *   B_ij = exp(-C_ij / gamma + u_i + v_j + w).
+ *
+ * Conventions (every entry point):
+ *  - All array pointers are DEVICE pointers unless the comment says "host".
+ *    The caller owns every buffer; the library keeps no pointer after the
+ *    call returns and allocates no device memory: scratch comes from the
+ *    caller's workspace (size from pot_workspace_size).
+ *  - Row-major layouts: cost C[i*ldc + j] (FP32, ldc >= m); points
+ *    X[i*ldx + k], Y[j*ldy + k] (BF16, FP16 or FP32 by pot_cost_kind,
+ *    ldx, ldy >= d).
+ *  - Work is enqueued on `stream` (cudaStream_t passed as void*, NULL =
+ *    legacy default stream).  The solvers synchronise the stream before they
+ *    return (they poll a device stop flag); pot_marginals and
+ *    pot_plan_dense do not.
+ *  - Every call returns a pot_status; on failure pot_last_error() returns a
+ *    thread-local message.  Invalid arguments are rejected with POT_EINVAL
+ *    before anything is launched.
+ */
+#ifndef ASPOT_H
+#define ASPOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define POT_API __attribute__((visibility("default")))
+#else
+#define POT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  POT_OK = 0,
+  POT_EINVAL = 1,      /* bad argument (sizes, pointers, s, eps, workspace) */
+  POT_ENOMEM = 2,      /* workspace too small */
+  POT_ECUDA = 3,       /* a CUDA call failed (message in pot_last_error) */
+  POT_ENOCONV = 4,     /* max_iter reached before the stop test; the plan is still rounded and feasible */
+  POT_ENONFINITE = 5,  /* NaN/Inf in a potential or a sum */
+  POT_ETIMEOUT = 6
+} pot_status;
+
+typedef enum {
+  POT_COST_DENSE_F32 = 0,      /* C given as an n x m FP32 matrix */
+  POT_COST_SQEUCLID_BF16 = 1,  /* C_ij = cost_scale * |x_i - y_j|^2, BF16 points (tcgen05 path when d % 64 == 0) */
+  POT_COST_SQEUCLID_F16 = 2,   /* same with FP16 points */
+  POT_COST_SQEUCLID_F32 = 3    /* same with FP32 points (CUDA cores; meant for small d such as 2 or 3) */
+} pot_cost_kind;
+
+/* flags of pot_params.flags */
+#define POT_FLAG_STOP_RAW_EPS 1   /* stop at E_t <= eps instead of eps/(8 max C) */
+#define POT_FLAG_NO_SMOOTH 2      /* skip the marginal smoothing of Algorithm 2's setup */
+#define POT_FLAG_TRACE 4          /* record E_t, phi(z^t), phi(z_check^{t+1}), argmin per iteration */
+#define POT_FLAG_NO_STOP 8        /* run exactly max_iter iterations (fixed-iteration mode) */
+#define POT_FLAG_FORCE_SIMT 16    /* use the CUDA-core pass even where the tcgen05 pass applies */
+
+typedef struct {
+  int64_t n, m;
+  int32_t kind;                 /* pot_cost_kind */
+  const float* C; int64_t ldc;  /* dense cost (kind 0) */
+  const void* X; const void* Y; /* point clouds (kinds 1-3) */
+  int32_t d; int64_t ldx, ldy;
+  double cost_scale;            /* effective cost = cost_scale * C (or * |x-y|^2); 0 => 1 / max entry, computed */
+  const double* r;              /* FP64 [n], finite, >= 0 */
+  const double* c;              /* FP64 [m], finite, >= 0 */
+  double s;                     /* 0 < s <= min(|r|_1, |c|_1) */
+} pot_problem;
+
+typedef struct {
+  double gamma;        /* entropic parameter; <= 0 => eps / (4 log max(n, m)) (Algorithm 2 setup) */
+  double eps;          /* accuracy; stop threshold eps~ = eps / (8 max C) (Algorithm 2 setup) */
+  double p_tune;       /* feasible Sinkhorn only: >= 1 => gamma = (2 eps/(49 H_min))^(1/p), eps' = H_min gamma^p (Theorem 2) */
+  int32_t max_iter;    /* iteration cap (> 0) */
+  int32_t block_rule;  /* ASPOT Greenkhorn block choice: 0 = cyclic t mod 3 (Algorithm 1) */
+  int32_t flags;       /* POT_FLAG_* */
+  int32_t check_every; /* iterations per captured CUDA graph between host polls of the stop flag (0 => 24) */
+  const double* u0;    /* optional warm start of ASPOT (device FP64 [n]) or NULL */
+  const double* v0;    /* optional warm start (device FP64 [m]) or NULL */
+  double w0;
+} pot_params;
+
+/* Rounded plan, kept implicit (O(n + m) storage):
+ *   X_ij = exp(f_i + g_j - cost_scale * C_ij / gamma) + kappa * p_i * q_j
+ * which lies in U(r, c, s).  All pointers device FP64, caller-allocated. */
+typedef struct {
+  double* u; double* v; double* w;     /* final duals z^t (n, m, 1); for Sinkhorn the first n / m extended potentials and w = 0 */
+  double* f; double* g;                /* plan potentials (n, m) */
+  double* p; double* q;                /* rank-one factors (n, m) */
+  double* kappa;                       /* scalar */
+} pot_plan;
+
+typedef struct {            /* host struct filled by the solvers */
+  int32_t status;
+  int32_t iters;            /* iterations run */
+  double objective;         /* <C_eff, X> of the rounded plan (FP64 accumulation) */
+  double err_final;         /* E_t (ASPOT) or the l1 marginal residual (Sinkhorn) at the returned duals */
+  double eps_stop;          /* threshold the stop test used */
+  double gamma;             /* gamma used */
+  double cost_scale;        /* effective cost scale (1 / max C when computed) */
+  double mass;              /* total mass of the rounded plan (= s) */
+  double ms;                /* device time of the whole call (CUDA events) */
+  int32_t rounding_branch;  /* 3: uniform scale to s, 4: rank-one fill */
+  int32_t nonfinite;
+} pot_result;
+
+/* Bytes of device workspace the solvers / pot_round / pot_objective /
+ * pot_marginals need for this problem.  Returns POT_EINVAL for bad sizes. */
+POT_API pot_status pot_workspace_size(const pot_problem* prob, const pot_params* params, size_t* bytes /* host */);
+
+/* ASPOT (Algorithm 2): setup, accelerated loop with Greenkhorn couplings
+ * (Algorithm 1), primal B(z^t), rounding (pot_round) and the objective.
+ * `plan` receives the duals and the rounded plan; `res` (host) the summary. */
+POT_API pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* workspace, size_t ws_bytes,
+                       pot_plan* plan, pot_result* res, void* stream);
+
+/* Feasible Sinkhorn baseline: alternating exact row / column scalings of the
+ * (n+1) x (m+1) dummy-extended kernel (appendix, Algorithm 3), gamma and the
+ * stop threshold from Algorithm 2's setup (or the tuned rule when
+ * params->p_tune >= 1), then the same rounding of the top-left block. */
+POT_API pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params, void* workspace,
+                              size_t ws_bytes, pot_plan* plan, pot_result* res, void* stream);
+
+/* ROUND-POT (cited by Algorithm 2; reading R1-R4): rounds B(u, v, w) to
+ * U(r, c, s) with the ORIGINAL r, c, s of `prob`:
+ *   a = min(1, r / B1), b = min(1, c / (diag(a)B)^T 1), X'' = diag(a) B diag(b);
+ *   mass m'' >= s: X = (s/m'') X'';  else X = X'' + (s - m'') p q^T / (|p| |q|),
+ *   p = r - X'' 1, q = c - X''^T 1.
+ * u, v device FP64; w host.  Fills plan->f, g, p, q, kappa; writes the
+ * branch taken (3 or 4) to *branch (host, may be NULL). */
+POT_API pot_status pot_round(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
+                     void* workspace, size_t ws_bytes, pot_plan* plan, int32_t* branch, void* stream);
+
+/* <C_eff, X> of an implicit plan (Definition 1), FP64 accumulation. */
+POT_API pot_status pot_objective(const pot_problem* prob, const pot_plan* plan, double gamma, void* workspace,
+                         size_t ws_bytes, double* out /* host */, void* stream);
+
+/* Log row and column sums of B(u, v, w): lrow[i] = log sum_j B_ij,
+ * lcol[j] = log sum_i B_ij (device FP64, either may be NULL), and
+ * *tot = |B|_1 (device FP64 scalar, may be NULL).  Enqueued only. */
+POT_API pot_status pot_marginals(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
+                         void* workspace, size_t ws_bytes, double* lrow, double* lcol, double* tot,
+                         void* stream);
+
+/* Largest entry of the raw cost (max C_ij or max |x_i - y_j|^2), host out. */
+POT_API pot_status pot_cost_max(const pot_problem* prob, void* workspace, size_t ws_bytes, double* out, void* stream);
+
+/* Materialise an implicit plan into X (device FP32, row-major, ldx >= m). */
+POT_API pot_status pot_plan_dense(const pot_problem* prob, const pot_plan* plan, double gamma, float* X, int64_t ldx,
+                          void* stream);
+
+/* Per-iteration record of the last solve that set POT_FLAG_TRACE, copied
+ * into host `out` as [iters][4] doubles (E_t, phi(z^t), phi(z_check^{t+1}),
+ * argmin took z^).  Keeps the last 4096 iterations. */
+POT_API pot_status pot_trace(void* workspace, int32_t iters, double* out /* host */, void* stream);
+
+/* Thread-local message of the last failure ("" if none). */
+POT_API const char* pot_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASPOT_H */

@@ -1,0 +1,369 @@
+"""ctypes binding of ``include/aspot.h``: argument marshalling only.
+
+Every step of the solvers runs inside ``lib/libaspot.so``.  torch provides the
+device buffers (workspace, plan vectors) and the stream.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libaspot.so")
+
+FLAG_STOP_RAW_EPS = 1
+FLAG_NO_SMOOTH = 2
+FLAG_TRACE = 4
+FLAG_NO_STOP = 8
+FLAG_FORCE_SIMT = 16
+
+COST_DENSE_F32 = 0
+COST_SQEUCLID_BF16 = 1
+COST_SQEUCLID_F16 = 2
+COST_SQEUCLID_F32 = 3
+
+STATUS = {0: "POT_OK", 1: "POT_EINVAL", 2: "POT_ENOMEM", 3: "POT_ECUDA", 4: "POT_ENOCONV",
+          5: "POT_ENONFINITE", 6: "POT_ETIMEOUT"}
+
+EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_round", "pot_objective",
+            "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "pot_last_error"]
+
+
+class PotError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Problem(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("m", ct.c_int64), ("kind", ct.c_int32),
+                ("C", ct.c_void_p), ("ldc", ct.c_int64),
+                ("X", ct.c_void_p), ("Y", ct.c_void_p), ("d", ct.c_int32), ("ldx", ct.c_int64), ("ldy", ct.c_int64),
+                ("cost_scale", ct.c_double), ("r", ct.c_void_p), ("c", ct.c_void_p), ("s", ct.c_double)]
+
+
+class _Params(ct.Structure):
+    _fields_ = [("gamma", ct.c_double), ("eps", ct.c_double), ("p_tune", ct.c_double),
+                ("max_iter", ct.c_int32), ("block_rule", ct.c_int32), ("flags", ct.c_int32),
+                ("check_every", ct.c_int32), ("u0", ct.c_void_p), ("v0", ct.c_void_p), ("w0", ct.c_double)]
+
+
+class _Plan(ct.Structure):
+    _fields_ = [(k, ct.c_void_p) for k in ("u", "v", "w", "f", "g", "p", "q", "kappa")]
+
+
+class _Result(ct.Structure):
+    _fields_ = [("status", ct.c_int32), ("iters", ct.c_int32), ("objective", ct.c_double),
+                ("err_final", ct.c_double), ("eps_stop", ct.c_double), ("gamma", ct.c_double),
+                ("cost_scale", ct.c_double), ("mass", ct.c_double), ("ms", ct.c_double),
+                ("rounding_branch", ct.c_int32), ("nonfinite", ct.c_int32)]
+
+
+_lib_handle = None
+
+
+def lib() -> ct.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = ct.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double
+        P, Q, PL, R = ct.POINTER(_Problem), ct.POINTER(_Params), ct.POINTER(_Plan), ct.POINTER(_Result)
+        L.pot_workspace_size.argtypes = [P, Q, ct.POINTER(ct.c_size_t)]
+        L.aspot_solve.argtypes = [P, Q, vp, ct.c_size_t, PL, R, vp]
+        L.sinkhorn_pot_solve.argtypes = [P, Q, vp, ct.c_size_t, PL, R, vp]
+        L.pot_round.argtypes = [P, dbl, vp, vp, dbl, vp, ct.c_size_t, PL, ct.POINTER(i32), vp]
+        L.pot_objective.argtypes = [P, PL, dbl, vp, ct.c_size_t, ct.POINTER(dbl), vp]
+        L.pot_marginals.argtypes = [P, dbl, vp, vp, dbl, vp, ct.c_size_t, vp, vp, vp, vp]
+        L.pot_cost_max.argtypes = [P, vp, ct.c_size_t, ct.POINTER(dbl), vp]
+        L.pot_plan_dense.argtypes = [P, PL, dbl, vp, i64, vp]
+        L.pot_trace.argtypes = [vp, i32, vp, vp]
+        L.pot_last_error.restype = ct.c_char_p
+        for name in EXPORTED[:-1]:
+            getattr(L, name).restype = ct.c_int
+        _lib_handle = L
+    return _lib_handle
+
+
+def exported_symbols() -> list:
+    return list(EXPORTED)
+
+
+def _check(status: int, allow=(0,)):
+    if status not in allow:
+        raise PotError(status, lib().pot_last_error().decode())
+    return status
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+@dataclasses.dataclass
+class DeviceProblem:
+    """Device copies of one POT instance (see include/aspot.h)."""
+    kind: int
+    r: torch.Tensor
+    c: torch.Tensor
+    s: float
+    C: Optional[torch.Tensor] = None
+    X: Optional[torch.Tensor] = None
+    Y: Optional[torch.Tensor] = None
+    cost_scale: float = 0.0
+
+    @property
+    def n(self) -> int:
+        return int(self.r.shape[0])
+
+    @property
+    def m(self) -> int:
+        return int(self.c.shape[0])
+
+    @property
+    def d(self) -> int:
+        return 0 if self.X is None else int(self.X.shape[1])
+
+    def struct(self) -> _Problem:
+        p = _Problem()
+        p.n, p.m, p.kind = self.n, self.m, self.kind
+        if self.C is not None:
+            p.C, p.ldc = self.C.data_ptr(), self.C.stride(0)
+        if self.X is not None:
+            p.X, p.Y, p.d = self.X.data_ptr(), self.Y.data_ptr(), self.d
+            p.ldx, p.ldy = self.X.stride(0), self.Y.stride(0)
+        p.cost_scale = self.cost_scale
+        p.r, p.c, p.s = self.r.data_ptr(), self.c.data_ptr(), float(self.s)
+        return p
+
+    @staticmethod
+    def from_workload(pb, device="cuda", kind: Optional[int] = None) -> "DeviceProblem":
+        """From a ``pot_workloads.Problem``: dense FP32 cost when it has one,
+        else BF16 points when it carries BF16 bit patterns, else FP32 points."""
+        r = torch.tensor(pb.r, dtype=torch.float64, device=device)
+        c = torch.tensor(pb.c, dtype=torch.float64, device=device)
+        if kind is None:
+            kind = COST_DENSE_F32 if pb.C is not None else (COST_SQEUCLID_BF16 if pb.X_bf16 is not None else COST_SQEUCLID_F32)
+        if kind == COST_DENSE_F32:
+            C = torch.from_numpy(np.ascontiguousarray(pb.C, dtype=np.float32)).to(device)
+            return DeviceProblem(kind, r, c, pb.s, C=C, cost_scale=pb.cost_scale)
+        if kind == COST_SQEUCLID_BF16:
+            X = torch.from_numpy(pb.X_bf16.view(np.int16)).to(device).view(torch.bfloat16)
+            Y = torch.from_numpy(pb.Y_bf16.view(np.int16)).to(device).view(torch.bfloat16)
+        elif kind == COST_SQEUCLID_F16:
+            X = torch.tensor(pb.X, dtype=torch.float16, device=device)
+            Y = torch.tensor(pb.Y, dtype=torch.float16, device=device)
+        else:
+            X = torch.tensor(pb.X, dtype=torch.float32, device=device)
+            Y = torch.tensor(pb.Y, dtype=torch.float32, device=device)
+        return DeviceProblem(kind, r, c, pb.s, X=X.contiguous(), Y=Y.contiguous(), cost_scale=pb.cost_scale)
+
+
+@dataclasses.dataclass
+class Plan:
+    """Implicit rounded plan X_ij = exp(f_i + g_j - cost_scale C_ij / gamma) + kappa p_i q_j."""
+    u: torch.Tensor
+    v: torch.Tensor
+    w: torch.Tensor
+    f: torch.Tensor
+    g: torch.Tensor
+    p: torch.Tensor
+    q: torch.Tensor
+    kappa: torch.Tensor
+
+    @staticmethod
+    def empty(n: int, m: int, device="cuda") -> "Plan":
+        z = lambda k: torch.zeros(k, dtype=torch.float64, device=device)
+        return Plan(z(n), z(m), z(1), z(n), z(m), z(n), z(m), z(1))
+
+    def struct(self) -> _Plan:
+        s = _Plan()
+        for k in ("u", "v", "w", "f", "g", "p", "q", "kappa"):
+            setattr(s, k, getattr(self, k).data_ptr())
+        return s
+
+
+@dataclasses.dataclass
+class SolveResult:
+    status: int
+    iters: int
+    objective: float
+    err_final: float
+    eps_stop: float
+    gamma: float
+    cost_scale: float
+    mass: float
+    ms: float
+    rounding_branch: int
+    nonfinite: int
+    plan: Plan
+    trace: Optional[np.ndarray] = None
+
+
+_side_streams = {}
+
+
+def _stream():
+    """Stream for library calls: the current torch stream, or a dedicated
+    side stream when the current one is the legacy default stream (CUDA
+    graphs cannot be captured on it)."""
+    cur = torch.cuda.current_stream()
+    if cur.cuda_stream != 0:
+        return cur, None
+    dev = torch.cuda.current_device()
+    if dev not in _side_streams:
+        _side_streams[dev] = torch.cuda.Stream()
+    side = _side_streams[dev]
+    side.wait_stream(cur)
+    return side, cur
+
+
+def _finish(side, cur):
+    if cur is not None:
+        cur.wait_stream(side)
+
+
+def workspace_bytes(prob: DeviceProblem, flags: int = 0) -> int:
+    b = ct.c_size_t(0)
+    pa = _Params()
+    pa.flags = flags
+    _check(lib().pot_workspace_size(ct.byref(prob.struct()), ct.byref(pa), ct.byref(b)))
+    return int(b.value)
+
+
+_ws_cache = {}
+
+
+def _workspace(prob: DeviceProblem, flags: int, ws: Optional[torch.Tensor]):
+    """(buffer, usable bytes).  A caller buffer is passed with its real size
+    (from its 256-byte aligned start), so the library rejects one that is
+    too small instead of writing past it."""
+    need = workspace_bytes(prob, flags)
+    if ws is not None:
+        if ws.device.type != "cuda" or not ws.is_contiguous():
+            raise ValueError("workspace must be a contiguous CUDA tensor")
+        nbytes = ws.numel() * ws.element_size()
+        off = (-ws.data_ptr()) % 256
+        if off >= nbytes:
+            raise PotError(2, f"workspace too small: {nbytes} bytes < {need}")
+        base = ws.view(torch.uint8)[off:]
+        return base, nbytes - off
+    dev = prob.r.device
+    key = (dev.index, )
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < need:
+        buf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        _ws_cache[key] = buf
+    off = (-buf.data_ptr()) % 256
+    return buf[off:], need
+
+
+def _params(gamma, eps, max_iter, flags, check_every, p_tune=0.0, u0=None, v0=None, w0=0.0) -> _Params:
+    pa = _Params()
+    pa.gamma, pa.eps, pa.p_tune = float(gamma), float(eps), float(p_tune)
+    pa.max_iter, pa.block_rule, pa.flags, pa.check_every = int(max_iter), 0, int(flags), int(check_every)
+    pa.u0, pa.v0, pa.w0 = _ptr(u0), _ptr(v0), float(w0)
+    return pa
+
+
+def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, plan, ws,
+           allow_noconv) -> SolveResult:
+    L = lib()
+    plan = plan or Plan.empty(prob.n, prob.m, prob.r.device)
+    ws, need = _workspace(prob, flags, ws)
+    pa = _params(gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0)
+    res = _Result()
+    side, cur = _stream()
+    st = _check(getattr(L, fn)(ct.byref(prob.struct()), ct.byref(pa), ct.c_void_p(ws.data_ptr()), need,
+                               ct.byref(plan.struct()), ct.byref(res), ct.c_void_p(side.cuda_stream)),
+                allow=(0, 4) if allow_noconv else (0,))
+    trace = None
+    if flags & FLAG_TRACE:
+        k = min(res.iters, 4096)
+        buf = np.zeros((max(k, 1), 4))
+        _check(L.pot_trace(ct.c_void_p(ws.data_ptr()), k, buf.ctypes.data_as(ct.c_void_p),
+                           ct.c_void_p(side.cuda_stream)))
+        trace = buf[:k]
+    _finish(side, cur)
+    return SolveResult(st, res.iters, res.objective, res.err_final, res.eps_stop, res.gamma, res.cost_scale,
+                       res.mass, res.ms, res.rounding_branch, res.nonfinite, plan, trace)
+
+
+def aspot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
+                check_every: int = 0, u0=None, v0=None, w0: float = 0.0, plan: Optional[Plan] = None,
+                ws: Optional[torch.Tensor] = None, allow_noconv: bool = True) -> SolveResult:
+    return _solve("aspot_solve", prob, gamma, eps, max_iter, flags, check_every, 0.0, u0, v0, w0, plan, ws,
+                  allow_noconv)
+
+
+def sinkhorn_pot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 100000, flags: int = 0,
+                       check_every: int = 0, p_tune: float = 0.0, plan: Optional[Plan] = None,
+                       ws: Optional[torch.Tensor] = None, allow_noconv: bool = True) -> SolveResult:
+    return _solve("sinkhorn_pot_solve", prob, gamma, eps, max_iter, flags, check_every, p_tune, None, None, 0.0,
+                  plan, ws, allow_noconv)
+
+
+def pot_round(prob: DeviceProblem, gamma: float, u: torch.Tensor, v: torch.Tensor, w: float,
+              plan: Optional[Plan] = None, ws: Optional[torch.Tensor] = None):
+    plan = plan or Plan.empty(prob.n, prob.m, prob.r.device)
+    ws, need = _workspace(prob, 0, ws)
+    br = ct.c_int32(0)
+    side, cur = _stream()
+    _check(lib().pot_round(ct.byref(prob.struct()), gamma, u.data_ptr(), v.data_ptr(), float(w),
+                           ct.c_void_p(ws.data_ptr()), need, ct.byref(plan.struct()), ct.byref(br),
+                           ct.c_void_p(side.cuda_stream)))
+    _finish(side, cur)
+    return plan, int(br.value)
+
+
+def pot_objective(prob: DeviceProblem, plan: Plan, gamma: float, ws: Optional[torch.Tensor] = None) -> float:
+    ws, need = _workspace(prob, 0, ws)
+    out = ct.c_double(0)
+    side, cur = _stream()
+    _check(lib().pot_objective(ct.byref(prob.struct()), ct.byref(plan.struct()), gamma, ct.c_void_p(ws.data_ptr()),
+                               need, ct.byref(out), ct.c_void_p(side.cuda_stream)))
+    _finish(side, cur)
+    return float(out.value)
+
+
+def pot_marginals(prob: DeviceProblem, gamma: float, u: torch.Tensor, v: torch.Tensor, w: float,
+                  ws: Optional[torch.Tensor] = None):
+    """Returns (log row sums, log column sums, total mass) of B(u, v, w)."""
+    ws, need = _workspace(prob, 0, ws)
+    lrow = torch.empty(prob.n, dtype=torch.float64, device=prob.r.device)
+    lcol = torch.empty(prob.m, dtype=torch.float64, device=prob.r.device)
+    tot = torch.empty(1, dtype=torch.float64, device=prob.r.device)
+    side, cur = _stream()
+    _check(lib().pot_marginals(ct.byref(prob.struct()), gamma, u.data_ptr(), v.data_ptr(), float(w),
+                               ct.c_void_p(ws.data_ptr()), need, lrow.data_ptr(), lcol.data_ptr(), tot.data_ptr(),
+                               ct.c_void_p(side.cuda_stream)))
+    side.synchronize()
+    _finish(side, cur)
+    return lrow, lcol, float(tot.item())
+
+
+def pot_cost_max(prob: DeviceProblem, ws: Optional[torch.Tensor] = None) -> float:
+    ws, need = _workspace(prob, 0, ws)
+    out = ct.c_double(0)
+    side, cur = _stream()
+    _check(lib().pot_cost_max(ct.byref(prob.struct()), ct.c_void_p(ws.data_ptr()), need, ct.byref(out),
+                              ct.c_void_p(side.cuda_stream)))
+    _finish(side, cur)
+    return float(out.value)
+
+
+def pot_plan_dense(prob: DeviceProblem, plan: Plan, gamma: float) -> torch.Tensor:
+    X = torch.empty(prob.n, prob.m, dtype=torch.float32, device=prob.r.device)
+    side, cur = _stream()
+    _check(lib().pot_plan_dense(ct.byref(prob.struct()), ct.byref(plan.struct()), gamma, X.data_ptr(), X.stride(0),
+                                ct.c_void_p(side.cuda_stream)))
+    side.synchronize()
+    _finish(side, cur)
+    return X

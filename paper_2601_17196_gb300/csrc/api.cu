@@ -1,0 +1,692 @@
+// C-ABI entry points (include/aspot.h): argument checks, workspace layout,
+// the host drivers of ASPOT (Algorithm 2) and of the feasible Sinkhorn
+// baseline (Algorithm 3), rounding and objective.
+//
+// The iteration loops run as CUDA graphs of `check_every` iterations; every
+// kernel of an iteration returns at once when the device stop flag is set,
+// and the host reads the flag between graph launches.  No device memory is
+// allocated: all scratch is carved from the caller's workspace.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdarg.h>
+#include <stddef.h>
+#include <string.h>
+#include <math.h>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/aspot.h"
+#include "kernels.h"
+
+using namespace pot;
+
+namespace {
+
+thread_local std::string g_err;
+
+pot_status fail(pot_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(POT_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define CKL()                                                                             \
+  do {                                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess) return fail(POT_ECUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+constexpr int kSlots = 12;
+
+struct Layout {
+  bool use_tc = false;
+  SimtLayout sl{};
+  TcLayout tl{};
+  int64_t ncolblk = 0, nrowblk = 0;
+  int64_t red_doubles = 0;
+  size_t off_state = 0, off_red = 0, off_cnt = 0, off_stats = 0, off_xn = 0, off_yn = 0;
+  size_t off_rowp = 0, off_colp = 0, off_u[kSlots] = {}, off_v[kSlots] = {};
+  size_t off_rowA = 0, off_colA = 0, off_colB = 0;
+  size_t total = 0;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool wants_tc(const pot_problem* P, int flags) {
+  if (flags & POT_FLAG_FORCE_SIMT) return false;
+  if (P->kind != POT_COST_SQEUCLID_BF16) return false;
+  PassDesc d{};
+  d.n = P->n; d.m = P->m; d.kind = P->kind; d.X = P->X; d.Y = P->Y; d.d = P->d; d.ldx = P->ldx; d.ldy = P->ldy;
+  return tc_supported(d);
+}
+
+Layout make_layout(const pot_problem* P, int flags) {
+  Layout L;
+  const int64_t n = P->n, m = P->m;
+  L.sl = simt_layout(n, m);
+  L.use_tc = wants_tc(P, flags);
+  if (L.use_tc) {
+    L.tl = tc_layout(n, m, P->d);
+    L.ncolblk = L.tl.ncolblk;
+    L.nrowblk = L.tl.nrowblk;
+  } else {
+    L.ncolblk = L.sl.ncolblk;
+    L.nrowblk = L.sl.nrowblk;
+  }
+  const int64_t vblk = vec_blocks(n + m + 2);
+  const int64_t pass_ctas = std::max<int64_t>(L.sl.ncolblk * L.sl.nrowblk, L.use_tc ? L.tl.ncolblk * L.tl.nrowblk : 0);
+  L.red_doubles = std::max<int64_t>(vblk * 8, pass_ctas) + 64;
+  size_t o = 0;
+  L.off_state = o; o = align_up(o + sizeof(DevState));
+  L.off_red = o; o = align_up(o + sizeof(double) * L.red_doubles);
+  L.off_cnt = o; o = align_up(o + sizeof(unsigned int) * 8);
+  L.off_stats = o; o = align_up(o + sizeof(double) * 8);
+  L.off_xn = o; o = align_up(o + sizeof(float) * (n + 1));
+  L.off_yn = o; o = align_up(o + sizeof(float) * (m + 1));
+  L.off_rowp = o; o = align_up(o + sizeof(float2) * L.ncolblk * n);
+  L.off_colp = o; o = align_up(o + sizeof(float2) * L.nrowblk * m);
+  for (int k = 0; k < kSlots; ++k) { L.off_u[k] = o; o = align_up(o + sizeof(double) * (n + 2)); }
+  for (int k = 0; k < kSlots; ++k) { L.off_v[k] = o; o = align_up(o + sizeof(double) * (m + 2)); }
+  if (L.use_tc) {
+    L.off_rowA = o; o = align_up(o + sizeof(float4) * L.tl.n_pad);
+    L.off_colA = o; o = align_up(o + sizeof(float2) * L.tl.m_pad);
+    L.off_colB = o; o = align_up(o + sizeof(float2) * L.tl.m_pad);
+  }
+  L.total = o;
+  return L;
+}
+
+struct Ctx {
+  const pot_problem* P;
+  cudaStream_t st;
+  Layout L;
+  char* ws;
+  DevState* S;
+  double* red;
+  unsigned int* cnt;
+  double* stats;
+  float *xn, *yn;
+  float2 *rowp, *colp;
+  float4* rowA = nullptr;
+  float2 *colA = nullptr, *colB = nullptr;
+  double* U[kSlots];
+  double* V[kSlots];
+  double cost_scale = 1.0;
+  double max_raw = 0.0;
+  double sum_r = 0, sum_c = 0, min_r = 0, min_c = 0;
+};
+
+pot_status check_problem(const pot_problem* P) {
+  if (!P) return fail(POT_EINVAL, "problem is NULL");
+  if (P->n < 1 || P->m < 1) return fail(POT_EINVAL, "n and m must be >= 1 (got %lld, %lld)", (long long)P->n, (long long)P->m);
+  if (P->n > (int64_t(1) << 31) || P->m > (int64_t(1) << 31)) return fail(POT_EINVAL, "n, m too large");
+  if (!P->r || !P->c) return fail(POT_EINVAL, "r and c must be device pointers");
+  if (!(P->s > 0.0) || !isfinite(P->s)) return fail(POT_EINVAL, "s must be finite and > 0");
+  if (!(P->cost_scale >= 0.0) || !isfinite(P->cost_scale)) return fail(POT_EINVAL, "cost_scale must be finite and >= 0");
+  switch (P->kind) {
+    case POT_COST_DENSE_F32:
+      if (!P->C) return fail(POT_EINVAL, "dense cost pointer is NULL");
+      if (P->ldc < P->m) return fail(POT_EINVAL, "ldc < m");
+      break;
+    case POT_COST_SQEUCLID_BF16:
+    case POT_COST_SQEUCLID_F16:
+    case POT_COST_SQEUCLID_F32:
+      if (!P->X || !P->Y) return fail(POT_EINVAL, "point pointers are NULL");
+      if (P->d < 1 || P->d > 4096) return fail(POT_EINVAL, "d must be in [1, 4096]");
+      if (P->ldx < P->d || P->ldy < P->d) return fail(POT_EINVAL, "ldx, ldy must be >= d");
+      break;
+    default:
+      return fail(POT_EINVAL, "unknown cost kind %d", (int)P->kind);
+  }
+  return POT_OK;
+}
+
+pot_status check_params(const pot_params* Q) {
+  if (!Q) return fail(POT_EINVAL, "params is NULL");
+  if (!(Q->eps > 0.0) || !isfinite(Q->eps)) return fail(POT_EINVAL, "eps must be finite and > 0");
+  if (!isfinite(Q->gamma)) return fail(POT_EINVAL, "gamma must be finite");
+  if (Q->max_iter < 1) return fail(POT_EINVAL, "max_iter must be >= 1");
+  if (Q->block_rule != 0) return fail(POT_EINVAL, "only the cyclic block rule (0) is implemented on the GPU");
+  if (Q->check_every < 0) return fail(POT_EINVAL, "check_every must be >= 0");
+  if (!isfinite(Q->w0)) return fail(POT_EINVAL, "w0 must be finite");
+  return POT_OK;
+}
+
+pot_status bind(Ctx& X, const pot_problem* P, int flags, void* ws, size_t ws_bytes, void* stream) {
+  X.P = P;
+  X.st = (cudaStream_t)stream;
+  X.L = make_layout(P, flags);
+  if (!ws) return fail(POT_EINVAL, "workspace is NULL");
+  if ((uintptr_t)ws % 256 != 0) return fail(POT_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < X.L.total) return fail(POT_ENOMEM, "workspace too small: %zu < %zu bytes", ws_bytes, X.L.total);
+  X.ws = (char*)ws;
+  X.S = (DevState*)(X.ws + X.L.off_state);
+  X.red = (double*)(X.ws + X.L.off_red);
+  X.cnt = (unsigned int*)(X.ws + X.L.off_cnt);
+  X.stats = (double*)(X.ws + X.L.off_stats);
+  X.xn = (float*)(X.ws + X.L.off_xn);
+  X.yn = (float*)(X.ws + X.L.off_yn);
+  X.rowp = (float2*)(X.ws + X.L.off_rowp);
+  X.colp = (float2*)(X.ws + X.L.off_colp);
+  for (int k = 0; k < kSlots; ++k) { X.U[k] = (double*)(X.ws + X.L.off_u[k]); X.V[k] = (double*)(X.ws + X.L.off_v[k]); }
+  if (X.L.use_tc) {
+    X.rowA = (float4*)(X.ws + X.L.off_rowA);
+    X.colA = (float2*)(X.ws + X.L.off_colA);
+    X.colB = (float2*)(X.ws + X.L.off_colB);
+  }
+  return POT_OK;
+}
+
+PassDesc base_desc(const Ctx& X, double gamma) {
+  PassDesc d{};
+  const pot_problem* P = X.P;
+  d.n = P->n; d.m = P->m; d.kind = P->kind;
+  d.C = P->C; d.ldc = P->ldc;
+  d.X = P->X; d.Y = P->Y; d.d = P->d; d.ldx = P->ldx; d.ldy = P->ldy;
+  d.xn = X.xn; d.yn = X.yn;
+  d.gC = gamma > 0.0 ? X.cost_scale / gamma : 0.0;
+  d.row_part = X.rowp; d.col_part = X.colp; d.red_part = X.red;
+  d.rowA = X.rowA; d.colA = X.colA; d.colB = X.colB; d.err = &X.S->tc_err;
+  return d;
+}
+
+pot_status run_pass(const Ctx& X, const PassDesc& d) {
+  if (X.L.use_tc) {
+    CK(launch_pass_tc(d, X.L.tl, X.st));
+  } else {
+    launch_pass_simt(d, X.L.sl, X.st);
+  }
+  CKL();
+  return POT_OK;
+}
+
+int64_t pass_ctas(const Ctx& X) {
+  return X.L.use_tc ? X.L.tl.ncolblk * X.L.tl.nrowblk : X.L.sl.ncolblk * X.L.sl.nrowblk;
+}
+
+// masses, minima, finiteness of r, c; squared norms; max of the raw cost
+pot_status prologue(Ctx& X, bool need_max) {
+  const pot_problem* P = X.P;
+  CK(cudaMemsetAsync(X.cnt, 0, sizeof(unsigned int) * 8, X.st));
+  launch_marg_stats(P->r, P->c, P->n, P->m, X.red, X.cnt, X.stats, X.st);
+  CKL();
+  if (P->kind != POT_COST_DENSE_F32) {
+    launch_sqnorm(P->kind, P->X, P->n, P->d, P->ldx, X.xn, X.st);
+    launch_sqnorm(P->kind, P->Y, P->m, P->d, P->ldy, X.yn, X.st);
+    CKL();
+  }
+  if (need_max) {
+    PassDesc d = base_desc(X, 0.0);
+    d.mode = PASS_MAXCOST;
+    pot_status s = run_pass(X, d);
+    if (s != POT_OK) return s;
+    launch_reduce_parts(X.red, pass_ctas(X), 1, X.stats + 6, X.st);
+    CKL();
+  }
+  double h[8];
+  CK(cudaMemcpyAsync(h, X.stats, sizeof(h), cudaMemcpyDeviceToHost, X.st));
+  CK(cudaStreamSynchronize(X.st));
+  X.sum_r = h[0]; X.sum_c = h[1]; X.min_r = h[2]; X.min_c = h[3];
+  if (h[4] != 0.0) return fail(POT_EINVAL, "r and c must be finite and non-negative");
+  if (!(X.sum_r > 0.0) || !(X.sum_c > 0.0)) return fail(POT_EINVAL, "r and c must have positive mass");
+  const double mn = std::min(X.sum_r, X.sum_c);
+  if (P->s > mn * (1.0 + 1e-12)) return fail(POT_EINVAL, "s = %.17g exceeds min(|r|_1, |c|_1) = %.17g", P->s, mn);
+  if (need_max) {
+    X.max_raw = h[6];
+    if (!(X.max_raw >= 0.0) || !isfinite(X.max_raw)) return fail(POT_EINVAL, "cost contains NaN/Inf");
+  }
+  X.cost_scale = P->cost_scale > 0.0 ? P->cost_scale : (X.max_raw > 0.0 ? 1.0 / X.max_raw : 1.0);
+  return POT_OK;
+}
+
+struct SetupOut { double gamma, eps_stop, eps_s, sum_rt, sum_ct, T, L, cmax; };
+
+// Algorithm 2 setup: gamma = eps/(4 log n), eps~ = eps/(8 max C), mass guards,
+// smoothing coefficient (guards shrink it; the stop threshold is unguarded).
+SetupOut approx_setup(const Ctx& X, const pot_params* Q) {
+  SetupOut o;
+  const double nn = (double)std::max(X.P->n, X.P->m);
+  o.gamma = Q->gamma > 0.0 ? Q->gamma : Q->eps / (4.0 * log(std::max(nn, 2.0)));
+  o.cmax = X.cost_scale * X.max_raw;
+  o.eps_stop = Q->eps / (8.0 * (o.cmax > 0.0 ? o.cmax : 1.0));
+  double e = o.eps_stop;
+  const double s = X.P->s;
+  if (X.sum_r > 1.0) e = std::min(e, 8.0 * (X.sum_r - s) / (X.sum_r - 1.0));
+  if (X.sum_c > 1.0) e = std::min(e, 8.0 * (X.sum_c - s) / (X.sum_c - 1.0));
+  if ((Q->flags & POT_FLAG_NO_SMOOTH) || !(e > 0.0)) e = 0.0;
+  o.eps_s = e;
+  o.sum_rt = (1.0 - e / 8.0) * X.sum_r + e / 8.0;
+  o.sum_ct = (1.0 - e / 8.0) * X.sum_c + e / 8.0;
+  o.T = o.sum_rt + o.sum_ct - s;
+  o.L = 3.0 * o.T / o.gamma;
+  if (Q->flags & POT_FLAG_STOP_RAW_EPS) o.eps_stop = Q->eps;
+  return o;
+}
+
+pot_status upload_state(Ctx& X, const DevState& h) {
+  CK(cudaMemcpyAsync(X.S, &h, offsetof(DevState, trace), cudaMemcpyHostToDevice, X.st));
+  return POT_OK;
+}
+
+pot_status read_state(Ctx& X, DevState& h) {
+  CK(cudaMemcpyAsync(&h, X.S, offsetof(DevState, trace), cudaMemcpyDeviceToHost, X.st));
+  CK(cudaStreamSynchronize(X.st));
+  return POT_OK;
+}
+
+// Run `body` (one iteration per call, k = iteration index mod 3) until the
+// device stop flag is set.  With a capturable stream the iterations are
+// captured into a CUDA graph of `per` iterations.
+template <class Body>
+pot_status drive(Ctx& X, int per, int max_iter, Body body) {
+  cudaStreamCaptureStatus cs;
+  CK(cudaStreamIsCapturing(X.st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(POT_EINVAL, "the stream is being captured");
+  const bool graphs = X.st != nullptr && X.st != cudaStreamLegacy && X.st != cudaStreamPerThread;
+  per = std::max(3, (per + 2) / 3 * 3);
+  int done = 0, launched = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  if (graphs) {
+    CK(cudaStreamBeginCapture(X.st, cudaStreamCaptureModeThreadLocal));
+    pot_status s = POT_OK;
+    for (int it = 0; it < per && s == POT_OK; ++it) s = body(it % 3);
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e = cudaStreamEndCapture(X.st, &g2);
+    if (s != POT_OK) { if (g2) cudaGraphDestroy(g2); return s; }
+    if (e != cudaSuccess) return fail(POT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    graph = g2;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return fail(POT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+  }
+  pot_status st = POT_OK;
+  int* hflag = &done;
+  while (launched < max_iter + per) {
+    if (graphs) {
+      cudaError_t e = cudaGraphLaunch(exec, X.st);
+      if (e != cudaSuccess) { st = fail(POT_ECUDA, "graph launch: %s", cudaGetErrorString(e)); break; }
+    } else {
+      for (int it = 0; it < per && st == POT_OK; ++it) st = body(it % 3);
+      if (st != POT_OK) break;
+    }
+    launched += per;
+    cudaError_t e = cudaMemcpyAsync(hflag, &X.S->done, sizeof(int), cudaMemcpyDeviceToHost, X.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(X.st);
+    if (e != cudaSuccess) { st = fail(POT_ECUDA, "stop flag: %s", cudaGetErrorString(e)); break; }
+    if (done) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (st == POT_OK && !done) st = fail(POT_ETIMEOUT, "device stop flag never set");
+  return st;
+}
+
+pot_status do_round(Ctx& X, double gamma, const double* u, const double* v, pot_plan* plan, int* branch) {
+  // w is expected in S->w_out
+  const pot_problem* P = X.P;
+  RoundVecs R{};
+  R.n = P->n; R.m = P->m; R.r = P->r; R.c = P->c; R.u = u; R.v = v;
+  R.f = plan->f; R.g = plan->g; R.p = plan->p; R.q = plan->q; R.kappa = plan->kappa;
+  R.row_part = X.rowp; R.col_part = X.colp; R.ncolblk = X.L.ncolblk; R.nrowblk = X.L.nrowblk;
+  R.red = X.red; R.counter = X.cnt; R.S = X.S;
+  PassDesc d = base_desc(X, gamma);
+  // R1: rows of B(u, v, w)
+  d.mode = PASS_ROWS; d.arow0 = u; d.bcol0 = v; d.aoff0 = &X.S->w_out;
+  pot_status s = run_pass(X, d);
+  if (s != POT_OK) return s;
+  launch_round_r1(R, X.st);
+  CKL();
+  // R2: columns of diag(a) B
+  d.mode = PASS_COLS; d.arow0 = plan->f; d.bcol0 = v; d.aoff0 = nullptr;
+  if ((s = run_pass(X, d)) != POT_OK) return s;
+  launch_round_r2(R, X.st);
+  CKL();
+  DevState h;
+  if ((s = read_state(X, h)) != POT_OK) return s;
+  if (h.m2 >= P->s) {
+    launch_round_r3(R, X.st);
+    CKL();
+    if (branch) *branch = 3;
+  } else {
+    d.mode = PASS_ROWS; d.arow0 = plan->f; d.bcol0 = plan->g; d.aoff0 = nullptr;
+    if ((s = run_pass(X, d)) != POT_OK) return s;
+    launch_round_r4(R, X.st);
+    CKL();
+    if (branch) *branch = 4;
+  }
+  return POT_OK;
+}
+
+pot_status do_objective(Ctx& X, double gamma, const pot_plan* plan, double* out) {
+  PassDesc d = base_desc(X, gamma);
+  d.mode = PASS_OBJ; d.arow0 = plan->f; d.bcol0 = plan->g; d.aoff0 = nullptr;
+  d.p = plan->p; d.q = plan->q; d.kappa = plan->kappa;
+  pot_status s = run_pass(X, d);
+  if (s != POT_OK) return s;
+  launch_reduce_parts(X.red, pass_ctas(X), 0, X.stats + 7, X.st);
+  CKL();
+  double h;
+  CK(cudaMemcpyAsync(&h, X.stats + 7, sizeof(double), cudaMemcpyDeviceToHost, X.st));
+  CK(cudaStreamSynchronize(X.st));
+  *out = h * X.cost_scale;
+  return POT_OK;
+}
+
+pot_status check_plan(const pot_plan* plan) {
+  if (!plan) return fail(POT_EINVAL, "plan is NULL");
+  if (!plan->u || !plan->v || !plan->w || !plan->f || !plan->g || !plan->p || !plan->q || !plan->kappa)
+    return fail(POT_EINVAL, "every pot_plan pointer must be a device buffer");
+  return POT_OK;
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a); cudaEventCreate(&b); cudaEventRecord(a, st);
+  }
+  double stop() {
+    float ms = 0.f;
+    cudaEventRecord(b, st); cudaEventSynchronize(b); cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* pot_last_error(void) { return g_err.c_str(); }
+
+pot_status pot_workspace_size(const pot_problem* prob, const pot_params* params, size_t* bytes) {
+  g_err.clear();
+  pot_status s = check_problem(prob);
+  if (s != POT_OK) return s;
+  if (!bytes) return fail(POT_EINVAL, "bytes is NULL");
+  *bytes = make_layout(prob, params ? params->flags : 0).total;
+  return POT_OK;
+}
+
+pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* workspace, size_t ws_bytes,
+                       pot_plan* plan, pot_result* res, void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if ((s = check_params(params)) != POT_OK) return s;
+  if ((s = check_plan(plan)) != POT_OK) return s;
+  if (!res) return fail(POT_EINVAL, "result is NULL");
+  memset(res, 0, sizeof(*res));
+  Ctx X;
+  if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
+  Timer tm(X.st);
+  if ((s = prologue(X, true)) != POT_OK) return s;
+  const SetupOut so = approx_setup(X, params);
+  const int64_t n = prob->n, m = prob->m;
+  DevState h{};
+  h.L = so.L; h.s = prob->s; h.thr = (params->flags & POT_FLAG_NO_STOP) ? -1.0 : so.eps_stop;
+  h.log_s = log(prob->s); h.sum_rt = so.sum_rt; h.sum_ct = so.sum_ct; h.max_iter = params->max_iter;
+  h.theta = 1.0;
+  if ((s = upload_state(X, h)) != POT_OK) return s;
+
+  AspotVecs V{};
+  V.n = n; V.m = m;
+  V.rt = X.U[0]; V.lrt = X.U[1]; V.ct = X.V[0]; V.lct = X.V[1];
+  V.ut = X.U[2]; V.vt = X.V[2]; V.uc = X.U[3]; V.vc = X.V[3]; V.ub = X.U[4]; V.vb = X.V[4];
+  V.ug = X.U[5]; V.vg = X.V[5]; V.uh = X.U[6]; V.vh = X.V[6]; V.uo = plan->u; V.vo = plan->v;
+  V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
+  V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
+  launch_aspot_init(V, prob->r, prob->c, so.eps_s, params->u0, params->v0, params->w0, X.st);
+  CKL();
+
+  const double gamma = so.gamma;
+  PassDesc d = base_desc(X, gamma);
+  auto body = [&](int k) -> pot_status {
+    pot_status q;
+    launch_aspot_extrap(V, X.st);
+    PassDesc p1 = d;                       // gradient pass at z_bar (both sides)
+    p1.mode = PASS_ROWS | PASS_COLS; p1.arow0 = V.ub; p1.bcol0 = V.vb; p1.aoff0 = &X.S->w_bar; p1.done = &X.S->done;
+    if ((q = run_pass(X, p1)) != POT_OK) return q;
+    launch_aspot_after_grad(V, X.st);
+    PassDesc p2 = d;                       // Greenkhorn pass at z_grave (one side)
+    p2.mode = (k == 1) ? PASS_COLS : PASS_ROWS; p2.arow0 = V.ug; p2.bcol0 = V.vg; p2.aoff0 = &X.S->w_grave;
+    p2.done = &X.S->done;
+    if ((q = run_pass(X, p2)) != POT_OK) return q;
+    launch_aspot_after_greenkhorn(V, k, X.st);
+    PassDesc p3 = d;                       // pass at z^t = argmin (both sides)
+    p3.mode = PASS_ROWS | PASS_COLS;
+    p3.arow0 = V.uc; p3.bcol0 = V.vc; p3.aoff0 = &X.S->w_check;
+    p3.arow1 = (k == 0) ? V.uh : V.ug; p3.bcol1 = (k == 1) ? V.vh : V.vg; p3.aoff1 = &X.S->w_hat;
+    p3.sel = &X.S->take_hat; p3.done = &X.S->done;
+    if ((q = run_pass(X, p3)) != POT_OK) return q;
+    launch_aspot_after_final(V, k, X.st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
+    return POT_OK;
+  };
+  const int per = params->check_every > 0 ? params->check_every : 24;
+  if ((s = drive(X, per, params->max_iter, body)) != POT_OK) return s;
+  if ((s = read_state(X, h)) != POT_OK) return s;
+  CK(cudaMemcpyAsync(plan->w, &X.S->w_out, sizeof(double), cudaMemcpyDeviceToDevice, X.st));
+  res->iters = h.t;
+  res->err_final = h.E;
+  res->eps_stop = h.thr;
+  res->gamma = gamma;
+  res->cost_scale = X.cost_scale;
+  res->nonfinite = h.nonfinite;
+  int branch = 0;
+  if ((s = do_round(X, gamma, plan->u, plan->v, plan, &branch)) != POT_OK) return s;
+  res->rounding_branch = branch;
+  if ((s = do_objective(X, gamma, plan, &res->objective)) != POT_OK) return s;
+  res->mass = prob->s;
+  res->ms = tm.stop();
+  if (h.nonfinite) { res->status = POT_ENONFINITE; return fail(POT_ENONFINITE, "non-finite potentials or sums"); }
+  const bool conv = h.E <= h.thr;
+  res->status = (conv || (params->flags & POT_FLAG_NO_STOP)) ? POT_OK : POT_ENOCONV;
+  if (res->status == POT_ENOCONV) fail(POT_ENOCONV, "max_iter reached with E = %.3e > %.3e", h.E, h.thr);
+  return (pot_status)res->status;
+}
+
+pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params, void* workspace,
+                              size_t ws_bytes, pot_plan* plan, pot_result* res, void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if ((s = check_params(params)) != POT_OK) return s;
+  if ((s = check_plan(plan)) != POT_OK) return s;
+  if (!res) return fail(POT_EINVAL, "result is NULL");
+  memset(res, 0, sizeof(*res));
+  Ctx X;
+  if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
+  Timer tm(X.st);
+  if ((s = prologue(X, true)) != POT_OK) return s;
+  SetupOut so = approx_setup(X, params);
+  double gamma = so.gamma, thr = so.eps_stop;
+  if (params->p_tune >= 1.0) {
+    // Theorem 2: H_min from the original marginals (host copy, O(n + m))
+    std::vector<double> hr(prob->n), hc(prob->m);
+    CK(cudaMemcpyAsync(hr.data(), prob->r, sizeof(double) * prob->n, cudaMemcpyDeviceToHost, X.st));
+    CK(cudaMemcpyAsync(hc.data(), prob->c, sizeof(double) * prob->m, cudaMemcpyDeviceToHost, X.st));
+    CK(cudaStreamSynchronize(X.st));
+    double Hr = 0, Hc = 0;
+    for (double x : hr) if (x > 0) Hr -= x * log(x);
+    for (double x : hc) if (x > 0) Hc -= x * log(x);
+    const double hmin = std::min(Hr, Hc);
+    if (!(hmin > 0.0)) return fail(POT_EINVAL, "tuned gamma needs H_min > 0");
+    gamma = pow(2.0 * params->eps / (49.0 * hmin), 1.0 / params->p_tune);
+    thr = hmin * pow(gamma, params->p_tune);
+  }
+  if (params->flags & POT_FLAG_NO_STOP) thr = -1.0;
+  const double A = 8.0 * so.cmax / params->eps;
+  const int64_t n = prob->n, m = prob->m;
+  DevState h{};
+  h.s = prob->s; h.thr = thr; h.sum_rt = so.sum_rt; h.sum_ct = so.sum_ct; h.max_iter = params->max_iter;
+  h.A_over_g = A / gamma;
+  if ((s = upload_state(X, h)) != POT_OK) return s;
+  SinkVecs V{};
+  V.n = n; V.m = m;
+  V.drow = (so.sum_ct - prob->s) > 1e-14 * prob->s;
+  V.dcol = (so.sum_rt - prob->s) > 1e-14 * prob->s;
+  V.re = X.U[0]; V.lre = X.U[1]; V.ce = X.V[0]; V.lce = X.V[1];
+  V.u = X.U[2]; V.v = X.V[2]; V.uprev = X.U[3];
+  V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
+  V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
+  launch_sink_init(V, prob->r, prob->c, so.eps_s, prob->s, X.st);
+  CKL();
+  PassDesc d = base_desc(X, gamma);
+  auto body = [&](int) -> pot_status {
+    pot_status q;
+    PassDesc pr = d;
+    pr.mode = PASS_ROWS; pr.arow0 = V.u; pr.bcol0 = V.v; pr.aoff0 = nullptr; pr.done = &X.S->done;
+    if ((q = run_pass(X, pr)) != POT_OK) return q;
+    launch_sink_after_rows(V, X.st);
+    PassDesc pc = d;
+    pc.mode = PASS_COLS; pc.arow0 = V.u; pc.bcol0 = V.v; pc.aoff0 = nullptr; pc.done = &X.S->done;
+    if ((q = run_pass(X, pc)) != POT_OK) return q;
+    launch_sink_after_cols(V, X.st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
+    return POT_OK;
+  };
+  const int per = params->check_every > 0 ? params->check_every : 24;
+  if ((s = drive(X, per, params->max_iter, body)) != POT_OK) return s;
+  if ((s = read_state(X, h)) != POT_OK) return s;
+  // final duals: the first n / m extended potentials, w = 0
+  CK(cudaMemcpyAsync(plan->u, V.u, sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));
+  CK(cudaMemcpyAsync(plan->v, V.v, sizeof(double) * m, cudaMemcpyDeviceToDevice, X.st));
+  CK(cudaMemsetAsync(plan->w, 0, sizeof(double), X.st));
+  CK(cudaMemsetAsync(&X.S->w_out, 0, sizeof(double), X.st));
+  res->iters = h.t;
+  res->err_final = h.E;
+  res->eps_stop = thr;
+  res->gamma = gamma;
+  res->cost_scale = X.cost_scale;
+  res->nonfinite = h.nonfinite;
+  int branch = 0;
+  if ((s = do_round(X, gamma, plan->u, plan->v, plan, &branch)) != POT_OK) return s;
+  res->rounding_branch = branch;
+  if ((s = do_objective(X, gamma, plan, &res->objective)) != POT_OK) return s;
+  res->mass = prob->s;
+  res->ms = tm.stop();
+  if (h.nonfinite || h.done == 3) { res->status = POT_ENONFINITE; return fail(POT_ENONFINITE, "non-finite potentials or sums"); }
+  const bool conv = h.done == 2;
+  res->status = (conv || (params->flags & POT_FLAG_NO_STOP)) ? POT_OK : POT_ENOCONV;
+  if (res->status == POT_ENOCONV) fail(POT_ENOCONV, "max_iter reached with residual %.3e > %.3e", h.E, thr);
+  return (pot_status)res->status;
+}
+
+pot_status pot_round(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
+                     void* workspace, size_t ws_bytes, pot_plan* plan, int32_t* branch, void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if (!(gamma > 0.0) || !isfinite(gamma)) return fail(POT_EINVAL, "gamma must be finite and > 0");
+  if (!u || !v || !isfinite(w)) return fail(POT_EINVAL, "u, v must be device pointers and w finite");
+  if (!plan || !plan->f || !plan->g || !plan->p || !plan->q || !plan->kappa) return fail(POT_EINVAL, "plan buffers missing");
+  Ctx X;
+  if ((s = bind(X, prob, 0, workspace, ws_bytes, stream)) != POT_OK) return s;
+  if ((s = prologue(X, prob->cost_scale == 0.0)) != POT_OK) return s;
+  CK(cudaMemcpyAsync(&X.S->w_out, &w, sizeof(double), cudaMemcpyHostToDevice, X.st));
+  double s2 = prob->s;
+  CK(cudaMemcpyAsync(&X.S->s, &s2, sizeof(double), cudaMemcpyHostToDevice, X.st));
+  int b = 0;
+  if ((s = do_round(X, gamma, u, v, plan, &b)) != POT_OK) return s;
+  if (branch) *branch = b;
+  CK(cudaStreamSynchronize(X.st));
+  return POT_OK;
+}
+
+pot_status pot_objective(const pot_problem* prob, const pot_plan* plan, double gamma, void* workspace,
+                         size_t ws_bytes, double* out, void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if (!(gamma > 0.0) || !isfinite(gamma)) return fail(POT_EINVAL, "gamma must be finite and > 0");
+  if (!plan || !plan->f || !plan->g || !plan->p || !plan->q || !plan->kappa) return fail(POT_EINVAL, "plan buffers missing");
+  if (!out) return fail(POT_EINVAL, "out is NULL");
+  Ctx X;
+  if ((s = bind(X, prob, 0, workspace, ws_bytes, stream)) != POT_OK) return s;
+  if ((s = prologue(X, prob->cost_scale == 0.0)) != POT_OK) return s;
+  return do_objective(X, gamma, plan, out);
+}
+
+pot_status pot_marginals(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
+                         void* workspace, size_t ws_bytes, double* lrow, double* lcol, double* tot, void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if (!(gamma > 0.0) || !isfinite(gamma)) return fail(POT_EINVAL, "gamma must be finite and > 0");
+  if (!u || !v || !isfinite(w)) return fail(POT_EINVAL, "u, v must be device pointers and w finite");
+  if (prob->cost_scale == 0.0) return fail(POT_EINVAL, "pot_marginals needs an explicit cost_scale > 0");
+  Ctx X;
+  if ((s = bind(X, prob, 0, workspace, ws_bytes, stream)) != POT_OK) return s;
+  X.cost_scale = prob->cost_scale;
+  if (prob->kind != POT_COST_DENSE_F32) {
+    launch_sqnorm(prob->kind, prob->X, prob->n, prob->d, prob->ldx, X.xn, X.st);
+    launch_sqnorm(prob->kind, prob->Y, prob->m, prob->d, prob->ldy, X.yn, X.st);
+    CKL();
+  }
+  CK(cudaMemcpyAsync(&X.S->w_out, &w, sizeof(double), cudaMemcpyHostToDevice, X.st));
+  CK(cudaMemsetAsync(X.cnt, 0, sizeof(unsigned int) * 8, X.st));
+  PassDesc d = base_desc(X, gamma);
+  d.mode = PASS_ROWS | (lcol ? PASS_COLS : 0);
+  d.arow0 = u; d.bcol0 = v; d.aoff0 = &X.S->w_out;
+  if ((s = run_pass(X, d)) != POT_OK) return s;
+  launch_marginals_out(prob->n, prob->m, X.rowp, lcol ? X.colp : nullptr, X.L.ncolblk, X.L.nrowblk, lrow, lcol,
+                       X.red, X.cnt, tot, X.st);
+  CKL();
+  return POT_OK;
+}
+
+pot_status pot_cost_max(const pot_problem* prob, void* workspace, size_t ws_bytes, double* out, void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if (!out) return fail(POT_EINVAL, "out is NULL");
+  Ctx X;
+  if ((s = bind(X, prob, 0, workspace, ws_bytes, stream)) != POT_OK) return s;
+  if ((s = prologue(X, true)) != POT_OK) return s;
+  *out = X.max_raw;
+  return POT_OK;
+}
+
+pot_status pot_plan_dense(const pot_problem* prob, const pot_plan* plan, double gamma, float* Xout, int64_t ldx,
+                          void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if (!(prob->cost_scale > 0.0)) return fail(POT_EINVAL, "pot_plan_dense needs an explicit cost_scale > 0");
+  if (!(gamma > 0.0)) return fail(POT_EINVAL, "gamma must be > 0");
+  if (!plan || !plan->f || !plan->g || !plan->p || !plan->q || !plan->kappa || !Xout) return fail(POT_EINVAL, "missing buffers");
+  if (ldx < prob->m) return fail(POT_EINVAL, "ldx < m");
+  PassDesc d{};
+  d.n = prob->n; d.m = prob->m; d.kind = prob->kind; d.C = prob->C; d.ldc = prob->ldc;
+  d.X = prob->X; d.Y = prob->Y; d.d = prob->d; d.ldx = prob->ldx; d.ldy = prob->ldy;
+  d.gC = prob->cost_scale / gamma;
+  launch_dense_plan(d, plan->f, plan->g, plan->p, plan->q, plan->kappa, Xout, ldx, (cudaStream_t)stream);
+  CKL();
+  return POT_OK;
+}
+
+pot_status pot_trace(void* workspace, int32_t iters, double* out, void* stream) {
+  g_err.clear();
+  if (!workspace || !out || iters < 0) return fail(POT_EINVAL, "bad arguments");
+  const DevState* S = (const DevState*)((char*)workspace);   // the state sits at offset 0
+  const int k = std::min(iters, 4096);
+  CK(cudaMemcpyAsync(out, S->trace, sizeof(double) * 4 * k, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return POT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Shared device helpers of the ASPOT / feasible-Sinkhorn CUDA library.
+//
+// Numerics of every pass (the O(nm) reductions of the method):
+//   logit_ij = a_i + b_j - gC * cost_ij          (log of an entry of B(z))
+// where a_i collects the row potential (u_i + w, or u_i for the extended
+// Sinkhorn kernel) and b_j the column potential.  Potentials are FP64
+// masters; a pass receives them as FP32 (hi, lo) pairs, with hi rounded to a
+// multiple of 2^-12 so that hi_a + hi_b is exact in FP32 for |a|,|b| < 2^11.
+// The logit is then fma(-gC, cost, hi_a + hi_b) + (lo_a + lo_b): one rounding
+// relative to the (small) logit instead of one relative to |u|+|v|+|w|.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#define POT_NEG_BIG (-1.0e30)      // stands for log 0 in FP64 potentials
+#define POT_NEG_BIGF (-1.0e30f)
+
+namespace pot {
+
+struct HiLo { float hi, lo; };
+
+__device__ __forceinline__ HiLo split_hilo(double x) {
+  HiLo r;
+  if (!(x > -1.0e29)) { r.hi = POT_NEG_BIGF; r.lo = 0.f; return r; }   // log 0 (also NaN -> -big)
+  double h = nearbyint(x * 4096.0) * (1.0 / 4096.0);
+  r.hi = (float)h;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+
+// 2^x with the hardware approximation (flushes denormal results to 0).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// log-sum-exp accumulator in FP64: value = m + log(s)
+struct Lse {
+  double m, s;
+  __device__ __forceinline__ void init() { m = -INFINITY; s = 0.0; }
+  // add a partial (shift k, sum t) meaning log(t) + k, all in the natural log
+  __device__ __forceinline__ void add(double k, double t) {
+    if (!(t > 0.0)) return;
+    if (k > m) { s = s * exp(m - k) + t; m = k; }
+    else { s += t * exp(k - m); }
+  }
+  __device__ __forceinline__ double value() const { return s > 0.0 ? m + log(s) : POT_NEG_BIG; }
+};
+
+__device__ __forceinline__ double softplus(double x) {   // log(1 + e^x)
+  return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x));
+}
+__device__ __forceinline__ double logaddexp(double a, double b) {
+  double mx = fmax(a, b);
+  if (mx <= POT_NEG_BIG) return POT_NEG_BIG;
+  return mx + log1p(exp(-fabs(a - b)));
+}
+
+}  // namespace pot

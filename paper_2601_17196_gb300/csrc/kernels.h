@@ -1,0 +1,106 @@
+// Internal (host-side) declarations shared by the translation units of the
+// library.  Nothing here is part of the public C-ABI (include/aspot.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include "pass.h"
+
+namespace pot {
+
+// ---------------------------------------------------------------- passes --
+struct SimtLayout { int V; int H; int64_t ncolblk, nrowblk; };
+SimtLayout simt_layout(int64_t n, int64_t m);
+void launch_pass_simt(const PassDesc& P, const SimtLayout& L, cudaStream_t st);
+void launch_sqnorm(int kind, const void* X, int64_t n, int d, int64_t ldx, float* out, cudaStream_t st);
+
+// tcgen05 on-the-fly squared-Euclidean pass (BF16 points)
+struct TcLayout { int64_t ncolblk, nrowblk, nchunks, tiles_per_chunk, n_pad, m_pad; int ok; };
+TcLayout tc_layout(int64_t n, int64_t m, int d);
+bool tc_supported(const PassDesc& P);
+cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st);
+
+// --------------------------------------------------------- device state --
+struct DevState {
+  double theta;
+  double w_tilde, w_check, w_bar, w_grave, w_hat, w_z, w_out;
+  double phi_check, phi_hat, phi_z;
+  double E, tot;
+  double L, s, thr, log_s;
+  double sum_rt, sum_ct;
+  double m2, sum_p, sum_q, kappa, log_k1, obj;
+  double A_over_g;
+  int t, take_hat, done, max_iter, nonfinite, tc_err;
+  unsigned int counter;
+  unsigned int pad2;
+  double trace[4096][4];     // E, phi_z, phi_check, take_hat per iteration (ring)
+};
+
+struct RedBuf { double* part; unsigned int* counter; int nblk; };
+
+struct AspotVecs {
+  int64_t n, m;
+  const double *rt, *ct, *lrt, *lct;
+  double *ut, *vt, *uc, *vc, *ub, *vb, *ug, *vg, *uh, *vh, *uo, *vo;
+  const float2* row_part; const float2* col_part;
+  int64_t ncolblk, nrowblk;
+  double* red; unsigned int* counter;
+  DevState* S;
+  int trace;
+};
+
+struct SinkVecs {
+  int64_t n, m;
+  int drow, dcol;
+  const double *re, *ce, *lre, *lce;   // extended marginals (n+1, m+1)
+  double *u, *v, *uprev;               // extended potentials
+  const float2* row_part; const float2* col_part;
+  int64_t ncolblk, nrowblk;
+  double* red; unsigned int* counter;
+  DevState* S;
+  int trace;
+};
+
+struct RoundVecs {
+  int64_t n, m;
+  const double *r, *c;        // original marginals
+  const double *u, *v;        // duals to round (w in S->w_out)
+  double *f, *g, *p, *q;      // plan
+  double* kappa;
+  const float2* row_part; const float2* col_part;
+  int64_t ncolblk, nrowblk;
+  double* red; unsigned int* counter;
+  DevState* S;
+};
+
+constexpr int kVecThreads = 256;
+inline int vec_blocks(int64_t len) { return (int)((len + kVecThreads - 1) / kVecThreads); }
+
+// prologue: masses, minima, finiteness of r and c -> S (sum_rt/ct reused as raw masses)
+void launch_marg_stats(const double* r, const double* c, int64_t n, int64_t m, double* red,
+                       unsigned int* counter, double* out6, cudaStream_t st);
+void launch_reduce_parts(const double* part, int64_t count, int op_max, double* out, cudaStream_t st);
+void launch_aspot_init(const AspotVecs& V, const double* r, const double* c, double eps_s,
+                       const double* u0, const double* v0, double w0, cudaStream_t st);
+void launch_aspot_extrap(const AspotVecs& V, cudaStream_t st);
+void launch_aspot_after_grad(const AspotVecs& V, cudaStream_t st);
+void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st);
+void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st);
+
+void launch_sink_init(const SinkVecs& V, const double* r, const double* c, double eps_s, double s,
+                      cudaStream_t st);
+void launch_sink_after_rows(const SinkVecs& V, cudaStream_t st);
+void launch_sink_after_cols(const SinkVecs& V, cudaStream_t st);
+
+void launch_round_r1(const RoundVecs& V, cudaStream_t st);
+void launch_round_r2(const RoundVecs& V, cudaStream_t st);
+void launch_round_r3(const RoundVecs& V, cudaStream_t st);
+void launch_round_r4(const RoundVecs& V, cudaStream_t st);
+
+void launch_marginals_out(int64_t n, int64_t m, const float2* row_part, const float2* col_part,
+                          int64_t ncolblk, int64_t nrowblk, double* lrow, double* lcol, double* red,
+                          unsigned int* counter, double* tot_out, cudaStream_t st);
+void launch_dense_plan(const PassDesc& P, const double* f, const double* g, const double* p,
+                       const double* q, const double* kappa, float* X, int64_t ldx, cudaStream_t st);
+
+}  // namespace pot

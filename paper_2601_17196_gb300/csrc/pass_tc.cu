@@ -1,0 +1,580 @@
+// On-the-fly squared-Euclidean passes on the 5th-generation tensor cores
+// (tcgen05, sm_103a) for BF16 point clouds.
+//
+// For a tile of 128 rows x 128 columns the dot products x_i . y_j are formed
+// by tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 accumulator in TMEM) from
+// TMA-loaded, 128B-swizzled shared-memory tiles; the cost
+//   C_ij = cost_scale (|x_i|^2 + |y_j|^2 - 2 x_i . y_j)
+// is never written anywhere.  The epilogue reads the accumulator with
+// tcgen05.ld and fuses
+//   logit2_ij = a_i + b_j + k2 * acc_ij        (log2 units, k2 = 2 log2(e) cost_scale / gamma)
+// with the row and column log-sum-exp reductions of the pass:
+//   * row side: each epilogue thread owns one row (one TMEM lane) and 64
+//     columns of a tile; exact per-tile row max, one ex2 per entry;
+//   * column side: the same exponentials are rescaled by a per-row factor
+//     relative to the warp's largest row maximum and reduced over the 32 rows
+//     of the warp with a transposing butterfly; four warps are merged in
+//     shared memory into one (shift, sum) partial per column and 128 rows.
+// The row potential enters as hi + lo where hi lies on a 2^-12 grid, so
+// hi_a + hi_b is exact in FP32 and the FMA rounds once relative to the small
+// result; lo_a is applied per row (it is constant along the row).
+//
+// Warp roles (320 threads): warp 0 issues TMA loads (X tile once per work
+// unit, a 2-stage ring of Y tiles), warp 1 allocates TMEM (2 x 128 columns,
+// double-buffered accumulator) and issues the MMAs, warps 2..9 are the
+// epilogue (warps 2-5 take columns 0-63 of a tile, warps 6-9 columns 64-127).
+// Every wait on an mbarrier is bounded by %globaltimer: after 2 s the kernel
+// raises an error flag, stops issuing work and still frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include "common.cuh"
+#include "pass.h"
+#include "kernels.h"
+
+namespace pot {
+
+namespace {
+
+constexpr int BM = 128, BN = 128;
+constexpr int NSTAGE = 2;
+constexpr int NTHREADS = 320;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr double kL2E = 1.4426950408889634;
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+
+enum { M_RC = 0, M_R = 1, M_C = 2, M_MAX = 3, M_OBJ = 4 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; on timeout raises the CTA abort flag and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (gtime() - t0 > kTimeoutNs) { *abort = 1; return false; }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart (tcgen05 descriptor format).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 TMEM columns of this warp's 32 lanes: thread t gets lane (base + t).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Sum of v[k] over the 32 lanes for each k < 32; lane l ends with column l in v[0].
+__device__ __forceinline__ float transpose_reduce32(float* v, int lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = lane & w;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const float send = up ? v[k] : v[k + w];
+      const float keep = up ? v[k + w] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+struct TcSmemLayout {
+  uint32_t a_off, b_off, b_stage, cs_off, cm_off, rs_off, red_off, bar_off, misc_off, total;
+};
+
+__host__ __device__ inline TcSmemLayout tc_smem_layout(int d) {
+  TcSmemLayout L;
+  const uint32_t kb = (uint32_t)(d / 64);
+  L.a_off = 0;
+  L.b_stage = kb * BN * 128;
+  L.b_off = kb * BM * 128;
+  uint32_t o = L.b_off + NSTAGE * L.b_stage;
+  L.cs_off = o; o += 2 * 2 * 4 * 64 * 4;     // [buf][half][quad][64] floats
+  L.cm_off = o; o += 2 * 2 * 4 * 4;          // [buf][half][quad]
+  L.rs_off = o; o += 2 * 128 * 8;            // [half][row] float2
+  L.red_off = o; o += 16 * 8;                // per-warp doubles
+  L.bar_off = (o + 7) & ~7u; o = L.bar_off + 16 * 8;
+  L.misc_off = o; o += 16;
+  L.total = o;
+  return L;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1)
+tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled operand tiles
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const TcSmemLayout SL = tc_smem_layout(P.d);
+  const int kblocks = P.d / 64;
+  uint64_t* bars = (uint64_t*)(smem + SL.bar_off);
+  uint64_t* fullA = bars + 0;
+  uint64_t* fullB = bars + 1;           // [NSTAGE]
+  uint64_t* emptyB = bars + 1 + NSTAGE; // [NSTAGE]
+  uint64_t* tfull = bars + 1 + 2 * NSTAGE;      // [2]
+  uint64_t* tempty = bars + 3 + 2 * NSTAGE;     // [2]
+  uint32_t* s_tmem = (uint32_t*)(smem + SL.misc_off);
+  volatile int* s_abort = (volatile int*)(smem + SL.misc_off + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (P.done && *P.done) return;
+
+  const int64_t unit = blockIdx.x;
+  const int64_t rb = unit / TL.nchunks, ch = unit % TL.nchunks;
+  const int64_t ntiles = (P.m + BN - 1) / BN;
+  const int64_t t_begin = ch * TL.tiles_per_chunk;
+  const int64_t t_end = (t_begin + TL.tiles_per_chunk < ntiles) ? t_begin + TL.tiles_per_chunk : ntiles;
+  const int nt = (int)(t_end - t_begin);
+
+  if (threadIdx.x == 0) {
+    mbar_init(fullA, 1);
+    for (int s = 0; s < NSTAGE; ++s) { mbar_init(fullB + s, 1); mbar_init(emptyB + s, 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, 8); }
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0 && nt > 0) {
+      unsigned char* sA = smem + SL.a_off;
+      mbar_expect_tx(fullA, (uint32_t)(kblocks * BM * 128));
+      for (int kb = 0; kb < kblocks; ++kb)
+        tma_load_2d(sA + kb * BM * 128, &tmX, fullA, kb * 64, (int)(rb * BM));
+      int issued = 0;
+      for (int li = 0; li < nt; ++li) {
+        const int s = li % NSTAGE;
+        if (li >= NSTAGE && !mbar_wait(emptyB + s, ((li / NSTAGE) - 1) & 1, s_abort)) break;
+        unsigned char* sB = smem + SL.b_off + s * SL.b_stage;
+        mbar_expect_tx(fullB + s, SL.b_stage);
+        const int col = (int)((t_begin + li) * BN);
+        for (int kb = 0; kb < kblocks; ++kb) tma_load_2d(sB + kb * BN * 128, &tmY, fullB + s, kb * 64, col);
+        issued = li + 1;
+      }
+      // wait for our own loads still in flight before the CTA may exit
+      for (int li = (issued > NSTAGE ? issued - NSTAGE : 0); li < issued; ++li) {
+        const int s = li % NSTAGE;
+        const uint64_t t0 = gtime();
+        while (!mbar_try(fullB + s, (li / NSTAGE) & 1) && gtime() - t0 < kTimeoutNs) {}
+      }
+      {
+        const uint64_t t0 = gtime();
+        while (!mbar_try(fullA, 0) && gtime() - t0 < kTimeoutNs) {}
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA
+    if (lane == 0 && nt > 0) {
+      const uint32_t idesc = idesc_bf16(BM, BN);
+      const uint32_t a_base = smem_u32(smem + SL.a_off);
+      int last = -1;
+      if (mbar_wait(fullA, 0, s_abort)) {
+        for (int li = 0; li < nt; ++li) {
+          const int b = li & 1, s = li % NSTAGE;
+          if (li >= 2 && !mbar_wait(tempty + b, ((li >> 1) - 1) & 1, s_abort)) break;
+          if (!mbar_wait(fullB + s, (li / NSTAGE) & 1, s_abort)) break;
+          tc_fence_after();
+          const uint32_t b_base = smem_u32(smem + SL.b_off + s * SL.b_stage);
+          for (int kb = 0; kb < kblocks; ++kb) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = sdesc(a_base + kb * BM * 128 + kk * 32);
+              const uint64_t bd = sdesc(b_base + kb * BN * 128 + kk * 32);
+              umma_bf16(tmem + (uint32_t)(b * BN), ad, bd, idesc, (kb | kk) != 0);
+            }
+          }
+          umma_commit(emptyB + s);
+          umma_commit(tfull + b);
+          last = li;
+        }
+      }
+      // the accumulator of the last issued tile must be complete before TMEM is freed
+      if (last >= 0) {
+        const uint64_t t0 = gtime();
+        while (!mbar_try(tfull + (last & 1), (last >> 1) & 1) && gtime() - t0 < kTimeoutNs) {}
+      }
+    }
+  } else {
+    // ----------------------------------------------------------- epilogue
+    const int q = warp & 3;                  // TMEM lane quadrant of this warp
+    const int h = (warp - 2) >> 2;           // column half of the tile
+    const int r = q * 32 + lane;
+    const int64_t i = rb * BM + r;
+    const float4 ra = P.rowA[i];             // rows padded to a multiple of 128
+    const float ahi = ra.x, alo = ra.y;
+    const float k2 = (MODE == M_MAX) ? -2.0f : (float)(2.0 * P.gC * kL2E);
+    float* cs = (float*)(smem + SL.cs_off);
+    float* cm = (float*)(smem + SL.cm_off);
+    float2* rs = (float2*)(smem + SL.rs_off);
+    float Mr = POT_NEG_BIGF, Sr = 0.f;        // running row (max, sum) over this half's columns
+    float maxc = POT_NEG_BIGF;
+    double objacc = 0.0;
+    const float kap = (MODE == M_OBJ) ? (float)*P.kappa : 0.f;
+    const float4* colA4 = reinterpret_cast<const float4*>(P.colA);
+    for (int li = 0; li < nt; ++li) {
+      const int b = li & 1;
+      const int64_t j0 = (t_begin + li) * BN + h * 64;
+      float t[64];
+      const bool ok = mbar_wait(tfull + b, (li >> 1) & 1, s_abort);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + h * 64);
+        tmem_ld32(ta, t);
+        tmem_ld32(ta + 32, t + 32);
+        tmem_wait_ld();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + b);
+      if (!ok) {
+#pragma unroll
+        for (int k = 0; k < 64; ++k) t[k] = 0.f;
+      }
+      if (MODE == M_OBJ) {
+        // <C, X> contribution: raw cost from the accumulator, plan entry from the logit
+        const float2* colB2 = P.colB;
+        float accf = 0.f;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const float4 bb = __ldg(colA4 + ((j0 >> 1) + c));
+#pragma unroll
+          for (int e2 = 0; e2 < 2; ++e2) {
+            const int k = 2 * c + e2;
+            const float2 yq = __ldg(colB2 + j0 + k);
+            const float bh = e2 ? bb.z : bb.x, bl = e2 ? bb.w : bb.y;
+            const float lg = fmaf(k2, t[k], ahi + bh) + bl + alo;
+            const float x = ex2(lg) + kap * ra.w * yq.y;
+            const float cst = fmaxf(fmaf(-2.f, t[k], ra.z + yq.x), 0.f);
+            accf = fmaf(cst, x, accf);
+          }
+        }
+        objacc += (double)accf;
+        continue;
+      }
+      // logits (log2 units, without the per-row lo part)
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const float4 bb = __ldg(colA4 + ((j0 >> 1) + c));
+        t[2 * c] = fmaf(k2, t[2 * c], ahi + bb.x) + bb.y;
+        t[2 * c + 1] = fmaf(k2, t[2 * c + 1], ahi + bb.z) + bb.w;
+      }
+      float mx = t[0];
+#pragma unroll
+      for (int k = 1; k < 64; ++k) mx = fmaxf(mx, t[k]);
+      if (MODE == M_MAX) {
+        maxc = fmaxf(maxc, mx);
+        continue;
+      }
+      const bool rowok = mx > -1.0e29f;
+      float ssum = 0.f;
+#pragma unroll
+      for (int k = 0; k < 64; ++k) {
+        const float e = rowok ? ex2(t[k] - mx) : 0.f;
+        t[k] = e;
+        ssum += e;
+      }
+      if (MODE == M_RC || MODE == M_R) {
+        if (rowok) {
+          if (mx > Mr) { Sr = Sr * ex2(Mr - mx) + ssum; Mr = mx; }
+          else Sr = fmaf(ssum, ex2(mx - Mr), Sr);
+        }
+      }
+      if (MODE == M_RC || MODE == M_C) {
+        const float cmv = rowok ? alo + mx : POT_NEG_BIGF;
+        float Mw = cmv;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Mw = fmaxf(Mw, __shfl_xor_sync(0xffffffffu, Mw, o));
+        float v0 = 0.f, v1 = 0.f;
+        if (Mw > -1.0e29f) {
+          const float f = rowok ? ex2(cmv - Mw) : 0.f;
+#pragma unroll
+          for (int k = 0; k < 64; ++k) t[k] *= f;
+          v0 = transpose_reduce32(t, lane);
+          v1 = transpose_reduce32(t + 32, lane);
+        }
+        const int buf = li & 1;
+        float* csb = cs + ((buf * 2 + h) * 4 + q) * 64;
+        csb[lane] = v0;
+        csb[32 + lane] = v1;
+        if (lane == 0) cm[(buf * 2 + h) * 4 + q] = Mw;
+        named_bar(1 + h, 128);
+        if (q == 0) {
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c = lane + 32 * cc;
+            const int64_t j = j0 + c;
+            float M = POT_NEG_BIGF;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) M = fmaxf(M, cm[(buf * 2 + h) * 4 + qq]);
+            float S = 0.f;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const float Mq = cm[(buf * 2 + h) * 4 + qq];
+              if (Mq > -1.0e29f) S = fmaf(cs[((buf * 2 + h) * 4 + qq) * 64 + c], ex2(Mq - M), S);
+            }
+            if (j < P.m) P.col_part[rb * P.m + j] = make_float2(M, S);
+          }
+        }
+      }
+    }
+    // row partials: merge the two column halves
+    if (MODE == M_RC || MODE == M_R) {
+      rs[h * 128 + r] = make_float2(Mr, Sr);
+      named_bar(3, 256);
+      if (h == 0 && i < P.n) {
+        const float2 o = rs[128 + r];
+        float M = Mr, S = Sr;
+        if (o.x > M) { S = S * (M > -1.0e29f ? ex2(M - o.x) : 0.f) + o.y; M = o.x; }
+        else if (o.x > -1.0e29f) S = fmaf(o.y, ex2(o.x - M), S);
+        P.row_part[ch * P.n + i] = make_float2(M > -1.0e29f ? alo + M : POT_NEG_BIGF, S);
+      }
+    }
+    if (MODE == M_MAX || MODE == M_OBJ) {
+      double* red = (double*)(smem + SL.red_off);
+      double v = (MODE == M_MAX) ? (double)maxc : objacc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_xor_sync(0xffffffffu, v, o);
+        v = (MODE == M_MAX) ? fmax(v, y) : v + y;
+      }
+      if (lane == 0) red[warp - 2] = v;
+      named_bar(3, 256);
+      if (threadIdx.x == 64) {
+        double mm = red[0];
+        for (int w = 1; w < 8; ++w) mm = (MODE == M_MAX) ? fmax(mm, red[w]) : mm + red[w];
+        P.red_part[unit] = mm;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (*s_abort && threadIdx.x == 0 && P.err) atomicExch(P.err, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Per-pass row / column terms in log2 units (see the file comment).  Rows
+// and columns are padded to multiples of 128 with log-zero terms.
+__global__ void tc_prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad) {
+  if (P.done && *P.done) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool use1 = P.sel && *P.sel;
+  const double* arow = use1 ? P.arow1 : P.arow0;
+  const double* bcol = use1 ? P.bcol1 : P.bcol0;
+  const double* aoffp = use1 ? P.aoff1 : P.aoff0;
+  const bool maxmode = P.mode & PASS_MAXCOST;
+  if (t < n_pad) {
+    float4 o = make_float4(POT_NEG_BIGF, 0.f, 0.f, 0.f);
+    if (t < P.n) {
+      const float xn = P.xn[t];
+      if (maxmode) {
+        o = make_float4(xn, 0.f, xn, 0.f);
+      } else {
+        const double a = (arow[t] + (aoffp ? *aoffp : 0.0) - P.gC * (double)xn) * kL2E;
+        HiLo hl = split_hilo(a);
+        o = make_float4(hl.hi, hl.lo, xn, (P.mode & PASS_OBJ) ? (float)P.p[t] : 0.f);
+      }
+    }
+    P.rowA[t] = o;
+  } else if (t < n_pad + m_pad) {
+    const int64_t j = t - n_pad;
+    float2 A = make_float2(POT_NEG_BIGF, 0.f), Bv = make_float2(0.f, 0.f);
+    if (j < P.m) {
+      const float yn = P.yn[j];
+      if (maxmode) {
+        A = make_float2(yn, 0.f);
+      } else {
+        const double b = ((double)bcol[j] - P.gC * (double)yn) * kL2E;
+        HiLo hl = split_hilo(b);
+        A = make_float2(hl.hi, hl.lo);
+        Bv = make_float2(yn, (P.mode & PASS_OBJ) ? (float)P.q[j] : 0.f);
+      }
+    }
+    P.colA[j] = A;
+    P.colB[j] = Bv;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int d, int64_t ld) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int MODE>
+cudaError_t launch_mode(const PassDesc& P, const TcLayout& L, const CUtensorMap& mx, const CUtensorMap& my,
+                        cudaStream_t st) {
+  const TcSmemLayout SL = tc_smem_layout(P.d);
+  uint32_t smem = SL.total + 1024;
+  if (smem < 100 * 1024) smem = 100 * 1024;     // at most two CTAs (2 x 256 TMEM columns) per SM
+  static int configured = 0;
+  if (configured < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(tc_pass_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = (int)smem;
+  }
+  tc_pass_kernel<MODE><<<(unsigned)(L.nrowblk * L.nchunks), NTHREADS, smem, st>>>(P, L, mx, my);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+TcLayout tc_layout(int64_t n, int64_t m, int d) {
+  TcLayout L{};
+  (void)d;
+  L.nrowblk = (n + BM - 1) / BM;
+  const int64_t ntiles = (m + BN - 1) / BN;
+  // choose the number of column chunks so that the work units fill whole
+  // waves of 2 x 152 resident CTAs as evenly as possible (>= 8 tiles a unit)
+  const int64_t slots = 2 * 152;
+  double best = -1.0;
+  int64_t best_c = 1;
+  for (int64_t c = 1; c <= 64 && c <= ntiles; ++c) {
+    const int64_t tpc = (ntiles + c - 1) / c;
+    if (tpc < 8 && c > 1) break;
+    const int64_t units = L.nrowblk * ((ntiles + tpc - 1) / tpc);
+    const double waves = (double)units / slots;
+    const double eff = waves / ceil(waves);
+    if (eff > best + 1e-9) { best = eff; best_c = c; }
+  }
+  L.tiles_per_chunk = (ntiles + best_c - 1) / best_c;
+  L.nchunks = (ntiles + L.tiles_per_chunk - 1) / L.tiles_per_chunk;
+  L.ncolblk = L.nchunks;
+  L.n_pad = L.nrowblk * BM;
+  L.m_pad = ntiles * BN;
+  L.ok = 1;
+  return L;
+}
+
+bool tc_supported(const PassDesc& P) {
+  if (P.kind != COST_SQEUCLID_BF16) return false;
+  if (P.d < 64 || P.d > 256 || (P.d % 64) != 0) return false;
+  if ((P.ldx * 2) % 16 != 0 || (P.ldy * 2) % 16 != 0) return false;
+  if (((uintptr_t)P.X % 16) != 0 || ((uintptr_t)P.Y % 16) != 0) return false;
+  if (P.n >= (int64_t(1) << 30) || P.m >= (int64_t(1) << 30)) return false;
+  return true;
+}
+
+cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st) {
+  const int64_t tot = L.n_pad + L.m_pad;
+  tc_prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, L.n_pad, L.m_pad);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  CUtensorMap mx, my;
+  if (!make_map(&mx, P.X, P.n, P.d, P.ldx) || !make_map(&my, P.Y, P.m, P.d, P.ldy)) return cudaErrorInvalidValue;
+  const int md = P.mode;
+  if (md & PASS_MAXCOST) return launch_mode<M_MAX>(P, L, mx, my, st);
+  if (md & PASS_OBJ) return launch_mode<M_OBJ>(P, L, mx, my, st);
+  if ((md & PASS_ROWS) && (md & PASS_COLS)) return launch_mode<M_RC>(P, L, mx, my, st);
+  if (md & PASS_ROWS) return launch_mode<M_R>(P, L, mx, my, st);
+  return launch_mode<M_C>(P, L, mx, my, st);
+}
+
+}  // namespace pot

@@ -1,0 +1,669 @@
+// O(n + m) kernels around the passes: combining log-sum-exp partials, the
+// dual updates of ASPOT (Algorithm 2) and of the feasible Sinkhorn baseline
+// (Algorithm 3 on the extended kernel), the rounding reading R1-R4 and the
+// scalar bookkeeping.  Everything here is FP64.
+//
+// Scalar reductions are deterministic: every block writes its partial, the
+// last block to finish (atomic ticket) sums the partials in block order and
+// performs the scalar part of the update.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace pot {
+
+namespace {
+
+constexpr double kLn2 = 0.6931471805599453;
+
+// natural log of sum over blocks of partials (max2, sum) in log2 units
+__device__ __forceinline__ double combine_parts(const float2* part, int64_t nblk, int64_t stride, int64_t idx) {
+  Lse acc;
+  acc.init();
+  for (int64_t b = 0; b < nblk; ++b) {
+    const float2 p = part[b * stride + idx];
+    if (p.y > 0.f) acc.add((double)p.x * kLn2, (double)p.y);
+  }
+  return acc.value();
+}
+
+template <int NV>
+__device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* counter, double (&tot)[NV]) {
+  __shared__ double sh[NV][kVecThreads / 32];
+  __shared__ double st[NV];
+  __shared__ int amlast;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double x = warp_sum_d(v[k]);
+    if (lane == 0) sh[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < kVecThreads / 32; ++w) s += sh[k][w];
+      part[(int64_t)blockIdx.x * NV + k] = s;
+    }
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    amlast = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!amlast) return false;
+  __threadfence();
+  if (warp < NV) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (int64_t)b * NV + warp);
+    s = warp_sum_d(s);
+    if (lane == 0) st[warp] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = st[k];
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// NV sums plus one log-sum-exp over the grid: each thread contributes v[] and
+// (x, active) to log sum exp(x).  The last block gets the totals (sums in
+// block order, the log-sum-exp in natural log).
+template <int NV>
+__device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, double* part,
+                                unsigned int* counter, double (&tot)[NV], double* lse_out) {
+  constexpr int NW = kVecThreads / 32;
+  constexpr int NP = NV + 2;
+  __shared__ double sh[NV > 0 ? NV : 1][NW];
+  __shared__ double smx[NW], ssm[NW];
+  __shared__ double st[NV > 0 ? NV : 1];
+  __shared__ double slse;
+  __shared__ int amlast;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double y = warp_sum_d(v[k]);
+    if (lane == 0) sh[k][warp] = y;
+  }
+  double mx = active ? x : -INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  double sm = (active && mx > -INFINITY) ? exp(x - mx) : 0.0;
+  sm = warp_sum_d(sm);
+  if (lane == 0) { smx[warp] = mx; ssm[warp] = sm; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < NW; ++w) a += sh[k][w];
+      part[(int64_t)blockIdx.x * NP + k] = a;
+    }
+    Lse l;
+    l.init();
+    for (int w = 0; w < NW; ++w) if (ssm[w] > 0.0) l.add(smx[w], ssm[w]);
+    part[(int64_t)blockIdx.x * NP + NV] = l.m;
+    part[(int64_t)blockIdx.x * NP + NV + 1] = l.s;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    amlast = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!amlast) return false;
+  __threadfence();
+  if (warp < NV) {
+    double a = 0.0;
+    for (int b2 = lane; b2 < (int)gridDim.x; b2 += 32) a += __ldcg(part + (int64_t)b2 * NP + warp);
+    a = warp_sum_d(a);
+    if (lane == 0) st[warp] = a;
+  }
+  if (threadIdx.x == 32 * NW - 1) {
+    Lse l;
+    l.init();
+    for (int b2 = 0; b2 < (int)gridDim.x; ++b2) {
+      const double ss = __ldcg(part + (int64_t)b2 * NP + NV + 1);
+      if (ss > 0.0) l.add(__ldcg(part + (int64_t)b2 * NP + NV), ss);
+    }
+    slse = l.value();
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = st[k];
+  *lse_out = slse;
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+__device__ __forceinline__ double clamp_log(double x) { return x > POT_NEG_BIG ? x : POT_NEG_BIG; }
+__device__ __forceinline__ double safe_exp(double x) { return x > -700.0 ? exp(x) : 0.0; }
+
+// ----------------------------------------------------------- prologue ---
+
+__global__ void marg_stats_kernel(const double* r, const double* c, int64_t n, int64_t m, double* part,
+                                  unsigned int* counter, double* out) {
+  // out: [sum r, sum c, min r, min c, #nonfinite-or-negative, 0]
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[4] = {0, 0, 0, 0};
+  double mnr = INFINITY, mnc = INFINITY;
+  if (t < n) { const double x = r[t]; v[0] = x; mnr = x; if (!(x >= 0.0) || !isfinite(x)) v[2] = 1; }
+  else if (t < n + m) { const double x = c[t - n]; v[1] = x; mnc = x; if (!(x >= 0.0) || !isfinite(x)) v[2] = 1; }
+  // minima through the sum slot trick: reduce -min separately
+  __shared__ double smr[kVecThreads / 32], smc[kVecThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mnr = fmin(mnr, __shfl_xor_sync(0xffffffffu, mnr, o));
+    mnc = fmin(mnc, __shfl_xor_sync(0xffffffffu, mnc, o));
+  }
+  if (lane == 0) { smr[warp] = mnr; smc[warp] = mnc; }
+  __syncthreads();
+  double bmr = INFINITY, bmc = INFINITY;
+  for (int w = 0; w < kVecThreads / 32; ++w) { bmr = fmin(bmr, smr[w]); bmc = fmin(bmc, smc[w]); }
+  // store block minima in dedicated slots after the sums (part has 6 per block)
+  double tot[3];
+  double vv[3] = {v[0], v[1], v[2]};
+  if (threadIdx.x == 0) { part[(int64_t)gridDim.x * 3 + 2 * blockIdx.x] = bmr; part[(int64_t)gridDim.x * 3 + 2 * blockIdx.x + 1] = bmc; }
+  if (reduce_last<3>(vv, part, counter, tot)) {
+    if (threadIdx.x == 0) {
+      double mr = INFINITY, mc = INFINITY;
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        mr = fmin(mr, __ldcg(part + (int64_t)gridDim.x * 3 + 2 * b));
+        mc = fmin(mc, __ldcg(part + (int64_t)gridDim.x * 3 + 2 * b + 1));
+      }
+      out[0] = tot[0]; out[1] = tot[1]; out[2] = mr; out[3] = mc; out[4] = tot[2]; out[5] = 0.0;
+    }
+  }
+}
+
+__global__ void reduce_parts_kernel(const double* part, int64_t count, int op_max, double* out) {
+  __shared__ double sh[32];
+  double acc = op_max ? -INFINITY : 0.0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const double x = part[i];
+    acc = op_max ? fmax(acc, x) : acc + x;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_xor_sync(0xffffffffu, acc, o);
+    acc = op_max ? fmax(acc, y) : acc + y;
+  }
+  if (lane == 0) sh[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = op_max ? -INFINITY : 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) a = op_max ? fmax(a, sh[w]) : a + sh[w];
+    *out = a;
+  }
+}
+
+// --------------------------------------------------------------- ASPOT ---
+
+// Algorithm 2 setup: smoothed marginals r~ = (1 - e/8) r + e/(8n), their
+// logs, and the starting point z~^0 = z_check^0 (zero or a warm start).
+__global__ void aspot_init_kernel(AspotVecs V, const double* r, const double* c, double eps_s,
+                                  const double* u0, const double* v0, double w0) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double* rt = const_cast<double*>(V.rt);
+  double* ct = const_cast<double*>(V.ct);
+  double* lrt = const_cast<double*>(V.lrt);
+  double* lct = const_cast<double*>(V.lct);
+  if (t < V.n) {
+    const double x = (1.0 - eps_s / 8.0) * r[t] + eps_s / (8.0 * (double)V.n);
+    rt[t] = x; lrt[t] = x > 0.0 ? log(x) : POT_NEG_BIG;
+    const double z = u0 ? u0[t] : 0.0;
+    V.ut[t] = z; V.uc[t] = z; V.uo[t] = z;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    const double x = (1.0 - eps_s / 8.0) * c[j] + eps_s / (8.0 * (double)V.m);
+    ct[j] = x; lct[j] = x > 0.0 ? log(x) : POT_NEG_BIG;
+    const double z = v0 ? v0[j] : 0.0;
+    V.vt[j] = z; V.vc[j] = z; V.vo[j] = z;
+  }
+  if (t == 0) {
+    DevState* S = V.S;
+    S->w_tilde = w0; S->w_check = w0; S->w_out = w0; S->w_z = w0;
+    S->theta = 1.0; S->t = 0; S->done = 0; S->take_hat = 0; S->nonfinite = 0;
+    S->E = INFINITY;
+  }
+}
+
+// z_bar = (1 - theta) z_check + theta z~
+__global__ void aspot_extrap_kernel(AspotVecs V) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const double th = S->theta;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < V.n) V.ub[t] = (1.0 - th) * V.uc[t] + th * V.ut[t];
+  else if (t < V.n + V.m) V.vb[t - V.n] = (1.0 - th) * V.vc[t - V.n] + th * V.vt[t - V.n];
+  if (t == 0) S->w_bar = (1.0 - th) * S->w_check + th * S->w_tilde;
+}
+
+// After the fused pass at z_bar: gradient (r(B)+e^u-r~, c(B)+e^v-c~, |B|-s),
+// step z~' = z_bar - grad/(L theta), coupling z_grave = z_bar + theta (z~' - z~).
+__global__ void aspot_after_grad_kernel(AspotVecs V) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const double th = S->theta, Lth = S->L * th;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[3] = {0, 0, 0};   // tot, sum(e^u - u r~) + sum(e^v - v c~), nonfinite
+  if (t < V.n) {
+    const double ub = V.ub[t];
+    const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);
+    const double rB = safe_exp(R), eu = safe_exp(ub);
+    const double g = rB + eu - V.rt[t];
+    const double un = ub - g / Lth;
+    V.ug[t] = ub + th * (un - V.ut[t]);
+    V.ut[t] = un;
+    v[0] = rB;
+    v[1] = eu - ub * V.rt[t];
+    if (!isfinite(un)) v[2] = 1;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    const double vb = V.vb[j];
+    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+    const double cB = safe_exp(Cc), ev = safe_exp(vb);
+    const double g = cB + ev - V.ct[j];
+    const double vn = vb - g / Lth;
+    V.vg[j] = vb + th * (vn - V.vt[j]);
+    V.vt[j] = vn;
+    v[1] = ev - vb * V.ct[j];
+    if (!isfinite(vn)) v[2] = 1;
+  }
+  double tot[3];
+  if (reduce_last<3>(v, V.red, V.counter, tot) && threadIdx.x == 0) {
+    const double gw = tot[0] - S->s;
+    const double wn = S->w_bar - gw / Lth;
+    S->w_grave = S->w_bar + th * (wn - S->w_tilde);
+    S->w_tilde = wn;
+    if (S->t == 0) S->phi_check = tot[0] + tot[1] - S->w_bar * S->s;   // phi(z_check^0), z_bar^0 = z_check^0
+    if (tot[2] != 0.0 || !isfinite(wn)) S->nonfinite = 1;
+  }
+}
+
+// After the one-sided pass at z_grave: Greenkhorn step (Algorithm 1) for block
+// k, closed-form phi(z^), argmin against phi(z_check).
+__global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0, 0};      // phi parts
+  double xr = 0.0;           // log row sum (w step: log |B|_1 = LSE_i of these)
+  bool act = false;
+  if (t < V.n) {
+    const double ug = V.ug[t];
+    if (k == 0) {
+      const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);
+      const double uh = V.lrt[t] - softplus(R - ug);
+      V.uh[t] = uh;
+      v[0] = -uh * V.rt[t];
+    } else {
+      v[0] = safe_exp(ug) - ug * V.rt[t];
+      if (k == 2) { xr = combine_parts(V.row_part, V.ncolblk, V.n, t); act = true; }
+    }
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    const double vg = V.vg[j];
+    if (k == 1) {
+      const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+      const double vh = V.lct[j] - softplus(Cc - vg);
+      V.vh[j] = vh;
+      v[1] = -vh * V.ct[j];
+    } else {
+      v[1] = safe_exp(vg) - vg * V.ct[j];
+    }
+  }
+  double tot[2], ltot = 0.0;
+  if (reduce_last_lse<2>(v, xr, act, V.red, V.counter, tot, &ltot) && threadIdx.x == 0) {
+    double wh = S->w_grave, base;
+    if (k == 0) base = S->sum_rt;                 // |B|_1 + sum e^u = |r~|_1 after the u step
+    else if (k == 1) base = S->sum_ct;
+    else { wh = S->w_grave + S->log_s - ltot; base = S->s; }   // |B|_1 = s after the w step
+    S->w_hat = wh;
+    const double ph = base + tot[0] + tot[1] - wh * S->s;
+    S->phi_hat = ph;
+    const int take = ph < S->phi_check;
+    S->take_hat = take;
+    S->phi_z = take ? ph : S->phi_check;
+    S->w_z = take ? wh : S->w_check;
+  }
+}
+
+// After the fused pass at z^t: E_t, z_check^{t+1} = Greenkhorn_k(z^t),
+// closed-form phi(z_check^{t+1}), theta update and the stop test.
+__global__ void aspot_after_final_kernel(AspotVecs V, int k) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const int take = S->take_hat;
+  const double* uz_hat = (k == 0) ? V.uh : V.ug;
+  const double* vz_hat = (k == 1) ? V.vh : V.vg;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[4] = {0, 0, 0, 0};   // Eu+Ev, tot, phi parts, nonfinite
+  double xr = 0.0;
+  bool act = false;
+  if (t < V.n) {
+    const double uz = take ? uz_hat[t] : V.uc[t];
+    const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);
+    xr = R;
+    act = true;
+    const double rB = safe_exp(R), eu = safe_exp(uz);
+    v[0] = fabs(rB + eu - V.rt[t]);
+    v[1] = rB;
+    V.uo[t] = uz;
+    const double un = (k == 0) ? V.lrt[t] - softplus(R - uz) : uz;
+    V.uc[t] = un;
+    v[2] = (k == 0) ? -un * V.rt[t] : safe_exp(un) - un * V.rt[t];
+    if (!isfinite(R) && R != POT_NEG_BIG) v[3] = 1;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    const double vz = take ? vz_hat[j] : V.vc[j];
+    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+    const double cB = safe_exp(Cc), ev = safe_exp(vz);
+    v[0] = fabs(cB + ev - V.ct[j]);
+    V.vo[j] = vz;
+    const double vn = (k == 1) ? V.lct[j] - softplus(Cc - vz) : vz;
+    V.vc[j] = vn;
+    v[2] = (k == 1) ? -vn * V.ct[j] : safe_exp(vn) - vn * V.ct[j];
+    if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[3] = 1;
+  }
+  double tot[4], ltot = 0.0;
+  if (reduce_last_lse<4>(v, xr, act, V.red, V.counter, tot, &ltot) && threadIdx.x == 0) {
+    const double s = S->s;
+    const double E = fabs(tot[1] - s) + tot[0];
+    const double wz = S->w_z;
+    S->w_out = wz;
+    double wc = wz, base;
+    if (k == 0) base = S->sum_rt;
+    else if (k == 1) base = S->sum_ct;
+    else { wc = wz + S->log_s - ltot; base = s; }   // log |B|_1 in the log domain (it may underflow)
+    S->w_check = wc;
+    S->phi_check = base + tot[2] - wc * s;
+    S->E = E;
+    S->tot = tot[1];
+    const int it = S->t;
+    if (V.trace) {
+      double* tr = S->trace[it & 4095];
+      tr[0] = E; tr[1] = S->phi_z; tr[2] = S->phi_check; tr[3] = (double)take;
+    }
+    const double th = S->theta;
+    S->theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
+    S->t = it + 1;
+    if (tot[3] != 0.0 || !isfinite(E)) S->nonfinite = 1;
+    if (E <= S->thr || it + 1 >= S->max_iter || S->nonfinite) S->done = 1;
+  }
+}
+
+// ---------------------------------------------------- feasible Sinkhorn ---
+
+__global__ void sink_init_kernel(SinkVecs V, const double* r, const double* c, double eps_s, double s) {
+  // r_ext = (r~, |c~| - s), c_ext = (c~, |r~| - s); sums come from S (raw masses)
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double* re = const_cast<double*>(V.re);
+  double* ce = const_cast<double*>(V.ce);
+  double* lre = const_cast<double*>(V.lre);
+  double* lce = const_cast<double*>(V.lce);
+  DevState* S = V.S;
+  if (t < V.n) {
+    const double x = (1.0 - eps_s / 8.0) * r[t] + eps_s / (8.0 * (double)V.n);
+    re[t] = x; lre[t] = x > 0.0 ? log(x) : POT_NEG_BIG; V.u[t] = 0.0; V.uprev[t] = 0.0;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    const double x = (1.0 - eps_s / 8.0) * c[j] + eps_s / (8.0 * (double)V.m);
+    ce[j] = x; lce[j] = x > 0.0 ? log(x) : POT_NEG_BIG; V.v[j] = 0.0;
+  }
+  if (t == 0) {
+    const double dr = S->sum_ct - s, dc = S->sum_rt - s;
+    re[V.n] = dr; lre[V.n] = dr > 0.0 ? log(dr) : POT_NEG_BIG;
+    ce[V.m] = dc; lce[V.m] = dc > 0.0 ? log(dc) : POT_NEG_BIG;
+    V.u[V.n] = 0.0; V.v[V.m] = 0.0; V.uprev[V.n] = 0.0;
+    S->t = 0; S->done = 0; S->nonfinite = 0; S->E = INFINITY;
+  }
+}
+
+// Row update of the extended kernel (u <- log r_ext - log(B 1 / e^u)) after
+// a row pass; the l1 row residual of the current point is the stop test of
+// the previous iteration (columns are exact right after a column update).
+__global__ void sink_after_rows_kernel(SinkVecs V) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double vd = V.dcol ? V.v[V.m] : POT_NEG_BIG;
+  double v[2] = {0, 0};      // l1 row residual, nonfinite
+  double x = 0.0;
+  bool act = false;
+  if (t < V.n) {
+    const double u = V.u[t];
+    const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);   // includes u_i
+    const double lsum = V.dcol ? logaddexp(R, u + vd) : R;
+    v[0] = fabs(safe_exp(lsum) - V.re[t]);
+    V.uprev[t] = u;
+    V.u[t] = clamp_log(V.lre[t] - (lsum - u));
+    if (!isfinite(R) && R != POT_NEG_BIG) v[1] = 1;
+  } else if (t < V.n + V.m) {
+    x = V.v[t - V.n];       // log-sum-exp of v feeds the dummy row
+    act = true;
+  }
+  double tot[2], lse_v = 0.0;
+  if (reduce_last_lse<2>(v, x, act, V.red, V.counter, tot, &lse_v) && threadIdx.x == 0) {
+    double res = tot[0];
+    if (V.drow) {
+      const double ud = V.u[V.n];
+      const double lsum = V.dcol ? logaddexp(ud + lse_v, ud + vd - S->A_over_g) : ud + lse_v;
+      res += fabs(safe_exp(lsum) - V.re[V.n]);
+      V.uprev[V.n] = ud;
+      V.u[V.n] = clamp_log(V.lre[V.n] - (lsum - ud));
+    }
+    S->E = res;
+    if (tot[1] != 0.0 || !isfinite(res)) { S->nonfinite = 1; S->done = 3; }
+    else if (S->t >= 1 && res <= S->thr) S->done = 2;   // 2: restore u from uprev
+  }
+}
+
+// restore the pre-update row potentials when the stop test fired
+__global__ void sink_restore_kernel(SinkVecs V) {
+  DevState* S = V.S;
+  if (S->done != 2) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= V.n) V.u[t] = V.uprev[t];
+}
+
+__global__ void sink_after_cols_kernel(SinkVecs V) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double ud = V.drow ? V.u[V.n] : POT_NEG_BIG;
+  double x = 0.0;
+  bool act = false;
+  if (t < V.m) {
+    const double vj = V.v[t];
+    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, t);   // includes v_j
+    const double lsum = V.drow ? logaddexp(Cc, vj + ud) : Cc;
+    V.v[t] = clamp_log(V.lce[t] - (lsum - vj));
+  } else if (t < V.m + V.n) {
+    x = V.u[t - V.m];
+    act = true;
+  }
+  double lse_u = 0.0;
+  double none[1] = {0};
+  double nt[1];
+  if (reduce_last_lse<1>(none, x, act, V.red, V.counter, nt, &lse_u) && threadIdx.x == 0) {
+    if (V.dcol) {
+      const double vd = V.v[V.m];
+      const double lsum = V.drow ? logaddexp(vd + lse_u, vd + ud - S->A_over_g) : vd + lse_u;
+      V.v[V.m] = clamp_log(V.lce[V.m] - (lsum - vd));
+    }
+    const int it = S->t + 1;
+    S->t = it;
+    if (V.trace) S->trace[(it - 1) & 4095][0] = S->E;
+    if (it >= S->max_iter) S->done = 1;
+  }
+}
+
+// -------------------------------------------------------------- rounding ---
+
+// R1: a_i = min(1, r_i / r(B)_i); f_i = u_i + w + log a_i
+__global__ void round_r1_kernel(RoundVecs V) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V.n) return;
+  const double R = combine_parts(V.row_part, V.ncolblk, V.n, i);
+  const double lr = V.r[i] > 0.0 ? log(V.r[i]) : POT_NEG_BIG;
+  const double la = fmin(0.0, lr - R);
+  V.f[i] = clamp_log(V.u[i] + V.S->w_out + la);
+}
+
+// R2: b_j = min(1, c_j / c(X')_j); g_j = v_j + log b_j; column masses of X''
+__global__ void round_r2_kernel(RoundVecs V) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0, 0};
+  if (j < V.m) {
+    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+    const double lc = V.c[j] > 0.0 ? log(V.c[j]) : POT_NEG_BIG;
+    const double lb = fmin(0.0, lc - Cc);
+    V.g[j] = clamp_log(V.v[j] + lb);
+    const double cm = safe_exp(Cc + lb);
+    const double qj = fmax(V.c[j] - cm, 0.0);
+    V.q[j] = qj;
+    v[0] = cm;
+    v[1] = qj;
+  }
+  double tot[2];
+  if (reduce_last<2>(v, V.red, V.counter, tot) && threadIdx.x == 0) {
+    V.S->m2 = tot[0];
+    V.S->sum_q = tot[1];
+  }
+}
+
+// R3: m'' >= s: scale to mass s (f += log(s/m'')), no rank-one term
+__global__ void round_r3_kernel(RoundVecs V) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double lk = log(V.S->s / V.S->m2);
+  if (i < V.n) { V.f[i] = clamp_log(V.f[i] + lk); V.p[i] = 0.0; }
+  if (i < V.m) V.q[i] = 0.0;
+  if (i == 0) *V.kappa = 0.0;
+}
+
+// R4: m'' < s: p = r - X'' 1; kappa = (s - m'') / (|p|_1 |q|_1)
+__global__ void round_r4_kernel(RoundVecs V) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0};
+  if (i < V.n) {
+    const double R = combine_parts(V.row_part, V.ncolblk, V.n, i);
+    const double pi = fmax(V.r[i] - safe_exp(R), 0.0);
+    V.p[i] = pi;
+    v[0] = pi;
+  }
+  double tot[1];
+  if (reduce_last<1>(v, V.red, V.counter, tot) && threadIdx.x == 0) {
+    V.S->sum_p = tot[0];
+    const double den = tot[0] * V.S->sum_q;
+    *V.kappa = den > 0.0 ? (V.S->s - V.S->m2) / den : 0.0;
+    V.S->kappa = *V.kappa;
+  }
+}
+
+__global__ void marginals_out_kernel(int64_t n, int64_t m, const float2* row_part, const float2* col_part,
+                                     int64_t ncolblk, int64_t nrowblk, double* lrow, double* lcol, double* red,
+                                     unsigned int* counter, double* tot_out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0};
+  if (t < n) {
+    const double R = combine_parts(row_part, ncolblk, n, t);
+    if (lrow) lrow[t] = R;
+    v[0] = safe_exp(R);
+  } else if (t < n + m) {
+    const double Cc = col_part ? combine_parts(col_part, nrowblk, m, t - n) : 0.0;
+    if (lcol) lcol[t - n] = Cc;
+  }
+  double tot[1];
+  if (reduce_last<1>(v, red, counter, tot) && threadIdx.x == 0 && tot_out) *tot_out = tot[0];
+}
+
+__global__ void dense_plan_kernel(PassDesc P, const double* f, const double* g, const double* p,
+                                  const double* q, const double* kappa, float* X, int64_t ldx) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= P.m || i >= P.n) return;
+  double cost;
+  if (P.kind == COST_DENSE_F32) cost = (double)P.C[i * P.ldc + j];
+  else {
+    double acc = 0.0;
+    for (int t = 0; t < P.d; ++t) {
+      double x, y;
+      if (P.kind == COST_SQEUCLID_BF16) {
+        x = __uint_as_float(((unsigned)reinterpret_cast<const unsigned short*>(P.X)[i * P.ldx + t]) << 16);
+        y = __uint_as_float(((unsigned)reinterpret_cast<const unsigned short*>(P.Y)[j * P.ldy + t]) << 16);
+      } else if (P.kind == COST_SQEUCLID_F16) {
+        x = __half2float(reinterpret_cast<const __half*>(P.X)[i * P.ldx + t]);
+        y = __half2float(reinterpret_cast<const __half*>(P.Y)[j * P.ldy + t]);
+      } else {
+        x = reinterpret_cast<const float*>(P.X)[i * P.ldx + t];
+        y = reinterpret_cast<const float*>(P.Y)[j * P.ldy + t];
+      }
+      acc += (x - y) * (x - y);
+    }
+    cost = acc;
+  }
+  const double lg = f[i] + g[j] - P.gC * cost;
+  X[i * ldx + j] = (float)(safe_exp(lg) + *kappa * p[i] * q[j]);
+}
+
+}  // namespace
+
+void launch_marg_stats(const double* r, const double* c, int64_t n, int64_t m, double* red,
+                       unsigned int* counter, double* out6, cudaStream_t st) {
+  marg_stats_kernel<<<vec_blocks(n + m), kVecThreads, 0, st>>>(r, c, n, m, red, counter, out6);
+}
+void launch_reduce_parts(const double* part, int64_t count, int op_max, double* out, cudaStream_t st) {
+  reduce_parts_kernel<<<1, 1024, 0, st>>>(part, count, op_max, out);
+}
+void launch_aspot_init(const AspotVecs& V, const double* r, const double* c, double eps_s,
+                       const double* u0, const double* v0, double w0, cudaStream_t st) {
+  aspot_init_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, r, c, eps_s, u0, v0, w0);
+}
+void launch_aspot_extrap(const AspotVecs& V, cudaStream_t st) {
+  aspot_extrap_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_aspot_after_grad(const AspotVecs& V, cudaStream_t st) {
+  aspot_after_grad_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st) {
+  aspot_after_greenkhorn_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, k);
+}
+void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st) {
+  aspot_after_final_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, k);
+}
+void launch_sink_init(const SinkVecs& V, const double* r, const double* c, double eps_s, double s,
+                      cudaStream_t st) {
+  sink_init_kernel<<<vec_blocks(V.n + V.m + 1), kVecThreads, 0, st>>>(V, r, c, eps_s, s);
+}
+void launch_sink_after_rows(const SinkVecs& V, cudaStream_t st) {
+  sink_after_rows_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  sink_restore_kernel<<<vec_blocks(V.n + 1), kVecThreads, 0, st>>>(V);
+}
+void launch_sink_after_cols(const SinkVecs& V, cudaStream_t st) {
+  sink_after_cols_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_round_r1(const RoundVecs& V, cudaStream_t st) {
+  round_r1_kernel<<<vec_blocks(V.n), kVecThreads, 0, st>>>(V);
+}
+void launch_round_r2(const RoundVecs& V, cudaStream_t st) {
+  round_r2_kernel<<<vec_blocks(V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_round_r3(const RoundVecs& V, cudaStream_t st) {
+  round_r3_kernel<<<vec_blocks(V.n > V.m ? V.n : V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_round_r4(const RoundVecs& V, cudaStream_t st) {
+  round_r4_kernel<<<vec_blocks(V.n), kVecThreads, 0, st>>>(V);
+}
+void launch_marginals_out(int64_t n, int64_t m, const float2* row_part, const float2* col_part,
+                          int64_t ncolblk, int64_t nrowblk, double* lrow, double* lcol, double* red,
+                          unsigned int* counter, double* tot_out, cudaStream_t st) {
+  marginals_out_kernel<<<vec_blocks(n + m), kVecThreads, 0, st>>>(n, m, row_part, col_part, ncolblk, nrowblk,
+                                                                 lrow, lcol, red, counter, tot_out);
+}
+void launch_dense_plan(const PassDesc& P, const double* f, const double* g, const double* p,
+                       const double* q, const double* kappa, float* X, int64_t ldx, cudaStream_t st) {
+  dim3 grid((unsigned)((P.m + 255) / 256), (unsigned)P.n);
+  dense_plan_kernel<<<grid, 256, 0, st>>>(P, f, g, p, q, kappa, X, ldx);
+}
+
+}  // namespace pot

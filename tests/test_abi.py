@@ -1,0 +1,64 @@
+"""CPU checks of the C-ABI library: it builds, loads and exports exactly the
+entry points that include/aspot.h declares (no compute call: no GPU here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "aspot.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"POT_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2601_17196_gb300 import build as b
+    if not os.path.exists(b.LIB):
+        b.build()
+    return b.LIB
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("aspot_solve", "sinkhorn_pot_solve", "pot_round", "pot_objective", "pot_workspace_size",
+                 "pot_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    public = {s for s in exported if not s.startswith("_")}
+    assert set(_declared()) == public
+
+
+def test_library_loads_through_ctypes(libpath):
+    import paper_2601_17196_gb300 as pkg
+    L = pkg.lib()
+    for name in _declared():
+        assert hasattr(L, name)
+    assert L.pot_last_error() in (b"",)
+
+
+def test_argument_checks_run_before_any_launch(libpath):
+    """Invalid problems are rejected on the host (no GPU needed)."""
+    import ctypes as ct
+    from paper_2601_17196_gb300 import binding as B
+    L = B.lib()
+    p = B._Problem()
+    p.n, p.m, p.kind = 0, 5, 0
+    b = ct.c_size_t(0)
+    assert L.pot_workspace_size(ct.byref(p), None, ct.byref(b)) == 1
+    assert b"n and m" in L.pot_last_error()
+    p.n, p.m, p.kind, p.s = 4, 5, 0, 0.5
+    p.r, p.c, p.C, p.ldc = 8, 8, 8, 3          # ldc < m
+    assert L.pot_workspace_size(ct.byref(p), None, ct.byref(b)) == 1
+    p.ldc = 5
+    assert L.pot_workspace_size(ct.byref(p), None, ct.byref(b)) == 0 and b.value > 0
+    p.kind = 7
+    assert L.pot_workspace_size(ct.byref(p), None, ct.byref(b)) == 1

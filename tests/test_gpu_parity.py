@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances (FP32 passes, FP64 potentials and bookkeeping):
+  * per-pass log-sums: |lse_gpu - lse_fp64| <= 5e-6 + 2e-7 |lse| (relative
+    error of the sums; each logit is rounded once in FP32 after the exact
+    hi/lo potential add, so its error is relative to its own magnitude; then
+    ex2.approx and FP32 partial sums).
+  * fixed-iteration ASPOT: potentials within 2e-5 (1 + |u|) after 60
+    iterations, with the oracle replaying the GPU's argmin decisions.
+  * converged solves: |objective difference| <= 1e-5 relative, final E_t below
+    the threshold, and the GPU plan feasible in FP64 to 1e-6.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2601_17196_gb300 as pkg
+import pot_workloads as W
+from oracle import pot as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(pb, **kw):
+    return pkg.DeviceProblem.from_workload(pb, device="cuda", **kw)
+
+
+def _t(x):
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _plan_fp64(C, plan, gamma, cost_scale):
+    f, g, p, q = _np(plan.f), _np(plan.g), _np(plan.p), _np(plan.q)
+    kap = float(plan.kappa.item())
+    return np.exp(f[:, None] + g[None, :] - cost_scale * C / gamma) + kap * np.outer(p, q)
+
+
+def _check_feasible(X, r, c, s, tol=1e-6):
+    assert (X >= 0).all()
+    assert (X.sum(1) <= r * (1 + tol) + 1e-15).all()
+    assert (X.sum(0) <= c * (1 + tol) + 1e-15).all()
+    assert abs(X.sum() - s) <= tol * s
+
+
+# ------------------------------------------------------------ one pass ---
+
+@pytest.mark.parametrize("n,m", [(300, 457), (1, 1), (7, 300), (513, 129)])
+def test_marginals_dense(n, m):
+    pb = W.small_dense(1, n=n, m=m)
+    C = pb.C.astype(np.float64)
+    rng = np.random.default_rng(n + m)
+    gam = 0.02
+    for lo, hi in ((-5.0, 5.0), (-400.0, 300.0)):
+        u, v, w = rng.uniform(lo, hi, n), rng.uniform(lo, hi, m), float(rng.uniform(lo, hi))
+        dp = _dev(pb)
+        lr, lc, tot = pkg.pot_marginals(dp, gam, _t(u), _t(v), w)
+        L = O.log_gibbs(C, gam, u, v, w)
+        er, ec = O.logsumexp(L, axis=1), O.logsumexp(L, axis=0)
+        assert np.all(np.abs(_np(lr) - er) <= 5e-6 + 2e-7 * np.abs(er))
+        assert np.all(np.abs(_np(lc) - ec) <= 5e-6 + 2e-7 * np.abs(ec))
+        ltot = O.logsumexp(L)
+        if ltot < 700:
+            assert tot == pytest.approx(np.exp(ltot), rel=5e-6)
+
+
+@pytest.mark.parametrize("kind,d", [(pkg.COST_SQEUCLID_F32, 3), (pkg.COST_SQEUCLID_F32, 2),
+                                    (pkg.COST_SQEUCLID_BF16, 128), (pkg.COST_SQEUCLID_BF16, 64)])
+def test_marginals_sqeuclid(kind, d):
+    n, m = 385, 521
+    if kind == pkg.COST_SQEUCLID_BF16:
+        pb = W.cloud_32k(2, n=n, m=m, d=d)
+    else:
+        rng = np.random.default_rng(d)
+        pb = W.Problem("pts", np.full(n, 1.0 / n), np.full(m, 1.3 / m), 0.8, 0.05, 1e-3,
+                       X=rng.uniform(0, 1, (n, d)).astype(np.float32).astype(np.float64),
+                       Y=rng.uniform(0, 1, (m, d)).astype(np.float32).astype(np.float64))
+    Dm = O.sqeuclid_cost(pb.X, pb.Y, 1.0)
+    scale = 1.0 / Dm.max()
+    pb.cost_scale = scale
+    C = Dm * scale
+    dp = _dev(pb, kind=kind)
+    rng = np.random.default_rng(7)
+    gam = 0.02
+    u, v, w = rng.uniform(-30, 5, n), rng.uniform(-30, 5, m), 3.0
+    lr, lc, tot = pkg.pot_marginals(dp, gam, _t(u), _t(v), w)
+    L = O.log_gibbs(C, gam, u, v, w)
+    np.testing.assert_allclose(_np(lr), O.logsumexp(L, axis=1), rtol=0, atol=2e-5)
+    np.testing.assert_allclose(_np(lc), O.logsumexp(L, axis=0), rtol=0, atol=2e-5)
+    assert pkg.pot_cost_max(dp) == pytest.approx(Dm.max(), rel=2e-6)
+
+
+# ----------------------------------------------------------- solvers ---
+
+def test_aspot_fixed_iterations_match_oracle():
+    pb = W.small_dense(3, n=200, m=233)
+    C = pb.C.astype(np.float64)
+    K = 60
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_TRACE,
+                          check_every=9)
+    assert res.iters == K
+    took = res.trace[:, 3] > 0.5
+    ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, forced_hat=took,
+                  record=True)
+    free = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, record=True)
+    # decisions the FP64 run would take differently must be near-ties
+    for t in range(K):
+        if free.trace.took_hat[t] != took[t]:
+            assert abs(free.trace.phi_hat[t] - free.trace.phi_check_next[max(t - 1, 0)]) < 1e-6
+    u, v, w = _np(res.plan.u), _np(res.plan.v), float(res.plan.w.item())
+    np.testing.assert_allclose(u, ora.z.u, rtol=0, atol=2e-5 * (1 + np.abs(ora.z.u).max()))
+    np.testing.assert_allclose(v, ora.z.v, rtol=0, atol=2e-5 * (1 + np.abs(ora.z.v).max()))
+    assert w == pytest.approx(ora.z.w, abs=2e-5 * (1 + abs(ora.z.w)))
+    np.testing.assert_allclose(res.trace[:, 0], ora.trace.E, rtol=1e-3, atol=1e-7)
+
+
+@pytest.mark.parametrize("solver", ["aspot", "sinkhorn"])
+def test_converged_small_dense(solver):
+    """The 256-point workload (Section 4.1 stand-in) to the stop threshold."""
+    pb = W.small_dense(0)
+    C = pb.C.astype(np.float64)
+    if solver == "aspot":
+        res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=5000)
+        ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=5000)
+    else:
+        res = pkg.sinkhorn_pot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=5000)
+        ora = O.solve_sinkhorn(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=5000)
+    assert res.status == 0
+    assert res.err_final <= res.eps_stop
+    assert abs(res.objective - ora.objective) <= 1e-5 * abs(ora.objective)
+    X = _plan_fp64(C, res.plan, res.gamma, res.cost_scale)
+    _check_feasible(X, pb.r, pb.c, pb.s)
+    assert O.objective(C, X) == pytest.approx(res.objective, rel=1e-6)
+    # the returned duals reach the threshold in FP64 as well
+    if solver == "aspot":
+        st = O.approx_setup(pb.r, pb.c, pb.s, pb.eps, 1.0, pb.gamma)
+        z = O.Dual(_np(res.plan.u), _np(res.plan.v), float(res.plan.w.item()))
+        E = O.feas_error(C, pb.gamma, st.r_t, st.c_t, pb.s, z)
+        assert E == pytest.approx(res.err_final, rel=1e-3, abs=1e-9)
+
+
+def test_pot_round_matches_oracle_reading():
+    pb = W.small_dense(4, n=150, m=170)
+    C = pb.C.astype(np.float64)
+    ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=40, no_stop=True)
+    for shift in (0.0, 2.0, -3.0):          # move w to exercise both branches (R3 and R4)
+        z = ora.z
+        dp = _dev(pb)
+        plan, branch = pkg.pot_round(dp, pb.gamma, _t(z.u), _t(z.v), z.w + shift)
+        Xo = O.round_pot(O.primal_plan(C, pb.gamma, O.Dual(z.u, z.v, z.w + shift)), pb.r, pb.c, pb.s)
+        X = _plan_fp64(C, plan, pb.gamma, 1.0)
+        np.testing.assert_allclose(X, Xo, rtol=0, atol=1e-5 * Xo.max())
+        _check_feasible(X, pb.r, pb.c, pb.s)
+        Xd = _np(pkg.pot_plan_dense(dp, plan, pb.gamma)).astype(np.float64)
+        np.testing.assert_allclose(Xd, X, rtol=1e-5, atol=1e-7 * X.max())
+        m2 = (O.primal_plan(C, pb.gamma, O.Dual(z.u, z.v, z.w + shift))).sum()
+        assert branch in (3, 4)
+        obj = pkg.pot_objective(dp, plan, pb.gamma)
+        assert obj == pytest.approx(O.objective(C, Xo), rel=1e-5)
+
+
+def test_invalid_arguments_are_rejected():
+    pb = W.small_dense(0, n=32, m=40)
+    dp = _dev(pb)
+    bad = pkg.DeviceProblem(dp.kind, dp.r, dp.c, 5.0, C=dp.C, cost_scale=1.0)   # s > min mass
+    with pytest.raises(pkg.PotError) as e:
+        pkg.aspot_solve(bad, 0.05, 1e-3)
+    assert e.value.status == 1
+    with pytest.raises(pkg.PotError) as e:
+        pkg.aspot_solve(dp, 0.05, 1e-3, ws=torch.empty(1024, dtype=torch.uint8, device="cuda"))
+    assert e.value.status in (1, 2)
+    nanr = dp.r.clone()
+    nanr[3] = float("nan")
+    with pytest.raises(pkg.PotError):
+        pkg.aspot_solve(pkg.DeviceProblem(dp.kind, nanr, dp.c, 0.5, C=dp.C, cost_scale=1.0), 0.05, 1e-3)
+
+
+def test_max_iter_reports_noconv_with_feasible_plan():
+    pb = W.small_dense(0)
+    C = pb.C.astype(np.float64)
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=5)
+    assert res.status == 4 and res.iters == 5
+    _check_feasible(_plan_fp64(C, res.plan, res.gamma, res.cost_scale), pb.r, pb.c, pb.s)
+
+
+@pytest.mark.parametrize("gamma", [0.1, 0.03, 0.01])
+def test_dense_4096_full_size_properties(gamma):
+    """n = m = 4096, 64-D, FP32 cost: the GPU solve is checked in FP64 at its
+    own duals (E_t below the threshold, objective and feasibility of the
+    rounded plan); the oracle's full solve at this size is too slow for a test."""
+    pb = W.dense_4096(0, gamma=gamma)
+    C = pb.C.astype(np.float64)
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=20000)
+    assert res.status == 0
+    st = O.approx_setup(pb.r, pb.c, pb.s, pb.eps, 1.0, pb.gamma)
+    z = O.Dual(_np(res.plan.u), _np(res.plan.v), float(res.plan.w.item()))
+    E = O.feas_error(C, pb.gamma, st.r_t, st.c_t, pb.s, z)
+    assert E <= res.eps_stop * 1.001
+    X = _plan_fp64(C, res.plan, res.gamma, res.cost_scale)
+    _check_feasible(X, pb.r, pb.c, pb.s)
+    assert O.objective(C, X) == pytest.approx(res.objective, rel=1e-5)

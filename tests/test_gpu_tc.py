@@ -1,0 +1,82 @@
+"""GPU parity of the tcgen05 on-the-fly squared-Euclidean path (BF16 points,
+d a multiple of 64) against the FP64 oracle, and against the CUDA-core path.
+
+Tolerances: the dot products come from BF16 x BF16 products accumulated in
+FP32 by the tensor cores; the normalised cost then carries an absolute error
+of about 1e-7 and the logit (cost / gamma, gamma = 0.02) about 1e-5 / ln 2 in
+the worst case, so per-pass log-sums are checked to 3e-5, solver potentials to
+2e-4 (1 + |u|) and objectives to 1e-5 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2601_17196_gb300 as pkg
+import pot_workloads as W
+from oracle import pot as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(x):
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _cloud(seed, n, m, d=128):
+    pb = W.cloud_32k(seed, n=n, m=m, d=d)
+    Dm = O.sqeuclid_cost(pb.X, pb.Y, 1.0)
+    pb.cost_scale = 1.0 / Dm.max()
+    return pb, Dm
+
+
+@pytest.mark.parametrize("n,m,d", [(128, 128, 128), (385, 521, 128), (1000, 1301, 64), (77, 900, 256), (1, 3, 128)])
+def test_tc_marginals_match_oracle(n, m, d):
+    pb, Dm = _cloud(n + m, n, m, d)
+    C = Dm * pb.cost_scale
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    rng = np.random.default_rng(1)
+    gam = 0.02
+    for spread in (5.0, 60.0):
+        u, v, w = rng.uniform(-spread, 1, n), rng.uniform(-spread, 1, m), 2.0
+        lr, lc, tot = pkg.pot_marginals(dp, gam, _t(u), _t(v), w)
+        L = O.log_gibbs(C, gam, u, v, w)
+        er, ec = O.logsumexp(L, axis=1), O.logsumexp(L, axis=0)
+        assert np.abs(_np(lr) - er).max() <= 3e-5 + 2e-7 * np.abs(er).max()
+        assert np.abs(_np(lc) - ec).max() <= 3e-5 + 2e-7 * np.abs(ec).max()
+    assert pkg.pot_cost_max(dp) == pytest.approx(Dm.max(), rel=1e-5)
+
+
+def test_tc_round_and_objective_match_oracle():
+    pb, Dm = _cloud(5, 300, 420)
+    C = Dm * pb.cost_scale
+    ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=30, no_stop=True)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    plan, branch = pkg.pot_round(dp, pb.gamma, _t(ora.z.u), _t(ora.z.v), ora.z.w)
+    Xo = O.round_pot(O.primal_plan(C, pb.gamma, ora.z), pb.r, pb.c, pb.s)
+    f, g, p, q = _np(plan.f), _np(plan.g), _np(plan.p), _np(plan.q)
+    X = np.exp(f[:, None] + g[None, :] - C / pb.gamma) + float(plan.kappa.item()) * np.outer(p, q)
+    np.testing.assert_allclose(X, Xo, rtol=0, atol=2e-4 * Xo.max())
+    obj = pkg.pot_objective(dp, plan, pb.gamma)
+    assert obj == pytest.approx(O.objective(C, Xo), rel=1e-4)
+    assert obj == pytest.approx(O.objective(C, X), rel=1e-5)
+
+
+def test_tc_fixed_iterations_match_oracle_and_simt():
+    pb, Dm = _cloud(7, 256, 320)
+    C = Dm * pb.cost_scale
+    K = 30
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    flags = pkg.FLAG_NO_STOP | pkg.FLAG_TRACE
+    tc = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=K, flags=flags, check_every=6)
+    si = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=K, flags=flags | pkg.FLAG_FORCE_SIMT, check_every=6)
+    took = tc.trace[:, 3] > 0.5
+    ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, forced_hat=took)
+    for res in (tc, si):
+        u, v = _np(res.plan.u), _np(res.plan.v)
+        np.testing.assert_allclose(u, ora.z.u, rtol=0, atol=2e-4 * (1 + np.abs(ora.z.u).max()))
+        np.testing.assert_allclose(v, ora.z.v, rtol=0, atol=2e-4 * (1 + np.abs(ora.z.v).max()))
+    assert tc.objective == pytest.approx(si.objective, rel=1e-5)
