@@ -66,6 +66,7 @@ typedef enum {
 #define POT_FLAG_TRACE 4          /* record E_t, phi(z^t), phi(z_check^{t+1}), argmin per iteration */
 #define POT_FLAG_NO_STOP 8        /* run exactly max_iter iterations (fixed-iteration mode) */
 #define POT_FLAG_FORCE_SIMT 16    /* use the CUDA-core pass even where the tcgen05 pass applies */
+#define POT_FLAG_PROFILE 32       /* time every main-loop pass with CUDA events (res->pass_ms, pass_launches) */
 
 typedef struct {
   int64_t n, m;
@@ -114,6 +115,9 @@ typedef struct {            /* host struct filled by the solvers */
   double ms;                /* device time of the whole call (CUDA events) */
   int32_t rounding_branch;  /* 3: uniform scale to s, 4: rank-one fill */
   int32_t nonfinite;
+  double pass_ms;           /* POT_FLAG_PROFILE: summed CUDA-event time of the main-loop passes */
+  int64_t pass_launches;    /* POT_FLAG_PROFILE: number of passes timed */
+  int64_t kernel_launches;  /* kernels this call launched (all of them this library's own) */
 } pot_result;
 
 /* Bytes of device workspace the solvers / pot_round / pot_objective /

@@ -26,6 +26,7 @@ from .binding import (  # noqa: F401
     FLAG_TRACE,
     FLAG_NO_STOP,
     FLAG_FORCE_SIMT,
+    FLAG_PROFILE,
     COST_DENSE_F32,
     COST_SQEUCLID_BF16,
     COST_SQEUCLID_F16,

@@ -21,6 +21,7 @@ FLAG_NO_SMOOTH = 2
 FLAG_TRACE = 4
 FLAG_NO_STOP = 8
 FLAG_FORCE_SIMT = 16
+FLAG_PROFILE = 32
 
 COST_DENSE_F32 = 0
 COST_SQEUCLID_BF16 = 1
@@ -61,7 +62,8 @@ class _Result(ct.Structure):
     _fields_ = [("status", ct.c_int32), ("iters", ct.c_int32), ("objective", ct.c_double),
                 ("err_final", ct.c_double), ("eps_stop", ct.c_double), ("gamma", ct.c_double),
                 ("cost_scale", ct.c_double), ("mass", ct.c_double), ("ms", ct.c_double),
-                ("rounding_branch", ct.c_int32), ("nonfinite", ct.c_int32)]
+                ("rounding_branch", ct.c_int32), ("nonfinite", ct.c_int32),
+                ("pass_ms", ct.c_double), ("pass_launches", ct.c_int64), ("kernel_launches", ct.c_int64)]
 
 
 _lib_handle = None
@@ -205,6 +207,9 @@ class SolveResult:
     nonfinite: int
     plan: Plan
     trace: Optional[np.ndarray] = None
+    pass_ms: float = 0.0
+    pass_launches: int = 0
+    kernel_launches: int = 0
 
 
 _side_streams = {}
@@ -293,7 +298,8 @@ def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w
         trace = buf[:k]
     _finish(side, cur)
     return SolveResult(st, res.iters, res.objective, res.err_final, res.eps_stop, res.gamma, res.cost_scale,
-                       res.mass, res.ms, res.rounding_branch, res.nonfinite, plan, trace)
+                       res.mass, res.ms, res.rounding_branch, res.nonfinite, plan, trace,
+                       res.pass_ms, res.pass_launches, res.kernel_launches)
 
 
 def aspot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,

@@ -125,6 +125,15 @@ struct Ctx {
   double cost_scale = 1.0;
   double max_raw = 0.0;
   double sum_r = 0, sum_c = 0, min_r = 0, min_c = 0;
+  // kernel launch count and optional CUDA-event timing of the main-loop passes
+  int64_t launches = 0;
+  bool prof = false;
+  bool in_loop = false;
+  int pass_ord = 0;
+  std::vector<cudaEvent_t> ev;      // pairs (start, end) per pass ordinal of one graph
+  double pass_ms = 0.0;
+  int64_t pass_count = 0;
+  ~Ctx() { for (cudaEvent_t e : ev) cudaEventDestroy(e); }
 };
 
 pot_status check_problem(const pot_problem* P) {
@@ -201,17 +210,33 @@ PassDesc base_desc(const Ctx& X, double gamma) {
   return d;
 }
 
-pot_status run_pass(const Ctx& X, const PassDesc& d) {
-  if (X.L.use_tc) {
-    CK(launch_pass_tc(d, X.L.tl, X.st));
-  } else {
-    launch_pass_simt(d, X.L.sl, X.st);
+pot_status run_pass(Ctx& X, const PassDesc& d) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (X.prof && X.in_loop) {
+    const size_t need = 2 * (size_t)(X.pass_ord + 1);
+    while (X.ev.size() < need) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      X.ev.push_back(e);
+    }
+    e0 = X.ev[2 * X.pass_ord];
+    e1 = X.ev[2 * X.pass_ord + 1];
+    X.pass_ord++;
   }
+  if (X.L.use_tc) {
+    CK(launch_pass_tc(d, X.L.tl, X.st, e0));
+    X.launches += 2;
+  } else {
+    if (e0) CK(cudaEventRecord(e0, X.st));
+    launch_pass_simt(d, X.L.sl, X.st);
+    X.launches += 1;
+  }
+  if (e1) CK(cudaEventRecord(e1, X.st));
   CKL();
   return POT_OK;
 }
 
-int64_t pass_ctas(const Ctx& X) {
+int64_t pass_ctas(const Ctx& X) {  // one partial per CTA of a pass
   return X.L.use_tc ? X.L.tl.ncolblk * X.L.tl.nrowblk : X.L.sl.ncolblk * X.L.sl.nrowblk;
 }
 
@@ -219,11 +244,12 @@ int64_t pass_ctas(const Ctx& X) {
 pot_status prologue(Ctx& X, bool need_max) {
   const pot_problem* P = X.P;
   CK(cudaMemsetAsync(X.cnt, 0, sizeof(unsigned int) * 8, X.st));
-  launch_marg_stats(P->r, P->c, P->n, P->m, X.red, X.cnt, X.stats, X.st);
+  launch_marg_stats(P->r, P->c, P->n, P->m, X.red, X.cnt, X.stats, X.st); X.launches += 1;
   CKL();
   if (P->kind != POT_COST_DENSE_F32) {
     launch_sqnorm(P->kind, P->X, P->n, P->d, P->ldx, X.xn, X.st);
     launch_sqnorm(P->kind, P->Y, P->m, P->d, P->ldy, X.yn, X.st);
+    X.launches += 2;
     CKL();
   }
   if (need_max) {
@@ -231,7 +257,7 @@ pot_status prologue(Ctx& X, bool need_max) {
     d.mode = PASS_MAXCOST;
     pot_status s = run_pass(X, d);
     if (s != POT_OK) return s;
-    launch_reduce_parts(X.red, pass_ctas(X), 1, X.stats + 6, X.st);
+    launch_reduce_parts(X.red, pass_ctas(X), 1, X.stats + 6, X.st); X.launches += 1;
     CKL();
   }
   double h[8];
@@ -289,7 +315,7 @@ pot_status read_state(Ctx& X, DevState& h) {
 // device stop flag is set.  With a capturable stream the iterations are
 // captured into a CUDA graph of `per` iterations.
 template <class Body>
-pot_status drive(Ctx& X, int per, int max_iter, Body body) {
+pot_status drive(Ctx& X, int per, int max_iter, int passes_per_iter, Body body) {
   cudaStreamCaptureStatus cs;
   CK(cudaStreamIsCapturing(X.st, &cs));
   if (cs != cudaStreamCaptureStatusNone) return fail(POT_EINVAL, "the stream is being captured");
@@ -298,10 +324,16 @@ pot_status drive(Ctx& X, int per, int max_iter, Body body) {
   int done = 0, launched = 0;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
+  int64_t per_graph_launches = 0;
+  X.in_loop = true;
   if (graphs) {
+    const int64_t l0 = X.launches;
+    X.pass_ord = 0;
     CK(cudaStreamBeginCapture(X.st, cudaStreamCaptureModeThreadLocal));
     pot_status s = POT_OK;
     for (int it = 0; it < per && s == POT_OK; ++it) s = body(it % 3);
+    per_graph_launches = X.launches - l0;
+    X.launches = l0;
     cudaGraph_t g2 = nullptr;
     cudaError_t e = cudaStreamEndCapture(X.st, &g2);
     if (s != POT_OK) { if (g2) cudaGraphDestroy(g2); return s; }
@@ -311,21 +343,36 @@ pot_status drive(Ctx& X, int per, int max_iter, Body body) {
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return fail(POT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
   }
   pot_status st = POT_OK;
-  int* hflag = &done;
+  int flags3[3] = {0, 0, 0};         // DevState t, take_hat, done (adjacent ints)
+  int t_prev = 0;
   while (launched < max_iter + per) {
     if (graphs) {
       cudaError_t e = cudaGraphLaunch(exec, X.st);
       if (e != cudaSuccess) { st = fail(POT_ECUDA, "graph launch: %s", cudaGetErrorString(e)); break; }
+      X.launches += per_graph_launches;
     } else {
+      X.pass_ord = 0;
       for (int it = 0; it < per && st == POT_OK; ++it) st = body(it % 3);
       if (st != POT_OK) break;
     }
     launched += per;
-    cudaError_t e = cudaMemcpyAsync(hflag, &X.S->done, sizeof(int), cudaMemcpyDeviceToHost, X.st);
+    cudaError_t e = cudaMemcpyAsync(flags3, &X.S->t, sizeof(flags3), cudaMemcpyDeviceToHost, X.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(X.st);
     if (e != cudaSuccess) { st = fail(POT_ECUDA, "stop flag: %s", cudaGetErrorString(e)); break; }
+    if (X.prof) {
+      // passes of the iterations that ran in this launch (later ones returned at once)
+      const int ran = std::min(flags3[0] - t_prev, per);
+      const int npass = std::min<int>(ran * passes_per_iter, (int)X.ev.size() / 2);
+      for (int k = 0; k < npass; ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, X.ev[2 * k], X.ev[2 * k + 1]) == cudaSuccess) { X.pass_ms += ms; X.pass_count++; }
+      }
+    }
+    t_prev = flags3[0];
+    done = flags3[2];
     if (done) break;
   }
+  X.in_loop = false;
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (st == POT_OK && !done) st = fail(POT_ETIMEOUT, "device stop flag never set");
@@ -345,23 +392,23 @@ pot_status do_round(Ctx& X, double gamma, const double* u, const double* v, pot_
   d.mode = PASS_ROWS; d.arow0 = u; d.bcol0 = v; d.aoff0 = &X.S->w_out;
   pot_status s = run_pass(X, d);
   if (s != POT_OK) return s;
-  launch_round_r1(R, X.st);
+  launch_round_r1(R, X.st); X.launches += 1;
   CKL();
   // R2: columns of diag(a) B
   d.mode = PASS_COLS; d.arow0 = plan->f; d.bcol0 = v; d.aoff0 = nullptr;
   if ((s = run_pass(X, d)) != POT_OK) return s;
-  launch_round_r2(R, X.st);
+  launch_round_r2(R, X.st); X.launches += 1;
   CKL();
   DevState h;
   if ((s = read_state(X, h)) != POT_OK) return s;
   if (h.m2 >= P->s) {
-    launch_round_r3(R, X.st);
+    launch_round_r3(R, X.st); X.launches += 1;
     CKL();
     if (branch) *branch = 3;
   } else {
     d.mode = PASS_ROWS; d.arow0 = plan->f; d.bcol0 = plan->g; d.aoff0 = nullptr;
     if ((s = run_pass(X, d)) != POT_OK) return s;
-    launch_round_r4(R, X.st);
+    launch_round_r4(R, X.st); X.launches += 1;
     CKL();
     if (branch) *branch = 4;
   }
@@ -374,7 +421,7 @@ pot_status do_objective(Ctx& X, double gamma, const pot_plan* plan, double* out)
   d.p = plan->p; d.q = plan->q; d.kappa = plan->kappa;
   pot_status s = run_pass(X, d);
   if (s != POT_OK) return s;
-  launch_reduce_parts(X.red, pass_ctas(X), 0, X.stats + 7, X.st);
+  launch_reduce_parts(X.red, pass_ctas(X), 0, X.stats + 7, X.st); X.launches += 1;
   CKL();
   double h;
   CK(cudaMemcpyAsync(&h, X.stats + 7, sizeof(double), cudaMemcpyDeviceToHost, X.st));
@@ -430,6 +477,7 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   memset(res, 0, sizeof(*res));
   Ctx X;
   if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
+  X.prof = (params->flags & POT_FLAG_PROFILE) != 0;
   Timer tm(X.st);
   if ((s = prologue(X, true)) != POT_OK) return s;
   const SetupOut so = approx_setup(X, params);
@@ -447,36 +495,36 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   V.ug = X.U[5]; V.vg = X.V[5]; V.uh = X.U[6]; V.vh = X.V[6]; V.uo = plan->u; V.vo = plan->v;
   V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
   V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
-  launch_aspot_init(V, prob->r, prob->c, so.eps_s, params->u0, params->v0, params->w0, X.st);
+  launch_aspot_init(V, prob->r, prob->c, so.eps_s, params->u0, params->v0, params->w0, X.st); X.launches += 1;
   CKL();
 
   const double gamma = so.gamma;
   PassDesc d = base_desc(X, gamma);
   auto body = [&](int k) -> pot_status {
     pot_status q;
-    launch_aspot_extrap(V, X.st);
+    launch_aspot_extrap(V, X.st); X.launches += 1;
     PassDesc p1 = d;                       // gradient pass at z_bar (both sides)
     p1.mode = PASS_ROWS | PASS_COLS; p1.arow0 = V.ub; p1.bcol0 = V.vb; p1.aoff0 = &X.S->w_bar; p1.done = &X.S->done;
     if ((q = run_pass(X, p1)) != POT_OK) return q;
-    launch_aspot_after_grad(V, X.st);
+    launch_aspot_after_grad(V, X.st); X.launches += 1;
     PassDesc p2 = d;                       // Greenkhorn pass at z_grave (one side)
     p2.mode = (k == 1) ? PASS_COLS : PASS_ROWS; p2.arow0 = V.ug; p2.bcol0 = V.vg; p2.aoff0 = &X.S->w_grave;
     p2.done = &X.S->done;
     if ((q = run_pass(X, p2)) != POT_OK) return q;
-    launch_aspot_after_greenkhorn(V, k, X.st);
+    launch_aspot_after_greenkhorn(V, k, X.st); X.launches += 1;
     PassDesc p3 = d;                       // pass at z^t = argmin (both sides)
     p3.mode = PASS_ROWS | PASS_COLS;
     p3.arow0 = V.uc; p3.bcol0 = V.vc; p3.aoff0 = &X.S->w_check;
     p3.arow1 = (k == 0) ? V.uh : V.ug; p3.bcol1 = (k == 1) ? V.vh : V.vg; p3.aoff1 = &X.S->w_hat;
     p3.sel = &X.S->take_hat; p3.done = &X.S->done;
     if ((q = run_pass(X, p3)) != POT_OK) return q;
-    launch_aspot_after_final(V, k, X.st);
+    launch_aspot_after_final(V, k, X.st); X.launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
     return POT_OK;
   };
   const int per = params->check_every > 0 ? params->check_every : 24;
-  if ((s = drive(X, per, params->max_iter, body)) != POT_OK) return s;
+  if ((s = drive(X, per, params->max_iter, 3, body)) != POT_OK) return s;
   if ((s = read_state(X, h)) != POT_OK) return s;
   CK(cudaMemcpyAsync(plan->w, &X.S->w_out, sizeof(double), cudaMemcpyDeviceToDevice, X.st));
   res->iters = h.t;
@@ -491,6 +539,9 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   if ((s = do_objective(X, gamma, plan, &res->objective)) != POT_OK) return s;
   res->mass = prob->s;
   res->ms = tm.stop();
+  res->pass_ms = X.pass_ms;
+  res->pass_launches = X.pass_count;
+  res->kernel_launches = X.launches;
   if (h.nonfinite) { res->status = POT_ENONFINITE; return fail(POT_ENONFINITE, "non-finite potentials or sums"); }
   const bool conv = h.E <= h.thr;
   res->status = (conv || (params->flags & POT_FLAG_NO_STOP)) ? POT_OK : POT_ENOCONV;
@@ -509,6 +560,7 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
   memset(res, 0, sizeof(*res));
   Ctx X;
   if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
+  X.prof = (params->flags & POT_FLAG_PROFILE) != 0;
   Timer tm(X.st);
   if ((s = prologue(X, true)) != POT_OK) return s;
   SetupOut so = approx_setup(X, params);
@@ -542,7 +594,7 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
   V.u = X.U[2]; V.v = X.V[2]; V.uprev = X.U[3];
   V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
   V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
-  launch_sink_init(V, prob->r, prob->c, so.eps_s, prob->s, X.st);
+  launch_sink_init(V, prob->r, prob->c, so.eps_s, prob->s, X.st); X.launches += 1;
   CKL();
   PassDesc d = base_desc(X, gamma);
   auto body = [&](int) -> pot_status {
@@ -550,17 +602,17 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
     PassDesc pr = d;
     pr.mode = PASS_ROWS; pr.arow0 = V.u; pr.bcol0 = V.v; pr.aoff0 = nullptr; pr.done = &X.S->done;
     if ((q = run_pass(X, pr)) != POT_OK) return q;
-    launch_sink_after_rows(V, X.st);
+    launch_sink_after_rows(V, X.st); X.launches += 2;
     PassDesc pc = d;
     pc.mode = PASS_COLS; pc.arow0 = V.u; pc.bcol0 = V.v; pc.aoff0 = nullptr; pc.done = &X.S->done;
     if ((q = run_pass(X, pc)) != POT_OK) return q;
-    launch_sink_after_cols(V, X.st);
+    launch_sink_after_cols(V, X.st); X.launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
     return POT_OK;
   };
   const int per = params->check_every > 0 ? params->check_every : 24;
-  if ((s = drive(X, per, params->max_iter, body)) != POT_OK) return s;
+  if ((s = drive(X, per, params->max_iter, 2, body)) != POT_OK) return s;
   if ((s = read_state(X, h)) != POT_OK) return s;
   // final duals: the first n / m extended potentials, w = 0
   CK(cudaMemcpyAsync(plan->u, V.u, sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));
@@ -579,6 +631,9 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
   if ((s = do_objective(X, gamma, plan, &res->objective)) != POT_OK) return s;
   res->mass = prob->s;
   res->ms = tm.stop();
+  res->pass_ms = X.pass_ms;
+  res->pass_launches = X.pass_count;
+  res->kernel_launches = X.launches;
   if (h.nonfinite || h.done == 3) { res->status = POT_ENONFINITE; return fail(POT_ENONFINITE, "non-finite potentials or sums"); }
   const bool conv = h.done == 2;
   res->status = (conv || (params->flags & POT_FLAG_NO_STOP)) ? POT_OK : POT_ENOCONV;

@@ -18,7 +18,7 @@ void launch_sqnorm(int kind, const void* X, int64_t n, int d, int64_t ldx, float
 struct TcLayout { int64_t ncolblk, nrowblk, nchunks, tiles_per_chunk, n_pad, m_pad; int ok; };
 TcLayout tc_layout(int64_t n, int64_t m, int d);
 bool tc_supported(const PassDesc& P);
-cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st);
+cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st, cudaEvent_t before_main = nullptr);
 
 // --------------------------------------------------------- device state --
 struct DevState {
