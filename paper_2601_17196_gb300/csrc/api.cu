@@ -223,15 +223,16 @@ pot_status run_pass(Ctx& X, const PassDesc& d) {
     e1 = X.ev[2 * X.pass_ord + 1];
     X.pass_ord++;
   }
+  // events inside a captured graph must be external event-record nodes
   if (X.L.use_tc) {
     CK(launch_pass_tc(d, X.L.tl, X.st, e0));
     X.launches += 2;
   } else {
-    if (e0) CK(cudaEventRecord(e0, X.st));
+    if (e0) CK(cudaEventRecordWithFlags(e0, X.st, cudaEventRecordExternal));
     launch_pass_simt(d, X.L.sl, X.st);
     X.launches += 1;
   }
-  if (e1) CK(cudaEventRecord(e1, X.st));
+  if (e1) CK(cudaEventRecordWithFlags(e1, X.st, cudaEventRecordExternal));
   CKL();
   return POT_OK;
 }

@@ -567,7 +567,7 @@ cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st
   tc_prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, L.n_pad, L.m_pad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (before_main && (e = cudaEventRecord(before_main, st)) != cudaSuccess) return e;
+  if (before_main && (e = cudaEventRecordWithFlags(before_main, st, cudaEventRecordExternal)) != cudaSuccess) return e;
   CUtensorMap mx, my;
   if (!make_map(&mx, P.X, P.n, P.d, P.ldx) || !make_map(&my, P.Y, P.m, P.d, P.ldy)) return cudaErrorInvalidValue;
   const int md = P.mode;

@@ -80,3 +80,15 @@ def test_tc_fixed_iterations_match_oracle_and_simt():
         np.testing.assert_allclose(u, ora.z.u, rtol=0, atol=2e-4 * (1 + np.abs(ora.z.u).max()))
         np.testing.assert_allclose(v, ora.z.v, rtol=0, atol=2e-4 * (1 + np.abs(ora.z.v).max()))
     assert tc.objective == pytest.approx(si.objective, rel=1e-5)
+
+
+def test_profiled_solve_times_every_pass():
+    """POT_FLAG_PROFILE: every main-loop pass timed, results unchanged."""
+    pb, Dm = _cloud(11, 200, 260)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    a = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=40, flags=pkg.FLAG_NO_STOP | pkg.FLAG_PROFILE, check_every=9)
+    b = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=40, flags=pkg.FLAG_NO_STOP, check_every=9)
+    assert a.pass_launches == 3 * 40 and a.pass_ms > 0
+    assert a.kernel_launches >= 40 * 10
+    np.testing.assert_array_equal(_np(a.plan.u), _np(b.plan.u))
+    assert a.objective == b.objective
