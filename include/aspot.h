@@ -158,6 +158,18 @@ POT_API pot_status pot_marginals(const pot_problem* prob, double gamma, const do
                          void* workspace, size_t ws_bytes, double* lrow, double* lcol, double* tot,
                          void* stream);
 
+/* pot_marginals without a workspace, for callers that cannot allocate
+ * device memory (for example while a framework's caching allocator owns the
+ * device, or in a loop that forbids allocation after start-up).  The paper
+ * has no counterpart: this is a deployment convenience.  Scratch comes from a
+ * 16 MiB array inside the library (held on every GPU that loads it); larger
+ * problems are rejected with POT_ENOMEM.  All calls share that array, so
+ * calls that overlap on the GPU race.  The first call on a device looks up
+ * the array's address and should come before any stream capture.
+ * Arguments and results as pot_marginals.  Enqueued only. */
+POT_API pot_status pot_marginals_static(const pot_problem* prob, double gamma, const double* u, const double* v,
+                                        double w, double* lrow, double* lcol, double* tot, void* stream);
+
 /* Largest entry of the raw cost (max C_ij or max |x_i - y_j|^2), host out. */
 POT_API pot_status pot_cost_max(const pot_problem* prob, void* workspace, size_t ws_bytes, double* out, void* stream);
 

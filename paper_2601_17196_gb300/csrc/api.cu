@@ -454,6 +454,14 @@ struct Timer {
 
 }  // namespace
 
+namespace pot {
+// Records a failure message for pot_last_error() from another translation unit.
+pot_status set_last_error(pot_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+}  // namespace pot
+
 extern "C" {
 
 const char* pot_last_error(void) { return g_err.c_str(); }
