@@ -42,6 +42,8 @@ def _args():
     ap.add_argument("--n", type=int, default=N_FULL, help="problem size (default: the 32k workload)")
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "pass"],
+                    help="'pass': time only the fused row+column pass (for ncu captures of that kernel)")
     return ap.parse_args()
 
 
@@ -279,8 +281,39 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_pass_only(args):
+    """K fused row+column passes (pot_marginals) on the cloud workload at size n."""
+    import numpy as np
+    import torch
+    import paper_2601_17196_gb300 as pkg
+    import pot_workloads as W
+    pb = W.cloud_32k(0, n=args.n)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    dp.cost_scale = 1.0 / pkg.pot_cost_max(dp)
+    rng = np.random.default_rng(0)
+    u = torch.tensor(rng.uniform(-12, -9, dp.n), device="cuda")
+    v = torch.tensor(rng.uniform(-12, -9, dp.m), device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            pkg.pot_marginals(dp, pb.gamma, u, v, 5.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pkg.pot_marginals(dp, pb.gamma, u, v, 5.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"mode": "pass", "n": args.n, "ms_per_pass_incl_combine": ms,
+                      "tflops": 2.0 * args.n * args.n * D_FULL / (ms * 1e-3) / 1e12}), flush=True)
+
+
 def main():
     args = _args()
+    if args.mode == "pass":
+        run_pass_only(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

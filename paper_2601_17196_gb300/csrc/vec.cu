@@ -15,15 +15,29 @@ namespace {
 
 constexpr double kLn2 = 0.6931471805599453;
 
-// natural log of sum over blocks of partials (max2, sum) in log2 units
+// Natural log of the sum over blocks of partials (max, sum) in log2 units:
+// the largest shift first, then a compensated (Kahan) FP32 sum of
+// sum_b * 2^(max_b - M) (each term <= 128, ex2.approx relative error 2^-22),
+// one FP64 log at the end.  FP64 exp per partial would dominate the O(n+m)
+// kernels on this GPU (FP64 runs at a small fraction of the FP32 rate).
 __device__ __forceinline__ double combine_parts(const float2* part, int64_t nblk, int64_t stride, int64_t idx) {
-  Lse acc;
-  acc.init();
+  float M = -INFINITY;
   for (int64_t b = 0; b < nblk; ++b) {
     const float2 p = part[b * stride + idx];
-    if (p.y > 0.f) acc.add((double)p.x * kLn2, (double)p.y);
+    if (p.y > 0.f) M = fmaxf(M, p.x);
   }
-  return acc.value();
+  if (!(M > -INFINITY)) return POT_NEG_BIG;
+  float S = 0.f, comp = 0.f;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const float2 p = part[b * stride + idx];
+    if (p.y > 0.f) {
+      const float y = p.y * ex2(p.x - M) - comp;
+      const float t = S + y;
+      comp = (t - S) - y;
+      S = t;
+    }
+  }
+  return ((double)M + log2((double)S)) * kLn2;
 }
 
 template <int NV>
