@@ -85,7 +85,7 @@ Layout make_layout(const pot_problem* P, int flags) {
     L.nrowblk = L.sl.nrowblk;
   }
   const int64_t vblk = vec_blocks(n + m + 2);
-  const int64_t pass_ctas = std::max<int64_t>(L.sl.ncolblk * L.sl.nrowblk, L.use_tc ? L.tl.ncolblk * L.tl.nrowblk : 0);
+  const int64_t pass_ctas = std::max<int64_t>(L.sl.ncolblk * L.sl.nrowblk, L.use_tc ? L.tl.v1_units : 0);
   L.red_doubles = std::max<int64_t>(vblk * 8, pass_ctas) + 64;
   size_t o = 0;
   L.off_state = o; o = align_up(o + sizeof(DevState));
@@ -237,8 +237,8 @@ pot_status run_pass(Ctx& X, const PassDesc& d) {
   return POT_OK;
 }
 
-int64_t pass_ctas(const Ctx& X) {  // one partial per CTA of a pass
-  return X.L.use_tc ? X.L.tl.ncolblk * X.L.tl.nrowblk : X.L.sl.ncolblk * X.L.sl.nrowblk;
+int64_t pass_ctas(const Ctx& X) {  // one partial per CTA of a max / objective pass
+  return X.L.use_tc ? X.L.tl.v1_units : X.L.sl.ncolblk * X.L.sl.nrowblk;
 }
 
 // masses, minima, finiteness of r, c; squared norms; max of the raw cost

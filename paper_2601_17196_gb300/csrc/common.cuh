@@ -5,7 +5,7 @@
 // where a_i collects the row potential (u_i + w, or u_i for the extended
 // Sinkhorn kernel) and b_j the column potential.  Potentials are FP64
 // masters; a pass receives them as FP32 (hi, lo) pairs, with hi rounded to a
-// multiple of 2^-12 so that hi_a + hi_b is exact in FP32 for |a|,|b| < 2^11.
+// multiple of 2^-10 so that hi_a + hi_b is exact in FP32 for |a|,|b| < 2^13.
 // The logit is then fma(-gC, cost, hi_a + hi_b) + (lo_a + lo_b): one rounding
 // relative to the (small) logit instead of one relative to |u|+|v|+|w|.
 #pragma once
@@ -23,7 +23,7 @@ struct HiLo { float hi, lo; };
 __device__ __forceinline__ HiLo split_hilo(double x) {
   HiLo r;
   if (!(x > -1.0e29)) { r.hi = POT_NEG_BIGF; r.lo = 0.f; return r; }   // log 0 (also NaN -> -big)
-  double h = nearbyint(x * 4096.0) * (1.0 / 4096.0);
+  double h = nearbyint(x * 1024.0) * (1.0 / 1024.0);
   r.hi = (float)h;
   r.lo = (float)(x - (double)r.hi);
   return r;

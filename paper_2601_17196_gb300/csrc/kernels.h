@@ -1,6 +1,7 @@
 // Internal (host-side) declarations shared by the translation units of the
 // library.  Nothing here is part of the public C-ABI (include/aspot.h).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -15,10 +16,23 @@ void launch_pass_simt(const PassDesc& P, const SimtLayout& L, cudaStream_t st);
 void launch_sqnorm(int kind, const void* X, int64_t n, int d, int64_t ldx, float* out, cudaStream_t st);
 
 // tcgen05 on-the-fly squared-Euclidean pass (BF16 points)
-struct TcLayout { int64_t ncolblk, nrowblk, nchunks, tiles_per_chunk, n_pad, m_pad; int ok; };
+struct TcLayout {
+  int64_t ncolblk, nrowblk;          // partial counts of the row / column passes (what the combines read)
+  int64_t nchunks, tiles_per_chunk;  // general kernel: 128-row units x column chunks
+  int64_t v1_nrowblk, v1_units;
+  int v2;                            // hot-loop kernel (pass_tc2.cu) serves rows / columns passes
+  int64_t G, T, ntiles2, nrb2, nslots, n_pad2;
+  int64_t n_pad, m_pad;              // padding of the per-pass row / column terms
+  int ok;
+};
 TcLayout tc_layout(int64_t n, int64_t m, int d);
 bool tc_supported(const PassDesc& P);
 cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st, cudaEvent_t before_main = nullptr);
+bool tc2_applicable(int d);
+int tc2_tile_cols();
+void tc2_fill_layout(TcLayout& L, int64_t n, int64_t m, int num_sms);
+cudaError_t launch_pass_tc2(const PassDesc& P, const TcLayout& L, const CUtensorMap& mx, const CUtensorMap& my,
+                            cudaStream_t st);
 
 // --------------------------------------------------------- device state --
 struct DevState {

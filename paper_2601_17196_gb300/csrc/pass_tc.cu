@@ -15,7 +15,7 @@
 //     relative to the warp's largest row maximum and reduced over the 32 rows
 //     of the warp with a transposing butterfly; four warps are merged in
 //     shared memory into one (shift, sum) partial per column and 128 rows.
-// The row potential enters as hi + lo where hi lies on a 2^-12 grid, so
+// The row potential enters as hi + lo where hi lies on a 2^-10 grid, so
 // hi_a + hi_b is exact in FP32 and the FMA rounds once relative to the small
 // result; lo_a is applied per row (it is constant along the row).
 //
@@ -30,6 +30,7 @@
 #include "common.cuh"
 #include "pass.h"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace pot {
 
@@ -40,118 +41,10 @@ constexpr int NSTAGE = 2;
 constexpr int NTHREADS = 320;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr double kL2E = 1.4426950408889634;
-constexpr uint64_t kTimeoutNs = 2000000000ull;
 
 enum { M_RC = 0, M_R = 1, M_C = 2, M_MAX = 3, M_OBJ = 4 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtime() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; on timeout raises the CTA abort flag and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = gtime();
-  while (true) {
-    if (mbar_try(bar, parity)) return true;
-    if (*abort) return false;
-    if (gtime() - t0 > kTimeoutNs) { *abort = 1; return false; }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart (tcgen05 descriptor format).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-  d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 TMEM columns of this warp's 32 lanes: thread t gets lane (base + t).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void named_bar(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// Sum of v[k] over the 32 lanes for each k < 32; lane l ends with column l in v[0].
-__device__ __forceinline__ float transpose_reduce32(float* v, int lane) {
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const bool up = lane & w;
-#pragma unroll
-    for (int k = 0; k < w; ++k) {
-      const float send = up ? v[k] : v[k + w];
-      const float keep = up ? v[k + w] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  return v[0];
-}
+using namespace tcx;
 
 struct TcSmemLayout {
   uint32_t a_off, b_off, b_stage, cs_off, cm_off, rs_off, red_off, bar_off, misc_off, total;
@@ -495,12 +388,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int d, int64_t ld) {
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int d, int64_t ld, int box_rows = 128) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {64, 128};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -520,7 +413,7 @@ cudaError_t launch_mode(const PassDesc& P, const TcLayout& L, const CUtensorMap&
     if (e != cudaSuccess) return e;
     configured = (int)smem;
   }
-  tc_pass_kernel<MODE><<<(unsigned)(L.nrowblk * L.nchunks), NTHREADS, smem, st>>>(P, L, mx, my);
+  tc_pass_kernel<MODE><<<(unsigned)L.v1_units, NTHREADS, smem, st>>>(P, L, mx, my);
   return cudaGetLastError();
 }
 
@@ -528,27 +421,42 @@ cudaError_t launch_mode(const PassDesc& P, const TcLayout& L, const CUtensorMap&
 
 TcLayout tc_layout(int64_t n, int64_t m, int d) {
   TcLayout L{};
-  (void)d;
-  L.nrowblk = (n + BM - 1) / BM;
+  L.v1_nrowblk = (n + BM - 1) / BM;
   const int64_t ntiles = (m + BN - 1) / BN;
-  // choose the number of column chunks so that the work units fill whole
-  // waves of 2 x 152 resident CTAs as evenly as possible (>= 8 tiles a unit)
+  // general kernel: choose the number of column chunks so that the work units
+  // fill whole waves of 2 x 152 resident CTAs as evenly as possible (>= 8 tiles a unit)
   const int64_t slots = 2 * 152;
   double best = -1.0;
   int64_t best_c = 1;
   for (int64_t c = 1; c <= 64 && c <= ntiles; ++c) {
     const int64_t tpc = (ntiles + c - 1) / c;
     if (tpc < 8 && c > 1) break;
-    const int64_t units = L.nrowblk * ((ntiles + tpc - 1) / tpc);
+    const int64_t units = L.v1_nrowblk * ((ntiles + tpc - 1) / tpc);
     const double waves = (double)units / slots;
     const double eff = waves / ceil(waves);
     if (eff > best + 1e-9) { best = eff; best_c = c; }
   }
   L.tiles_per_chunk = (ntiles + best_c - 1) / best_c;
   L.nchunks = (ntiles + L.tiles_per_chunk - 1) / L.tiles_per_chunk;
-  L.ncolblk = L.nchunks;
-  L.n_pad = L.nrowblk * BM;
+  L.v1_units = L.v1_nrowblk * L.nchunks;
+  L.n_pad = L.v1_nrowblk * BM;
   L.m_pad = ntiles * BN;
+  L.v2 = tc2_applicable(d) ? 1 : 0;
+  if (L.v2) {
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    tc2_fill_layout(L, n, m, sms);
+    if (L.n_pad2 > L.n_pad) L.n_pad = L.n_pad2;
+    L.ncolblk = L.nslots;
+    L.nrowblk = L.nrb2;
+  } else {
+    L.ncolblk = L.nchunks;
+    L.nrowblk = L.v1_nrowblk;
+  }
   L.ok = 1;
   return L;
 }
@@ -569,8 +477,13 @@ cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st
   if (e != cudaSuccess) return e;
   if (before_main && (e = cudaEventRecordWithFlags(before_main, st, cudaEventRecordExternal)) != cudaSuccess) return e;
   CUtensorMap mx, my;
-  if (!make_map(&mx, P.X, P.n, P.d, P.ldx) || !make_map(&my, P.Y, P.m, P.d, P.ldy)) return cudaErrorInvalidValue;
   const int md = P.mode;
+  if (L.v2 && !(md & (PASS_MAXCOST | PASS_OBJ))) {
+    if (!make_map(&mx, P.X, P.n, P.d, P.ldx, 128) || !make_map(&my, P.Y, P.m, P.d, P.ldy, tc2_tile_cols()))
+      return cudaErrorInvalidValue;
+    return launch_pass_tc2(P, L, mx, my, st);
+  }
+  if (!make_map(&mx, P.X, P.n, P.d, P.ldx) || !make_map(&my, P.Y, P.m, P.d, P.ldy)) return cudaErrorInvalidValue;
   if (md & PASS_MAXCOST) return launch_mode<M_MAX>(P, L, mx, my, st);
   if (md & PASS_OBJ) return launch_mode<M_OBJ>(P, L, mx, my, st);
   if ((md & PASS_ROWS) && (md & PASS_COLS)) return launch_mode<M_RC>(P, L, mx, my, st);

@@ -202,3 +202,21 @@ def test_dense_4096_full_size_properties(gamma):
     X = _plan_fp64(C, res.plan, res.gamma, res.cost_scale)
     _check_feasible(X, pb.r, pb.c, pb.s)
     assert O.objective(C, X) == pytest.approx(res.objective, rel=1e-5)
+
+
+@pytest.mark.parametrize("p_tune", [1.5, 2.0, 4.0])
+def test_tuned_gamma_sinkhorn_matches_oracle(p_tune):
+    """Theorem 2 / Algorithm 3: gamma = (2 eps / (49 H_min))^(1/p) and the
+    stop threshold eps' = H_min gamma^p; same iterations and objective as the
+    oracle's tuned Sinkhorn."""
+    pb = W.small_dense(2, n=180, m=210)
+    C = pb.C.astype(np.float64)
+    eps = 0.05
+    res = pkg.sinkhorn_pot_solve(_dev(pb), 0.0, eps, max_iter=20000, p_tune=p_tune)
+    ora = O.solve_sinkhorn(C, pb.r, pb.c, pb.s, eps, None, max_iter=20000, p_tune=p_tune)
+    g, e1 = O.tuned_gamma(pb.r, pb.c, eps, p_tune)
+    assert res.gamma == pytest.approx(g, rel=1e-12)
+    assert res.eps_stop == pytest.approx(e1, rel=1e-12)
+    assert res.status == 0 and abs(res.iters - ora.iters) <= 1
+    assert abs(res.objective - ora.objective) <= 1e-5 * abs(ora.objective)
+    _check_feasible(_plan_fp64(C, res.plan, res.gamma, res.cost_scale), pb.r, pb.c, pb.s)
