@@ -44,6 +44,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="solve", choices=["solve", "pass"],
                     help="'pass': time only the fused row+column pass (for ncu captures of that kernel)")
+    ap.add_argument("--workload", default="cloud_32k", choices=["cloud_32k", "dense_4096", "scaling_e4", "batch_3d"],
+                    help="cloud_32k: the headline line; dense_4096: the FP32 dense-cost path (gamma sweep, "
+                         "HBM roofline of the CUDA-core pass); scaling_e4: the appendix's runtime-vs-n study")
     return ap.parse_args()
 
 
@@ -309,8 +312,115 @@ def run_pass_only(args):
                       "tflops": 2.0 * args.n * args.n * D_FULL / (ms * 1e-3) / 1e12}), flush=True)
 
 
+def run_dense(args):
+    """Dense FP32 cost, n = m = 4096 (and a 16384 point, 1 GiB of cost, for the
+    HBM claim): ASPOT to eps at gamma in {0.1, 0.03, 0.01}; achieved bytes of
+    the CUDA-core pass = 4 n m per launch over its CUDA-event time."""
+    import torch
+    import paper_2601_17196_gb300 as pkg
+    import pot_workloads as W
+    burst, sustained, hbm, src = _peaks()
+    out = {"workload": "dense_4096", "rows": []}
+    stream = torch.cuda.Stream()
+    for n, gammas in ((4096, (0.1, 0.03, 0.01)), (16384, (0.03,))):
+        for gam in gammas:
+            pb = W.dense_4096(0, n=n, gamma=gam)
+            dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+            with torch.cuda.stream(stream):
+                for _ in range(args.warmup):
+                    pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_PROFILE)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                res = [pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_PROFILE)
+                       for _ in range(args.steps)]
+                e1.record(stream)
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            it = sum(r.iters for r in res) / args.steps
+            pms = sum(r.pass_ms for r in res) / max(sum(r.pass_launches for r in res), 1)
+            gbs = 4.0 * n * n / (pms * 1e-3) / 1e9
+            out["rows"].append({"n": n, "gamma": gam, "iters": it, "time_to_eps_ms": ms, "it_per_s": it / (ms / 1e3),
+                                "pass_ms": pms, "pass_GBps": gbs, "hbm_frac": gbs / hbm, "hbm_peak": hbm,
+                                "l2_note": "64 MiB cost fits in L2" if n == 4096 else "1 GiB cost > L2",
+                                "objective": res[-1].objective, "converged": all(r.status == 0 for r in res)})
+            del dp
+            torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def run_scaling(args):
+    """Runtime of 1500 fixed ASPOT iterations vs n (appendix scalability study):
+    masses 5 / 3, s = 0.6, gamma = 1e-3, 2-D points, dense FP32 cost; the
+    log-log slope is compared with the paper's ~2.27 (its hardware unstated)."""
+    import numpy as np
+    import torch
+    import paper_2601_17196_gb300 as pkg
+    import pot_workloads as W
+    ns = [200, 300, 500, 1000, 1500, 2000, 2500, 3000, 3500, 4000]
+    rows = []
+    stream = torch.cuda.Stream()
+    for n in ns:
+        pb = W.scaling_e4(0, n=n)
+        dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+        with torch.cuda.stream(stream):
+            pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=1500, flags=pkg.FLAG_NO_STOP)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=1500, flags=pkg.FLAG_NO_STOP)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        rows.append({"n": n, "ms": e0.elapsed_time(e1), "iters": r.iters, "E": r.err_final})
+    x = np.log([q["n"] for q in rows])
+    y = np.log([q["ms"] for q in rows])
+    slope = float(np.polyfit(x, y, 1)[0])
+    big = [q for q in rows if q["n"] >= 1500]
+    slope_big = float(np.polyfit(np.log([q["n"] for q in big]), np.log([q["ms"] for q in big]), 1)[0])
+    print(json.dumps({"workload": "scaling_e4", "rows": rows, "loglog_slope": slope,
+                      "loglog_slope_n_ge_1500": slope_big, "paper_slope": 2.27}), flush=True)
+
+
+def run_batched(args):
+    """512 independent 3-D instances (n_k, m_k ~ U{64..2048}), solved in
+    lockstep by aspot_solve_batched to each one's own threshold."""
+    import torch
+    import paper_2601_17196_gb300 as pkg
+    import pot_workloads as W
+    insts = W.batch_3d(seed=0, count=512)
+    probs = [pkg.DeviceProblem.from_workload(pb, device="cuda") for pb in insts]
+    elems = sum(p.n * p.m for p in probs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    its = [r.iters for r in res]
+    print(json.dumps({"workload": "batch_3d", "instances": len(probs), "cost_entries": elems,
+                      "ms_all_to_eps": ms, "instances_per_s": len(probs) / (ms / 1e3),
+                      "iters_max": max(its), "iters_mean": sum(its) / len(its),
+                      "converged": sum(r.status == 0 for r in res), "kernel_launches": res[0].kernel_launches}),
+          flush=True)
+
+
 def main():
     args = _args()
+    if args.workload == "batch_3d":
+        run_batched(args)
+        return
+    if args.workload == "dense_4096":
+        run_dense(args)
+        return
+    if args.workload == "scaling_e4":
+        run_scaling(args)
+        return
     if args.mode == "pass":
         run_pass_only(args)
         return

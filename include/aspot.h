@@ -158,6 +158,20 @@ POT_API pot_status pot_marginals(const pot_problem* prob, double gamma, const do
                          void* workspace, size_t ws_bytes, double* lrow, double* lcol, double* tot,
                          void* stream);
 
+/* Batched ASPOT: `count` independent problems (host array `probs`, each with
+ * its own device buffers, sizes and s; squared-Euclidean point clouds of one
+ * kind with d <= 4, as in the 3-D registration workloads of Section 4.2)
+ * solved in lockstep with the shared `params` (gamma, eps, max_iter, flags).
+ * Every O(nm) pass of an iteration is one launch over a work list of tiles of
+ * all instances still running; an instance stops at its own threshold.
+ * `plans` and `res` are host arrays of `count` entries (plan buffers on the
+ * device); the return value is the worst instance status.  Workspace size
+ * from pot_workspace_size_batched. */
+POT_API pot_status pot_workspace_size_batched(const pot_problem* probs, int32_t count, size_t* bytes /* host */);
+POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, const pot_params* params,
+                                       void* workspace, size_t ws_bytes, pot_plan* plans, pot_result* res,
+                                       void* stream);
+
 /* pot_marginals without a workspace, for callers that cannot allocate
  * device memory (for example while a framework's caching allocator owns the
  * device, or in a loop that forbids allocation after start-up).  The paper

@@ -13,6 +13,7 @@ from .binding import (  # noqa: F401
     Plan,
     SolveResult,
     aspot_solve,
+    aspot_solve_batched,
     sinkhorn_pot_solve,
     pot_round,
     pot_objective,

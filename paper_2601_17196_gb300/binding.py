@@ -32,7 +32,8 @@ STATUS = {0: "POT_OK", 1: "POT_EINVAL", 2: "POT_ENOMEM", 3: "POT_ECUDA", 4: "POT
           5: "POT_ENONFINITE", 6: "POT_ETIMEOUT"}
 
 EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_round", "pot_objective",
-            "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "pot_last_error"]
+            "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "pot_workspace_size_batched",
+            "aspot_solve_batched", "pot_last_error"]
 
 
 class PotError(RuntimeError):
@@ -88,6 +89,8 @@ def lib() -> ct.CDLL:
         L.pot_cost_max.argtypes = [P, vp, ct.c_size_t, ct.POINTER(dbl), vp]
         L.pot_plan_dense.argtypes = [P, PL, dbl, vp, i64, vp]
         L.pot_trace.argtypes = [vp, i32, vp, vp]
+        L.pot_workspace_size_batched.argtypes = [P, i32, ct.POINTER(ct.c_size_t)]
+        L.aspot_solve_batched.argtypes = [P, i32, Q, vp, ct.c_size_t, PL, R, vp]
         L.pot_last_error.restype = ct.c_char_p
         for name in EXPORTED[:-1]:
             getattr(L, name).restype = ct.c_int
@@ -373,3 +376,40 @@ def pot_plan_dense(prob: DeviceProblem, plan: Plan, gamma: float) -> torch.Tenso
     side.synchronize()
     _finish(side, cur)
     return X
+
+
+def aspot_solve_batched(probs, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
+                        check_every: int = 0, plans=None, ws: Optional[torch.Tensor] = None,
+                        allow_noconv: bool = True):
+    """Solve many independent squared-Euclidean problems (d <= 4) in lockstep.
+    Returns one SolveResult per problem."""
+    L = lib()
+    count = len(probs)
+    parr = (_Problem * count)(*[p.struct() for p in probs])
+    b = ct.c_size_t(0)
+    _check(L.pot_workspace_size_batched(parr, count, ct.byref(b)))
+    need = int(b.value)
+    dev = probs[0].r.device
+    if ws is None:
+        buf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        off = (-buf.data_ptr()) % 256
+        ws, nbytes = buf[off:], need
+    else:
+        off = (-ws.data_ptr()) % 256
+        ws = ws.view(torch.uint8)[off:]
+        nbytes = ws.numel()
+    plans = plans or [Plan.empty(p.n, p.m, dev) for p in probs]
+    plarr = (_Plan * count)(*[pl.struct() for pl in plans])
+    rarr = (_Result * count)()
+    pa = _params(gamma, eps, max_iter, flags, check_every)
+    side, cur = _stream()
+    _check(L.aspot_solve_batched(parr, count, ct.byref(pa), ct.c_void_p(ws.data_ptr()), nbytes, plarr, rarr,
+                                 ct.c_void_p(side.cuda_stream)), allow=(0, 4) if allow_noconv else (0,))
+    _finish(side, cur)
+    out = []
+    for k in range(count):
+        r = rarr[k]
+        out.append(SolveResult(r.status, r.iters, r.objective, r.err_final, r.eps_stop, r.gamma, r.cost_scale,
+                               r.mass, r.ms, r.rounding_branch, r.nonfinite, plans[k], None, r.pass_ms,
+                               r.pass_launches, r.kernel_launches))
+    return out

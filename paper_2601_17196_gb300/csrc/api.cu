@@ -98,10 +98,12 @@ Layout make_layout(const pot_problem* P, int flags) {
   L.off_colp = o; o = align_up(o + sizeof(float2) * L.nrowblk * m);
   for (int k = 0; k < kSlots; ++k) { L.off_u[k] = o; o = align_up(o + sizeof(double) * (n + 2)); }
   for (int k = 0; k < kSlots; ++k) { L.off_v[k] = o; o = align_up(o + sizeof(double) * (m + 2)); }
-  if (L.use_tc) {
-    L.off_rowA = o; o = align_up(o + sizeof(float4) * L.tl.n_pad);
-    L.off_colA = o; o = align_up(o + sizeof(float2) * L.tl.m_pad);
-    L.off_colB = o; o = align_up(o + sizeof(float2) * L.tl.m_pad);
+  {
+    const int64_t np = L.use_tc ? std::max<int64_t>(L.tl.n_pad, n) : n;
+    const int64_t mp = L.use_tc ? std::max<int64_t>(L.tl.m_pad, m) : m;
+    L.off_rowA = o; o = align_up(o + sizeof(float4) * np);
+    L.off_colA = o; o = align_up(o + sizeof(float2) * mp);
+    L.off_colB = o; o = align_up(o + sizeof(float2) * mp);
   }
   L.total = o;
   return L;
@@ -120,6 +122,7 @@ struct Ctx {
   float2 *rowp, *colp;
   float4* rowA = nullptr;
   float2 *colA = nullptr, *colB = nullptr;
+  double *lrow = nullptr, *lcol = nullptr;     // combined log-sums of the last row / column pass
   double* U[kSlots];
   double* V[kSlots];
   double cost_scale = 1.0;
@@ -189,11 +192,11 @@ pot_status bind(Ctx& X, const pot_problem* P, int flags, void* ws, size_t ws_byt
   X.rowp = (float2*)(X.ws + X.L.off_rowp);
   X.colp = (float2*)(X.ws + X.L.off_colp);
   for (int k = 0; k < kSlots; ++k) { X.U[k] = (double*)(X.ws + X.L.off_u[k]); X.V[k] = (double*)(X.ws + X.L.off_v[k]); }
-  if (X.L.use_tc) {
-    X.rowA = (float4*)(X.ws + X.L.off_rowA);
-    X.colA = (float2*)(X.ws + X.L.off_colA);
-    X.colB = (float2*)(X.ws + X.L.off_colB);
-  }
+  X.lrow = X.U[kSlots - 1];
+  X.lcol = X.V[kSlots - 1];
+  X.rowA = (float4*)(X.ws + X.L.off_rowA);
+  X.colA = (float2*)(X.ws + X.L.off_colA);
+  X.colB = (float2*)(X.ws + X.L.off_colB);
   return POT_OK;
 }
 
@@ -228,11 +231,20 @@ pot_status run_pass(Ctx& X, const PassDesc& d) {
     CK(launch_pass_tc(d, X.L.tl, X.st, e0));
     X.launches += 2;
   } else {
+    if (d.mode & (PASS_ROWS | PASS_COLS | PASS_OBJ)) {
+      launch_prep(d, d.n, d.m, X.st);
+      X.launches += 1;
+    }
     if (e0) CK(cudaEventRecordWithFlags(e0, X.st, cudaEventRecordExternal));
     launch_pass_simt(d, X.L.sl, X.st);
     X.launches += 1;
   }
   if (e1) CK(cudaEventRecordWithFlags(e1, X.st, cudaEventRecordExternal));
+  if (d.mode & (PASS_ROWS | PASS_COLS)) {
+    launch_combine(X.rowp, X.L.ncolblk, d.n, (d.mode & PASS_ROWS) ? X.lrow : nullptr, X.colp, X.L.nrowblk, d.m,
+                   (d.mode & PASS_COLS) ? X.lcol : nullptr, d.done, X.st);
+    X.launches += 1;
+  }
   CKL();
   return POT_OK;
 }
@@ -387,6 +399,7 @@ pot_status do_round(Ctx& X, double gamma, const double* u, const double* v, pot_
   R.n = P->n; R.m = P->m; R.r = P->r; R.c = P->c; R.u = u; R.v = v;
   R.f = plan->f; R.g = plan->g; R.p = plan->p; R.q = plan->q; R.kappa = plan->kappa;
   R.row_part = X.rowp; R.col_part = X.colp; R.ncolblk = X.L.ncolblk; R.nrowblk = X.L.nrowblk;
+  R.lrow = X.lrow; R.lcol = X.lcol;
   R.red = X.red; R.counter = X.cnt; R.S = X.S;
   PassDesc d = base_desc(X, gamma);
   // R1: rows of B(u, v, w)
@@ -503,6 +516,7 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   V.ut = X.U[2]; V.vt = X.V[2]; V.uc = X.U[3]; V.vc = X.V[3]; V.ub = X.U[4]; V.vb = X.V[4];
   V.ug = X.U[5]; V.vg = X.V[5]; V.uh = X.U[6]; V.vh = X.V[6]; V.uo = plan->u; V.vo = plan->v;
   V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
+  V.lrow = X.lrow; V.lcol = X.lcol;
   V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
   launch_aspot_init(V, prob->r, prob->c, so.eps_s, params->u0, params->v0, params->w0, X.st); X.launches += 1;
   CKL();
@@ -602,6 +616,7 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
   V.re = X.U[0]; V.lre = X.U[1]; V.ce = X.V[0]; V.lce = X.V[1];
   V.u = X.U[2]; V.v = X.V[2]; V.uprev = X.U[3];
   V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
+  V.lrow = X.lrow; V.lcol = X.lcol;
   V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
   launch_sink_init(V, prob->r, prob->c, so.eps_s, prob->s, X.st); X.launches += 1;
   CKL();
@@ -707,8 +722,7 @@ pot_status pot_marginals(const pot_problem* prob, double gamma, const double* u,
   d.mode = PASS_ROWS | (lcol ? PASS_COLS : 0);
   d.arow0 = u; d.bcol0 = v; d.aoff0 = &X.S->w_out;
   if ((s = run_pass(X, d)) != POT_OK) return s;
-  launch_marginals_out(prob->n, prob->m, X.rowp, lcol ? X.colp : nullptr, X.L.ncolblk, X.L.nrowblk, lrow, lcol,
-                       X.red, X.cnt, tot, X.st);
+  launch_marginals_out(prob->n, prob->m, X.lrow, lcol ? X.lcol : nullptr, lrow, lcol, X.red, X.cnt, tot, X.st);
   CKL();
   return POT_OK;
 }

@@ -1,0 +1,759 @@
+// Batched ASPOT: many independent POT instances of uneven size solved in
+// lockstep (the same iteration t for every instance still running).
+//
+// Rows and columns of all instances are concatenated; each O(nm) pass is ONE
+// launch over a work list of (instance, row block, column block) tiles of the
+// CUDA-core pass (squared-Euclidean costs of low-dimensional points, d <= 4),
+// followed by the wide partial combine.  The O(n+m) updates of Algorithm 2 run
+// with one CTA per instance, so every scalar reduction is a deterministic
+// block reduction.  A converged instance sets its own done flag; its tiles and
+// its update kernels return at once, and the solve ends when all are done.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+#include <math.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/aspot.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace pot {
+pot_status set_last_error(pot_status s, const char* msg);
+}
+
+using namespace pot;
+
+namespace {
+
+constexpr int kBT = 512;       // threads of a per-instance CTA
+constexpr int kH = 32;         // rows of a batched tile (8 warps x 4 rows)
+constexpr int kW = 256;        // columns of a batched tile
+
+template <int NV>
+__device__ void block_sums(double (&v)[NV]) {
+  __shared__ double sh[NV][kBT / 32];
+  __shared__ double tot[NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double x = warp_sum_d(v[k]);
+    if (lane == 0) sh[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < kBT / 32; ++w) s += sh[threadIdx.x][w];
+    tot[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = tot[k];
+  __syncthreads();
+}
+
+// log-sum-exp over the block of (x, active) -> natural log (all threads)
+__device__ double block_lse(double x, bool act) {
+  __shared__ double smx[kBT / 32], ssm[kBT / 32];
+  __shared__ double res;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double mx = act ? x : -INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) smx[warp] = mx;
+  __syncthreads();
+  double M = -INFINITY;
+  for (int w = 0; w < kBT / 32; ++w) M = fmax(M, smx[w]);
+  double s = (act && M > -INFINITY) ? exp(x - M) : 0.0;
+  s = warp_sum_d(s);
+  if (lane == 0) ssm[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBT / 32; ++w) t += ssm[w];
+    res = (t > 0.0) ? M + log(t) : POT_NEG_BIG;
+  }
+  __syncthreads();
+  const double r = res;
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double sexp(double x) { return x > -700.0 ? exp(x) : 0.0; }
+__device__ __forceinline__ double clampl(double x) { return x > POT_NEG_BIG ? x : POT_NEG_BIG; }
+
+struct BVecs {
+  BInst* inst;
+  double *rt, *ct, *lrt, *lct, *ut, *vt, *uc, *vc, *ub, *vb, *ug, *vg, *uh, *vh;
+  double *uo, *vo, *fc, *gc;          // concatenated final duals and plan potentials
+  const double *lrow, *lcol;
+  int* ndone;
+};
+
+// masses, minima and finiteness of r and c per instance
+__global__ void b_stats_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  double v[3] = {0, 0, 0};
+  double mr = INFINITY, mc = INFINITY;
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const double x = I.r[i];
+    v[0] += x; mr = fmin(mr, x);
+    if (!(x >= 0.0) || !isfinite(x)) v[2] = 1.0;
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const double x = I.c[j];
+    v[1] += x; mc = fmin(mc, x);
+    if (!(x >= 0.0) || !isfinite(x)) v[2] = 1.0;
+  }
+  double w[2] = {-mr, -mc};
+  block_sums<3>(v);
+  __shared__ double smn[2][kBT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    double x = w[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) smn[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = -INFINITY, b = -INFINITY;
+    for (int q = 0; q < kBT / 32; ++q) { a = fmax(a, smn[0][q]); b = fmax(b, smn[1][q]); }
+    I.mass_r = v[0]; I.mass_c = v[1]; I.bad = v[2]; I.min_r = -a; I.min_c = -b;
+  }
+}
+
+// largest raw cost per instance from the per-tile maxima
+__global__ void b_max_kernel(BInst* inst, const double* red) {
+  BInst& I = inst[blockIdx.x];
+  double mx = 0.0;
+  for (int64_t k = threadIdx.x; k < I.ntile; k += kBT) mx = fmax(mx, red[I.tile0 + k]);
+  __shared__ double sm[kBT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int q = 0; q < kBT / 32; ++q) a = fmax(a, sm[q]);
+    I.maxc = a;
+  }
+}
+
+// Algorithm 2 setup per instance: smoothed marginals, zero start
+__global__ void b_init_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  const double e = I.eps_s;
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double x = (1.0 - e / 8.0) * I.r[i] + e / (8.0 * (double)I.n);
+    V.rt[g] = x; V.lrt[g] = x > 0.0 ? log(x) : POT_NEG_BIG;
+    V.ut[g] = 0.0; V.uc[g] = 0.0; I.pu[i] = 0.0;
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    const double x = (1.0 - e / 8.0) * I.c[j] + e / (8.0 * (double)I.m);
+    V.ct[g] = x; V.lct[g] = x > 0.0 ? log(x) : POT_NEG_BIG;
+    V.vt[g] = 0.0; V.vc[g] = 0.0; I.pv[j] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    I.w_tilde = 0.0; I.w_check = 0.0; I.w_out = 0.0; I.w_z = 0.0;
+    I.theta = 1.0; I.t = 0; I.done = 0; I.take_hat = 0; I.nonfinite = 0; I.E = INFINITY;
+  }
+}
+
+__global__ void b_extrap_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  if (I.done) return;
+  const double th = I.theta;
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    V.ub[g] = (1.0 - th) * V.uc[g] + th * V.ut[g];
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    V.vb[g] = (1.0 - th) * V.vc[g] + th * V.vt[g];
+  }
+  if (threadIdx.x == 0) I.w_bar = (1.0 - th) * I.w_check + th * I.w_tilde;
+}
+
+// gradient step and coupling (same formulas as the single-instance solver)
+__global__ void b_after_grad_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  if (I.done) return;
+  const double th = I.theta, Lth = I.L * th;
+  double v[3] = {0, 0, 0};
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double ub = V.ub[g];
+    const double rB = sexp(V.lrow[g]), eu = sexp(ub);
+    const double un = ub - (rB + eu - V.rt[g]) / Lth;
+    V.ug[g] = ub + th * (un - V.ut[g]);
+    V.ut[g] = un;
+    v[0] += rB;
+    v[1] += eu - ub * V.rt[g];
+    if (!isfinite(un)) v[2] = 1.0;
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    const double vb = V.vb[g];
+    const double cB = sexp(V.lcol[g]), ev = sexp(vb);
+    const double vn = vb - (cB + ev - V.ct[g]) / Lth;
+    V.vg[g] = vb + th * (vn - V.vt[g]);
+    V.vt[g] = vn;
+    v[1] += ev - vb * V.ct[g];
+    if (!isfinite(vn)) v[2] = 1.0;
+  }
+  block_sums<3>(v);
+  if (threadIdx.x == 0) {
+    const double wn = I.w_bar - (v[0] - I.s) / Lth;
+    I.w_grave = I.w_bar + th * (wn - I.w_tilde);
+    I.w_tilde = wn;
+    if (I.t == 0) I.phi_check = v[0] + v[1] - I.w_bar * I.s;
+    if (v[2] != 0.0 || !isfinite(wn)) I.nonfinite = 1;
+  }
+}
+
+__global__ void b_after_greenkhorn_kernel(BVecs V, int k) {
+  BInst& I = V.inst[blockIdx.x];
+  if (I.done) return;
+  double v[2] = {0, 0};
+  double xr = 0.0;
+  bool act = false;
+  double lt = 0.0;
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double ug = V.ug[g];
+    if (k == 0) {
+      const double uh = V.lrt[g] - softplus(V.lrow[g] - ug);
+      V.uh[g] = uh;
+      v[0] += -uh * V.rt[g];
+    } else {
+      v[0] += sexp(ug) - ug * V.rt[g];
+    }
+  }
+  if (k == 2) {
+    // log |B|_1 at z_grave over the instance's rows (blockwise log-sum-exp of the row log-sums)
+    double acc = -INFINITY, s = 0.0;
+    for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+      const double x = V.lrow[I.row0 + i];
+      if (x > acc) { s = s * exp(acc - x) + 1.0; acc = x; } else s += exp(x - acc);
+    }
+    xr = acc > -INFINITY ? acc + log(s) : POT_NEG_BIG;
+    act = acc > -INFINITY;
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    const double vg = V.vg[g];
+    if (k == 1) {
+      const double vh = V.lct[g] - softplus(V.lcol[g] - vg);
+      V.vh[g] = vh;
+      v[1] += -vh * V.ct[g];
+    } else {
+      v[1] += sexp(vg) - vg * V.ct[g];
+    }
+  }
+  block_sums<2>(v);
+  if (k == 2) lt = block_lse(xr, act);
+  if (threadIdx.x == 0) {
+    double wh = I.w_grave, base;
+    if (k == 0) base = I.sum_rt;
+    else if (k == 1) base = I.sum_ct;
+    else { wh = I.w_grave + I.log_s - lt; base = I.s; }
+    I.w_hat = wh;
+    const double ph = base + v[0] + v[1] - wh * I.s;
+    I.phi_hat = ph;
+    const int take = ph < I.phi_check;
+    I.take_hat = take;
+    I.phi_z = take ? ph : I.phi_check;
+    I.w_z = take ? wh : I.w_check;
+  }
+}
+
+__global__ void b_after_final_kernel(BVecs V, int k) {
+  BInst& I = V.inst[blockIdx.x];
+  if (I.done) return;
+  const int take = I.take_hat;
+  const double* uzh = (k == 0) ? V.uh : V.ug;
+  const double* vzh = (k == 1) ? V.vh : V.vg;
+  double v[4] = {0, 0, 0, 0};
+  double acc = -INFINITY, ssum = 0.0;
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double uz = take ? uzh[g] : V.uc[g];
+    const double R = V.lrow[g];
+    const double rB = sexp(R), eu = sexp(uz);
+    v[0] += fabs(rB + eu - V.rt[g]);
+    v[1] += rB;
+    I.pu[i] = uz;
+    V.uo[g] = uz;
+    const double un = (k == 0) ? V.lrt[g] - softplus(R - uz) : uz;
+    V.uc[g] = un;
+    v[2] += (k == 0) ? -un * V.rt[g] : sexp(un) - un * V.rt[g];
+    if (!isfinite(R) && R != POT_NEG_BIG) v[3] = 1.0;
+    if (R > acc) { ssum = ssum * exp(acc - R) + 1.0; acc = R; } else ssum += exp(R - acc);
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    const double vz = take ? vzh[g] : V.vc[g];
+    const double Cc = V.lcol[g];
+    const double cB = sexp(Cc), ev = sexp(vz);
+    v[0] += fabs(cB + ev - V.ct[g]);
+    I.pv[j] = vz;
+    V.vo[g] = vz;
+    const double vn = (k == 1) ? V.lct[g] - softplus(Cc - vz) : vz;
+    V.vc[g] = vn;
+    v[2] += (k == 1) ? -vn * V.ct[g] : sexp(vn) - vn * V.ct[g];
+    if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[3] = 1.0;
+  }
+  block_sums<4>(v);
+  const double lt = block_lse(acc > -INFINITY ? acc + log(ssum) : POT_NEG_BIG, acc > -INFINITY);
+  if (threadIdx.x == 0) {
+    const double s = I.s;
+    const double E = fabs(v[1] - s) + v[0];
+    const double wz = I.w_z;
+    I.w_out = wz;
+    double wc = wz, base;
+    if (k == 0) base = I.sum_rt;
+    else if (k == 1) base = I.sum_ct;
+    else { wc = wz + I.log_s - lt; base = s; }
+    I.w_check = wc;
+    I.phi_check = base + v[2] - wc * s;
+    I.E = E;
+    I.tot = v[1];
+    const double th = I.theta;
+    I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
+    I.t = I.t + 1;
+    if (v[3] != 0.0 || !isfinite(E)) I.nonfinite = 1;
+    if (E <= I.thr || I.t >= I.max_iter || I.nonfinite) {
+      I.done = 1;
+      atomicAdd(V.ndone, 1);
+    }
+  }
+}
+
+// rounding reading R1-R4, per instance (original r, c, s)
+__global__ void b_round1_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const double lr = I.r[i] > 0.0 ? log(I.r[i]) : POT_NEG_BIG;
+    const double f = clampl(I.pu[i] + I.w_out + fmin(0.0, lr - V.lrow[I.row0 + i]));
+    I.pf[i] = f;
+    V.fc[I.row0 + i] = f;
+  }
+}
+__global__ void b_round2_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  double v[2] = {0, 0};
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const double Cc = V.lcol[I.col0 + j];
+    const double lc = I.c[j] > 0.0 ? log(I.c[j]) : POT_NEG_BIG;
+    const double lb = fmin(0.0, lc - Cc);
+    const double gj = clampl(I.pv[j] + lb);
+    I.pg[j] = gj;
+    V.gc[I.col0 + j] = gj;
+    const double cm = sexp(Cc + lb);
+    const double qj = fmax(I.c[j] - cm, 0.0);
+    I.pq[j] = qj;
+    V.vh[I.col0 + j] = qj;
+    v[0] += cm;
+    v[1] += qj;
+  }
+  block_sums<2>(v);
+  if (threadIdx.x == 0) { I.m2 = v[0]; I.sum_q = v[1]; }
+}
+// after the row pass at (f, g): R3 (uniform scale) or R4 (rank-one fill)
+__global__ void b_round34_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  const bool r3 = I.m2 >= I.s;
+  double v[1] = {0};
+  if (r3) {
+    const double lk = log(I.s / I.m2);
+    for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+      const double f = clampl(I.pf[i] + lk);
+      I.pf[i] = f; V.fc[I.row0 + i] = f;
+      I.pp[i] = 0.0; V.uh[I.row0 + i] = 0.0;
+    }
+    for (int64_t j = threadIdx.x; j < I.m; j += kBT) { I.pq[j] = 0.0; V.vh[I.col0 + j] = 0.0; }
+  } else {
+    for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+      const double pi = fmax(I.r[i] - sexp(V.lrow[I.row0 + i]), 0.0);
+      I.pp[i] = pi;
+      V.uh[I.row0 + i] = pi;
+      v[0] += pi;
+    }
+  }
+  block_sums<1>(v);
+  if (threadIdx.x == 0) {
+    const double den = v[0] * I.sum_q;
+    I.kappa = r3 ? 0.0 : (den > 0.0 ? (I.s - I.m2) / den : 0.0);
+    I.branch = r3 ? 3 : 4;
+    *I.pkappa = I.kappa;
+    *I.pw = I.w_out;
+  }
+}
+__global__ void b_obj_kernel(BInst* inst, const double* red) {
+  BInst& I = inst[blockIdx.x];
+  double v[1] = {0};
+  for (int64_t k = threadIdx.x; k < I.ntile; k += kBT) v[0] += red[I.tile0 + k];
+  block_sums<1>(v);
+  if (threadIdx.x == 0) I.obj = v[0] * I.cost_scale;
+}
+__global__ void b_sqnorm_kernel(BInst* inst, float* xn, float* yn) {
+  BInst& I = inst[blockIdx.x];
+  for (int64_t i = threadIdx.x; i < I.n + I.m; i += kBT) {
+    const bool row = i < I.n;
+    const int64_t k = row ? i : i - I.n;
+    const void* P = row ? I.X : I.Y;
+    const int64_t ld = row ? I.ldx : I.ldy;
+    float acc = 0.f;
+    for (int t = 0; t < I.d; ++t) {
+      float x;
+      if (I.kind == COST_SQEUCLID_BF16) x = __uint_as_float(((unsigned)reinterpret_cast<const unsigned short*>(P)[k * ld + t]) << 16);
+      else if (I.kind == COST_SQEUCLID_F16) x = __half2float(reinterpret_cast<const __half*>(P)[k * ld + t]);
+      else x = reinterpret_cast<const float*>(P)[k * ld + t];
+      acc = fmaf(x, x, acc);
+    }
+    if (row) xn[I.row0 + k] = acc; else yn[I.col0 + k] = acc;
+  }
+}
+__global__ void b_clear_kernel(float2* a, int64_t na, float2* b, int64_t nb) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < na) a[t] = make_float2(POT_NEG_BIGF, 0.f);
+  else if (t < na + nb) b[t - na] = make_float2(POT_NEG_BIGF, 0.f);
+}
+
+// ----------------------------------------------------------------- host ---
+
+struct BLayout {
+  int64_t N = 0, M = 0, T = 0, maxcb = 0, maxrb = 0;
+  size_t off_inst, off_tiles, off_cnt, off_xn, off_yn, off_rowp, off_colp, off_red, off_u[16], off_v[16], total;
+  size_t off_rowA, off_colA, off_colB;
+};
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr int kBSlots = 10;   // rt lrt ut uc ub ug uh lrow + spare
+
+BLayout b_layout(const pot_problem* P, int count, std::vector<BTile>* tiles) {
+  BLayout L;
+  for (int k = 0; k < count; ++k) {
+    const int64_t nrb = (P[k].n + kH - 1) / kH, ncb = (P[k].m + kW - 1) / kW;
+    L.N += P[k].n; L.M += P[k].m; L.T += nrb * ncb;
+    L.maxcb = std::max(L.maxcb, ncb); L.maxrb = std::max(L.maxrb, nrb);
+    if (tiles)
+      for (int64_t rb = 0; rb < nrb; ++rb)
+        for (int64_t cb = 0; cb < ncb; ++cb) tiles->push_back(BTile{k, (int32_t)rb, (int32_t)cb, 0});
+  }
+  size_t o = 0;
+  L.off_inst = o; o = al(o + sizeof(BInst) * count);
+  L.off_tiles = o; o = al(o + sizeof(BTile) * L.T);
+  L.off_cnt = o; o = al(o + 64);
+  L.off_xn = o; o = al(o + sizeof(float) * L.N);
+  L.off_yn = o; o = al(o + sizeof(float) * L.M);
+  L.off_rowp = o; o = al(o + sizeof(float2) * L.maxcb * L.N);
+  L.off_colp = o; o = al(o + sizeof(float2) * L.maxrb * L.M);
+  L.off_red = o; o = al(o + sizeof(double) * (L.T + 1));
+  L.off_rowA = o; o = al(o + sizeof(float4) * L.N);
+  L.off_colA = o; o = al(o + sizeof(float2) * L.M);
+  L.off_colB = o; o = al(o + sizeof(float2) * L.M);
+  for (int s = 0; s < kBSlots; ++s) { L.off_u[s] = o; o = al(o + sizeof(double) * L.N); }
+  for (int s = 0; s < kBSlots; ++s) { L.off_v[s] = o; o = al(o + sizeof(double) * L.M); }
+  L.total = o;
+  return L;
+}
+
+pot_status bfail(pot_status s, const char* msg) { return set_last_error(s, msg); }
+
+pot_status check_batch(const pot_problem* probs, int32_t count) {
+  if (!probs || count < 1) return bfail(POT_EINVAL, "batched: probs must be a host array of count >= 1 problems");
+  for (int k = 0; k < count; ++k) {
+    const pot_problem& p = probs[k];
+    if (p.n < 1 || p.m < 1 || p.n > (1 << 24) || p.m > (1 << 24)) return bfail(POT_EINVAL, "batched: bad n or m");
+    if (p.kind != POT_COST_SQEUCLID_F32 && p.kind != POT_COST_SQEUCLID_BF16 && p.kind != POT_COST_SQEUCLID_F16)
+      return bfail(POT_EINVAL, "batched: only squared-Euclidean point clouds are batched");
+    if (p.kind != probs[0].kind) return bfail(POT_EINVAL, "batched: all instances must share one cost kind");
+    if (p.d < 1 || p.d > 4) return bfail(POT_EINVAL, "batched: point dimension must be 1..4");
+    if (!p.X || !p.Y || !p.r || !p.c) return bfail(POT_EINVAL, "batched: NULL pointer in a problem");
+    if (p.ldx < p.d || p.ldy < p.d) return bfail(POT_EINVAL, "batched: ldx, ldy must be >= d");
+    if (!(p.s > 0.0) || !isfinite(p.s)) return bfail(POT_EINVAL, "batched: s must be finite and > 0");
+    if (!(p.cost_scale >= 0.0) || !isfinite(p.cost_scale)) return bfail(POT_EINVAL, "batched: bad cost_scale");
+  }
+  return POT_OK;
+}
+
+#define BCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      char b_[256];                                                                       \
+      snprintf(b_, sizeof(b_), "batched: %s: %s", #call, cudaGetErrorString(e_));         \
+      return bfail(POT_ECUDA, b_);                                                        \
+    }                                                                                     \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+POT_API pot_status pot_workspace_size_batched(const pot_problem* probs, int32_t count, size_t* bytes) {
+  pot_status s = check_batch(probs, count);
+  if (s != POT_OK) return s;
+  if (!bytes) return bfail(POT_EINVAL, "bytes is NULL");
+  *bytes = b_layout(probs, count, nullptr).total;
+  return POT_OK;
+}
+
+POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, const pot_params* params,
+                                       void* workspace, size_t ws_bytes, pot_plan* plans, pot_result* res,
+                                       void* stream) {
+  pot_status s = check_batch(probs, count);
+  if (s != POT_OK) return s;
+  if (!params || !(params->eps > 0.0) || params->max_iter < 1 || !isfinite(params->gamma))
+    return bfail(POT_EINVAL, "batched: bad params");
+  if (!plans || !res) return bfail(POT_EINVAL, "batched: plans and results must be host arrays of count entries");
+  for (int k = 0; k < count; ++k) {
+    const pot_plan& pl = plans[k];
+    if (!pl.u || !pl.v || !pl.w || !pl.f || !pl.g || !pl.p || !pl.q || !pl.kappa)
+      return bfail(POT_EINVAL, "batched: every plan pointer must be a device buffer");
+  }
+  if (!workspace || (uintptr_t)workspace % 256) return bfail(POT_EINVAL, "batched: workspace NULL or not 256-byte aligned");
+  std::vector<BTile> tiles;
+  const BLayout L = b_layout(probs, count, &tiles);
+  if (ws_bytes < L.total) return bfail(POT_ENOMEM, "batched: workspace too small");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  BInst* dinst = (BInst*)(ws + L.off_inst);
+  BTile* dtiles = (BTile*)(ws + L.off_tiles);
+  int* ndone = (int*)(ws + L.off_cnt);
+  float* xn = (float*)(ws + L.off_xn);
+  float* yn = (float*)(ws + L.off_yn);
+  float2* rowp = (float2*)(ws + L.off_rowp);
+  float2* colp = (float2*)(ws + L.off_colp);
+  double* red = (double*)(ws + L.off_red);
+  double* U[kBSlots];
+  double* Vv[kBSlots];
+  for (int q = 0; q < kBSlots; ++q) { U[q] = (double*)(ws + L.off_u[q]); Vv[q] = (double*)(ws + L.off_v[q]); }
+
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  BCK(cudaEventRecord(e0, st));
+
+  // instance table
+  std::vector<BInst> hi(count);
+  int64_t r0 = 0, c0 = 0, t0 = 0;
+  for (int k = 0; k < count; ++k) {
+    const pot_problem& p = probs[k];
+    BInst& I = hi[k];
+    memset(&I, 0, sizeof(I));
+    I.n = p.n; I.m = p.m; I.row0 = r0; I.col0 = c0;
+    const int64_t nt = ((p.n + kH - 1) / kH) * ((p.m + kW - 1) / kW);
+    I.tile0 = t0; I.ntile = nt;
+    I.X = p.X; I.Y = p.Y; I.d = p.d; I.kind = p.kind; I.ldx = p.ldx; I.ldy = p.ldy;
+    I.r = p.r; I.c = p.c; I.s = p.s; I.cost_scale = p.cost_scale;
+    I.max_iter = params->max_iter;
+    I.pu = plans[k].u; I.pv = plans[k].v; I.pw = plans[k].w; I.pf = plans[k].f; I.pg = plans[k].g;
+    I.pp = plans[k].p; I.pq = plans[k].q; I.pkappa = plans[k].kappa;
+    r0 += p.n; c0 += p.m; t0 += nt;
+  }
+  BCK(cudaMemcpyAsync(dinst, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(dtiles, tiles.data(), sizeof(BTile) * L.T, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemsetAsync(ndone, 0, 64, st));
+
+  BVecs V{};
+  V.inst = dinst;
+  V.rt = U[0]; V.lrt = U[1]; V.ut = U[2]; V.uc = U[3]; V.ub = U[4]; V.ug = U[5]; V.uh = U[6];
+  V.ct = Vv[0]; V.lct = Vv[1]; V.vt = Vv[2]; V.vc = Vv[3]; V.vb = Vv[4]; V.vg = Vv[5]; V.vh = Vv[6];
+  double* lrow = U[7];
+  double* lcol = Vv[7];
+  V.lrow = lrow; V.lcol = lcol; V.ndone = ndone;
+  V.uo = U[8]; V.vo = Vv[8]; V.fc = U[9]; V.gc = Vv[9];
+
+  BatchPass B{};
+  B.kind = probs[0].kind; B.H = kH; B.Ntot = L.N; B.Mtot = L.M; B.tiles = dtiles; B.ntiles = L.T; B.inst = dinst;
+  B.xn = xn; B.yn = yn; B.row_part = rowp; B.col_part = colp; B.red_part = red; B.aoff0 = -1; B.aoff1 = -1;
+  B.count = count;
+  B.rowA = (float4*)(ws + L.off_rowA); B.colA = (float2*)(ws + L.off_colA); B.colB = (float2*)(ws + L.off_colB);
+  int64_t launches = 0;
+  bool in_loop = false;
+  auto pass = [&](int mode, const double* a0, const double* b0, int w0, const double* a1, const double* b1, int w1,
+                  int use_sel) -> pot_status {
+    BatchPass q = B;
+    q.check_done = in_loop ? 1 : 0;
+    q.mode = mode; q.arow0 = a0; q.bcol0 = b0; q.aoff0 = w0; q.arow1 = a1; q.bcol1 = b1; q.aoff1 = w1;
+    q.use_sel = use_sel;
+    if (mode & (PASS_ROWS | PASS_COLS)) {
+      const int64_t na = (mode & PASS_ROWS) ? L.maxcb * L.N : 0, nb = (mode & PASS_COLS) ? L.maxrb * L.M : 0;
+      b_clear_kernel<<<(unsigned)((na + nb + 255) / 256), 256, 0, st>>>(rowp, na, colp, nb);
+      ++launches;
+    }
+    if (mode & (PASS_ROWS | PASS_COLS | PASS_OBJ)) {
+      launch_prep_batched(q, st);
+      ++launches;
+    }
+    launch_pass_simt_batched(q, st);
+    ++launches;
+    if (mode & (PASS_ROWS | PASS_COLS)) {
+      launch_combine(rowp, L.maxcb, L.N, (mode & PASS_ROWS) ? lrow : nullptr, colp, L.maxrb, L.M,
+                     (mode & PASS_COLS) ? lcol : nullptr, nullptr, st);
+      ++launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(POT_ECUDA, cudaGetErrorString(e));
+    return POT_OK;
+  };
+
+  // prologue: masses, squared norms, largest cost of every instance
+  b_stats_kernel<<<count, kBT, 0, st>>>(V);
+  b_sqnorm_kernel<<<count, kBT, 0, st>>>(dinst, xn, yn);
+  launches += 2;
+  if ((s = pass(PASS_MAXCOST, nullptr, nullptr, -1, nullptr, nullptr, -1, 0)) != POT_OK) return s;
+  b_max_kernel<<<count, kBT, 0, st>>>(dinst, red);
+  ++launches;
+  BCK(cudaMemcpyAsync(hi.data(), dinst, sizeof(BInst) * count, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  // Algorithm 2 setup per instance (host, FP64)
+  for (int k = 0; k < count; ++k) {
+    BInst& I = hi[k];
+    if (I.bad != 0.0) return bfail(POT_EINVAL, "batched: r and c must be finite and non-negative");
+    if (!(I.mass_r > 0.0) || !(I.mass_c > 0.0)) return bfail(POT_EINVAL, "batched: r and c must have positive mass");
+    if (I.s > std::min(I.mass_r, I.mass_c) * (1.0 + 1e-12)) return bfail(POT_EINVAL, "batched: s exceeds a mass");
+    I.cost_scale = I.cost_scale > 0.0 ? I.cost_scale : (I.maxc > 0.0 ? 1.0 / I.maxc : 1.0);
+    const double nn = (double)std::max(I.n, I.m);
+    const double gamma = params->gamma > 0.0 ? params->gamma : params->eps / (4.0 * log(std::max(nn, 2.0)));
+    I.gC = I.cost_scale / gamma;
+    const double cmax = I.cost_scale * I.maxc;
+    double thr = params->eps / (8.0 * (cmax > 0.0 ? cmax : 1.0));
+    double e = thr;
+    if (I.mass_r > 1.0) e = std::min(e, 8.0 * (I.mass_r - I.s) / (I.mass_r - 1.0));
+    if (I.mass_c > 1.0) e = std::min(e, 8.0 * (I.mass_c - I.s) / (I.mass_c - 1.0));
+    if ((params->flags & POT_FLAG_NO_SMOOTH) || !(e > 0.0)) e = 0.0;
+    I.eps_s = e;
+    I.sum_rt = (1.0 - e / 8.0) * I.mass_r + e / 8.0;
+    I.sum_ct = (1.0 - e / 8.0) * I.mass_c + e / 8.0;
+    I.L = 3.0 * (I.sum_rt + I.sum_ct - I.s) / gamma;
+    if (params->flags & POT_FLAG_STOP_RAW_EPS) thr = params->eps;
+    I.thr = (params->flags & POT_FLAG_NO_STOP) ? -1.0 : thr;
+    I.log_s = log(I.s);
+  }
+  BCK(cudaMemcpyAsync(dinst, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, st));
+  b_init_kernel<<<count, kBT, 0, st>>>(V);
+  ++launches;
+
+  const int offw_bar = (int)offsetof(BInst, w_bar), offw_grave = (int)offsetof(BInst, w_grave);
+  const int offw_check = (int)offsetof(BInst, w_check), offw_hat = (int)offsetof(BInst, w_hat);
+  const int offw_out = (int)offsetof(BInst, w_out);
+  auto body = [&](int k) -> pot_status {
+    pot_status q;
+    b_extrap_kernel<<<count, kBT, 0, st>>>(V);
+    ++launches;
+    if ((q = pass(PASS_ROWS | PASS_COLS, V.ub, V.vb, offw_bar, nullptr, nullptr, -1, 0)) != POT_OK) return q;
+    b_after_grad_kernel<<<count, kBT, 0, st>>>(V);
+    ++launches;
+    if ((q = pass(k == 1 ? PASS_COLS : PASS_ROWS, V.ug, V.vg, offw_grave, nullptr, nullptr, -1, 0)) != POT_OK) return q;
+    b_after_greenkhorn_kernel<<<count, kBT, 0, st>>>(V, k);
+    ++launches;
+    if ((q = pass(PASS_ROWS | PASS_COLS, V.uc, V.vc, offw_check, (k == 0) ? V.uh : V.ug, (k == 1) ? V.vh : V.vg,
+                  offw_hat, 1)) != POT_OK)
+      return q;
+    b_after_final_kernel<<<count, kBT, 0, st>>>(V, k);
+    ++launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(POT_ECUDA, cudaGetErrorString(e));
+    return POT_OK;
+  };
+
+  // the loop: graphs of `per` iterations, host polls the number of finished instances
+  in_loop = true;
+  const bool graphs = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+  const int per = std::max(3, ((params->check_every > 0 ? params->check_every : 24) + 2) / 3 * 3);
+  cudaGraphExec_t exec = nullptr;
+  int64_t per_graph = 0;
+  if (graphs) {
+    cudaGraph_t g = nullptr;
+    const int64_t l0 = launches;
+    BCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    pot_status q = POT_OK;
+    for (int it = 0; it < per && q == POT_OK; ++it) q = body(it % 3);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (q != POT_OK) { if (g) cudaGraphDestroy(g); return q; }
+    BCK(e);
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    BCK(e);
+    per_graph = launches - l0;
+    launches = l0;
+  }
+  int hdone = 0, rounds = 0;
+  while (rounds * per < params->max_iter + per) {
+    if (graphs) {
+      BCK(cudaGraphLaunch(exec, st));
+      launches += per_graph;
+    } else {
+      for (int it = 0; it < per; ++it)
+        if ((s = body(it % 3)) != POT_OK) return s;
+    }
+    ++rounds;
+    BCK(cudaMemcpyAsync(&hdone, ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    if (hdone >= count) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (hdone < count) return bfail(POT_ETIMEOUT, "batched: not every instance set its stop flag");
+
+  in_loop = false;
+  // rounding (R1-R4) and the objective, all instances at once
+  if ((s = pass(PASS_ROWS, V.uo, V.vo, offw_out, nullptr, nullptr, -1, 0)) != POT_OK) return s;
+  b_round1_kernel<<<count, kBT, 0, st>>>(V);
+  if ((s = pass(PASS_COLS, V.fc, V.vo, -1, nullptr, nullptr, -1, 0)) != POT_OK) return s;
+  b_round2_kernel<<<count, kBT, 0, st>>>(V);
+  if ((s = pass(PASS_ROWS, V.fc, V.gc, -1, nullptr, nullptr, -1, 0)) != POT_OK) return s;
+  b_round34_kernel<<<count, kBT, 0, st>>>(V);
+  launches += 3;
+  {
+    BatchPass q = B;
+    q.mode = PASS_OBJ; q.arow0 = V.fc; q.bcol0 = V.gc; q.aoff0 = -1; q.p = V.uh; q.q = V.vh; q.check_done = 0;
+    launch_prep_batched(q, st);
+    launch_pass_simt_batched(q, st);
+    b_obj_kernel<<<count, kBT, 0, st>>>(dinst, red);
+    launches += 2;
+  }
+  BCK(cudaGetLastError());
+  BCK(cudaEventRecord(e1, st));
+  BCK(cudaMemcpyAsync(hi.data(), dinst, sizeof(BInst) * count, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pot_status worst = POT_OK;
+  for (int k = 0; k < count; ++k) {
+    const BInst& I = hi[k];
+    pot_result& R = res[k];
+    memset(&R, 0, sizeof(R));
+    R.iters = I.t;
+    R.objective = I.obj;
+    R.err_final = I.E;
+    R.eps_stop = I.thr;
+    R.gamma = I.cost_scale / I.gC;
+    R.cost_scale = I.cost_scale;
+    R.mass = I.s;
+    R.ms = ms;
+    R.rounding_branch = I.branch;
+    R.nonfinite = I.nonfinite;
+    R.kernel_launches = launches;
+    R.status = I.nonfinite ? POT_ENONFINITE
+                           : ((I.E <= I.thr || (params->flags & POT_FLAG_NO_STOP)) ? POT_OK : POT_ENOCONV);
+    if (R.status == POT_ENONFINITE) worst = POT_ENONFINITE;
+    else if (R.status == POT_ENOCONV && worst == POT_OK) worst = POT_ENOCONV;
+  }
+  if (worst == POT_ENOCONV) bfail(POT_ENOCONV, "batched: some instances reached max_iter");
+  if (worst == POT_ENONFINITE) bfail(POT_ENONFINITE, "batched: non-finite potentials in some instances");
+  return worst;
+}
+
+}  // extern "C"

@@ -13,6 +13,8 @@ namespace pot {
 struct SimtLayout { int V; int H; int64_t ncolblk, nrowblk; };
 SimtLayout simt_layout(int64_t n, int64_t m);
 void launch_pass_simt(const PassDesc& P, const SimtLayout& L, cudaStream_t st);
+// per-pass FP32 hi/lo row and column terms (rowA / colA / colB of the descriptor)
+void launch_prep(const PassDesc& P, int64_t n_pad, int64_t m_pad, cudaStream_t st);
 void launch_sqnorm(int kind, const void* X, int64_t n, int d, int64_t ldx, float* out, cudaStream_t st);
 
 // tcgen05 on-the-fly squared-Euclidean pass (BF16 points)
@@ -57,6 +59,7 @@ struct AspotVecs {
   const double *rt, *ct, *lrt, *lct;
   double *ut, *vt, *uc, *vc, *ub, *vb, *ug, *vg, *uh, *vh, *uo, *vo;
   const float2* row_part; const float2* col_part;
+  const double* lrow; const double* lcol;   // combined log row / column sums of the last pass
   int64_t ncolblk, nrowblk;
   double* red; unsigned int* counter;
   DevState* S;
@@ -69,6 +72,7 @@ struct SinkVecs {
   const double *re, *ce, *lre, *lce;   // extended marginals (n+1, m+1)
   double *u, *v, *uprev;               // extended potentials
   const float2* row_part; const float2* col_part;
+  const double* lrow; const double* lcol;   // combined log row / column sums of the last pass
   int64_t ncolblk, nrowblk;
   double* red; unsigned int* counter;
   DevState* S;
@@ -82,10 +86,45 @@ struct RoundVecs {
   double *f, *g, *p, *q;      // plan
   double* kappa;
   const float2* row_part; const float2* col_part;
+  const double* lrow; const double* lcol;   // combined log row / column sums of the last pass
   int64_t ncolblk, nrowblk;
   double* red; unsigned int* counter;
   DevState* S;
 };
+
+// ------------------------------------------------------- batched solves --
+// One instance of a batched solve: problem, setup scalars, iteration state
+// and the caller's plan pointers.  Rows / columns of all instances are
+// concatenated (row0 / col0 offsets).
+struct BInst {
+  int64_t n, m, row0, col0, tile0, ntile;
+  const void* X; const void* Y; int32_t d, kind; int64_t ldx, ldy;
+  const double* r; const double* c;
+  double s, cost_scale, gC, maxc;
+  double L, thr, log_s, sum_rt, sum_ct, eps_s;
+  double theta, w_tilde, w_check, w_bar, w_grave, w_hat, w_z, w_out;
+  double phi_check, phi_hat, phi_z, E, tot, m2, sum_q, kappa, obj;
+  double mass_r, mass_c, min_r, min_c, bad;
+  int32_t t, take_hat, done, nonfinite, branch, max_iter;
+  double *pu, *pv, *pw, *pf, *pg, *pp, *pq, *pkappa;
+};
+struct BTile { int32_t inst, rb, cb, pad; };
+struct BatchPass {
+  int mode, kind, H, vec;
+  int64_t Ntot, Mtot;
+  const BTile* tiles; int64_t ntiles;
+  BInst* inst; int64_t count;
+  const float* xn; const float* yn;                    // concatenated squared norms
+  float4* rowA; float2* colA; float2* colB;           // concatenated per-pass terms (batched prep)
+  const double *arow0, *bcol0, *arow1, *bcol1;          // concatenated potentials (set 0 / set 1)
+  int aoff0, aoff1;                                    // byte offset of the scalar w in BInst, -1: none
+  int use_sel;                                         // set 1 when the instance's take_hat is set
+  int check_done;                                      // tiles of finished instances return at once
+  float2* row_part; float2* col_part; double* red_part;
+  const double *p, *q;                                 // concatenated rank-one factors (objective)
+};
+void launch_pass_simt_batched(const BatchPass& B, cudaStream_t st);
+void launch_prep_batched(const BatchPass& B, cudaStream_t st);
 
 constexpr int kVecThreads = 256;
 inline int vec_blocks(int64_t len) { return (int)((len + kVecThreads - 1) / kVecThreads); }
@@ -111,9 +150,10 @@ void launch_round_r2(const RoundVecs& V, cudaStream_t st);
 void launch_round_r3(const RoundVecs& V, cudaStream_t st);
 void launch_round_r4(const RoundVecs& V, cudaStream_t st);
 
-void launch_marginals_out(int64_t n, int64_t m, const float2* row_part, const float2* col_part,
-                          int64_t ncolblk, int64_t nrowblk, double* lrow, double* lcol, double* red,
-                          unsigned int* counter, double* tot_out, cudaStream_t st);
+void launch_marginals_out(int64_t n, int64_t m, const double* lrow_in, const double* lcol_in, double* lrow,
+                          double* lcol, double* red, unsigned int* counter, double* tot_out, cudaStream_t st);
+void launch_combine(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow, const float2* col_part,
+                    int64_t nrowblk, int64_t m, double* lcol, const int* done, cudaStream_t st);
 void launch_dense_plan(const PassDesc& P, const double* f, const double* g, const double* p,
                        const double* q, const double* kappa, float* X, int64_t ldx, cudaStream_t st);
 

@@ -42,21 +42,66 @@ __device__ __forceinline__ float load_pt(const void* base, int64_t idx) {
   }
 }
 
-// DMAX > 0: the lane's point coordinates live in registers (d <= DMAX).
-// DMAX == 0: generic loop over d (slow; any d).
-template <int KIND, int V, int DMAX, bool VEC>
-__global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) {
+// Per-pass row / column terms of the logit, formed once per pass in FP64 and
+// handed to the pass kernels as FP32 (hi, lo) pairs in log2 units:
+//   rowA[i] = (hi, lo of (a_i + aoff - gC |x_i|^2) log2 e, |x_i|^2, p_i)
+//   colA[j] = (hi, lo of (b_j - gC |y_j|^2) log2 e),  colB[j] = (|y_j|^2, q_j)
+// (no norm terms for a dense cost).  Entries past n / m (padding) are log 0.
+// In max-cost mode the tensor-core pass reads the norms through the same slots.
+__global__ void prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad) {
   if (P.done && *P.done) return;
-  constexpr int NC = 4 * V;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t col0 = (int64_t)blockIdx.x * (128 * V);
-  const int64_t row0 = (int64_t)blockIdx.y * H;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool use1 = P.sel && *P.sel;
   const double* arow = use1 ? P.arow1 : P.arow0;
   const double* bcol = use1 ? P.bcol1 : P.bcol0;
   const double* aoffp = use1 ? P.aoff1 : P.aoff0;
-  const double aoff = (aoffp && (P.mode & (PASS_ROWS | PASS_COLS | PASS_OBJ))) ? *aoffp : 0.0;
-  const bool want_rows = P.mode & PASS_ROWS, want_cols = P.mode & PASS_COLS;
+  const bool maxmode = P.mode & PASS_MAXCOST;
+  const bool sq = P.kind != COST_DENSE_F32;
+  if (t < n_pad) {
+    float4 o = make_float4(POT_NEG_BIGF, 0.f, 0.f, 0.f);
+    if (t < P.n) {
+      const float xn = sq ? P.xn[t] : 0.f;
+      if (maxmode) {
+        o = make_float4(xn, 0.f, xn, 0.f);
+      } else {
+        const double a = (arow[t] + (aoffp ? *aoffp : 0.0) - P.gC * (double)xn) * kL2E;
+        HiLo hl = split_hilo(a);
+        o = make_float4(hl.hi, hl.lo, xn, (P.mode & PASS_OBJ) ? (float)P.p[t] : 0.f);
+      }
+    }
+    P.rowA[t] = o;
+  } else if (t < n_pad + m_pad) {
+    const int64_t j = t - n_pad;
+    float2 A = make_float2(POT_NEG_BIGF, 0.f), Bv = make_float2(0.f, 0.f);
+    if (j < P.m) {
+      const float yn = sq ? P.yn[j] : 0.f;
+      if (maxmode) {
+        A = make_float2(yn, 0.f);
+      } else {
+        const double b = ((double)bcol[j] - P.gC * (double)yn) * kL2E;
+        HiLo hl = split_hilo(b);
+        A = make_float2(hl.hi, hl.lo);
+        Bv = make_float2(yn, (P.mode & PASS_OBJ) ? (float)P.q[j] : 0.f);
+      }
+    }
+    P.colA[j] = A;
+    P.colB[j] = Bv;
+  }
+}
+
+// DMAX > 0: the lane's point coordinates live in registers (d <= DMAX).
+// DMAX == 0: generic loop over d (slow; any d).
+// One H x 128V tile (column block cb, row block rb) of the pass.  Partials
+// go to row_part[cb * rstride + i] and col_part[rb * cstride + j]; objective /
+// max-cost partials to red_part[red_idx].
+template <int KIND, int V, int DMAX, bool VEC>
+__device__ __forceinline__ void simt_tile(const PassDesc& P, int H, int64_t cb, int64_t rb, int64_t rstride,
+                                          int64_t cstride, int64_t red_idx) {
+  constexpr int NC = 4 * V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t col0 = cb * (128 * V);
+  const int64_t row0 = rb * H;
+const bool want_rows = P.mode & PASS_ROWS, want_cols = P.mode & PASS_COLS;
   const bool want_obj = P.mode & PASS_OBJ, want_max = P.mode & PASS_MAXCOST;
   const bool need_pot = P.mode & (PASS_ROWS | PASS_COLS | PASS_OBJ);
   const float g2 = (float)(P.gC * kL2E);
@@ -68,21 +113,16 @@ __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) 
 
   float bh[NC], bl[NC], colS[NC];
   float yv[DMAX > 0 ? NC * DMAX : 1];
-  double qv[NC];
+  float qv[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
     const int k = q >> 2, e = q & 3;
     const int64_t j = col0 + 128 * k + 4 * lane + e;
     const bool ok = j < P.m;
-    double b = POT_NEG_BIG;
-    if (ok && need_pot) {
-      b = bcol[j];
-      if (sq) b -= P.gC * (double)P.yn[j];
-    }
-    HiLo h = split_hilo(ok ? b * kL2E : POT_NEG_BIG);
-    bh[q] = h.hi; bl[q] = h.lo;
+    const float2 cb2 = (ok && need_pot) ? P.colA[j] : make_float2(POT_NEG_BIGF, 0.f);
+    bh[q] = cb2.x; bl[q] = cb2.y;
     colS[q] = 0.f;
-    qv[q] = (want_obj && ok) ? P.q[j] : 0.0;
+    qv[q] = (want_obj && ok) ? P.colB[j].y : 0.f;
     if (DMAX > 0) {
 #pragma unroll
       for (int t = 0; t < (DMAX > 0 ? DMAX : 1); ++t)
@@ -106,10 +146,13 @@ __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) 
     for (int rr = 0; rr < R; ++rr) {
       const int64_t i = ib + (int64_t)kWarps * rr;
       const bool rowv = i < rend;
-      double a = (need_pot && rowv) ? arow[i] + aoff : POT_NEG_BIG;
-      if (sq && rowv) a -= P.gC * (double)P.xn[i];
-      HiLo ah = split_hilo(rowv ? a * kL2E : POT_NEG_BIG);
-      if (!need_pot && rowv) { ah.hi = 0.f; ah.lo = 0.f; }
+      HiLo ah;
+      if (rowv && need_pot) {
+        const float4 ra = P.rowA[i];
+        ah.hi = ra.x; ah.lo = ra.y;
+      } else {
+        ah.hi = rowv ? 0.f : POT_NEG_BIGF; ah.lo = 0.f;
+      }
       if (KIND == COST_DENSE_F32) {
         const float* crow = P.C + (rowv ? i : 0) * P.ldc;
 #pragma unroll
@@ -166,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) 
       for (int rr = 0; rr < R; ++rr) {
         const int64_t i = ib + (int64_t)kWarps * rr;
         if (i >= rend) continue;
-        const double pi = want_obj ? P.p[i] : 0.0;
+        const float kpi = want_obj ? (float)(kap * (double)P.rowA[i].w) : 0.f;
         const float xn = sq ? P.xn[i] : 0.f;
         float rowacc = 0.f;
 #pragma unroll
@@ -176,7 +219,7 @@ __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) 
             const float cst = sq ? fmaxf(xn + P.yn[j] - 2.f * cost[rr][q], 0.f) : cost[rr][q];
             maxc = fmaxf(maxc, cst);
             if (want_obj) {
-              const float x = (lg[rr][q] > -1.0e29f ? ex2(lg[rr][q]) : 0.f) + (float)(kap * pi * qv[q]);
+              const float x = (lg[rr][q] > -1.0e29f ? ex2(lg[rr][q]) : 0.f) + kpi * qv[q];
               rowacc = fmaf(cst, x, rowacc);
             }
           }
@@ -197,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) 
 #pragma unroll
         for (int q = 0; q < NC; ++q) ssum += (lg[rr][q] > -1.0e29f) ? ex2(lg[rr][q] - m_i) : 0.f;
         ssum = warp_sum(ssum);
-        if (lane == 0 && i < rend) P.row_part[(int64_t)blockIdx.x * P.n + i] = make_float2(m_i, ssum);
+        if (lane == 0 && i < rend) P.row_part[cb * rstride + i] = make_float2(m_i, ssum);
       }
     }
     if (want_cols) {
@@ -237,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) 
 #pragma unroll
       for (int w = 0; w < kWarps; ++w)
         if (sM[w][t] > -1.0e29f) S = fmaf(sS[w][t], ex2(sM[w][t] - Km), S);
-      P.col_part[(int64_t)blockIdx.y * P.m + j] = make_float2(Km, S);
+      P.col_part[rb * cstride + j] = make_float2(Km, S);
     }
   }
   if (want_obj || want_max) {
@@ -252,9 +295,15 @@ __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) 
     if (threadIdx.x == 0) {
       double acc = want_obj ? 0.0 : sRed[0];
       for (int w = 0; w < kWarps; ++w) acc = want_obj ? acc + sRed[w] : fmax(acc, sRed[w]);
-      P.red_part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+      P.red_part[red_idx] = acc;
     }
   }
+}
+
+template <int KIND, int V, int DMAX, bool VEC>
+__global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) {
+  if (P.done && *P.done) return;
+  simt_tile<KIND, V, DMAX, VEC>(P, H, blockIdx.x, blockIdx.y, P.n, P.m, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 template <int KIND, int V, int DMAX>
@@ -276,17 +325,100 @@ void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
   }
 }
 
+// Batched pass: one CTA per tile of the work list; the tile's instance
+// supplies sizes, points, offsets and its scalar potentials.
+template <int KIND, bool VEC>
+__global__ void __launch_bounds__(kThreads) pass_simt_batched_kernel(BatchPass B) {
+  const BTile tl = B.tiles[blockIdx.x];
+  BInst* I = B.inst + tl.inst;
+  if (B.check_done && I->done) return;
+  PassDesc P{};
+  P.n = I->n; P.m = I->m; P.kind = KIND;
+  P.X = I->X; P.Y = I->Y; P.d = I->d; P.ldx = I->ldx; P.ldy = I->ldy;
+  P.xn = B.xn + I->row0; P.yn = B.yn + I->col0;
+  P.gC = I->gC;
+  const char* base = reinterpret_cast<const char*>(I);
+  P.arow0 = B.arow0 ? B.arow0 + I->row0 : nullptr;
+  P.bcol0 = B.bcol0 ? B.bcol0 + I->col0 : nullptr;
+  P.aoff0 = B.aoff0 >= 0 ? reinterpret_cast<const double*>(base + B.aoff0) : nullptr;
+  P.arow1 = B.arow1 ? B.arow1 + I->row0 : nullptr;
+  P.bcol1 = B.bcol1 ? B.bcol1 + I->col0 : nullptr;
+  P.aoff1 = B.aoff1 >= 0 ? reinterpret_cast<const double*>(base + B.aoff1) : nullptr;
+  P.sel = B.use_sel ? &I->take_hat : nullptr;
+  P.mode = B.mode;
+  P.row_part = B.row_part + I->row0;
+  P.col_part = B.col_part + I->col0;
+  P.red_part = B.red_part;
+  P.p = B.p ? B.p + I->row0 : nullptr;
+  P.q = B.q ? B.q + I->col0 : nullptr;
+  P.kappa = &I->kappa;
+  P.rowA = B.rowA + I->row0;
+  P.colA = B.colA + I->col0;
+  P.colB = B.colB + I->col0;
+  simt_tile<KIND, 2, 4, VEC>(P, B.H, tl.cb, tl.rb, B.Ntot, B.Mtot, blockIdx.x);
+}
+
+// Batched counterpart of prep_kernel: one CTA per instance.
+__global__ void prep_batched_kernel(BatchPass B) {
+  BInst* I = B.inst + blockIdx.x;
+  if (B.check_done && I->done) return;
+  const bool use1 = B.use_sel && I->take_hat;
+  const double* arow = use1 ? B.arow1 : B.arow0;
+  const double* bcol = use1 ? B.bcol1 : B.bcol0;
+  const int aoffb = use1 ? B.aoff1 : B.aoff0;
+  const double aoff = aoffb >= 0 ? *reinterpret_cast<const double*>(reinterpret_cast<const char*>(I) + aoffb) : 0.0;
+  const bool obj = B.mode & PASS_OBJ;
+  for (int64_t i = threadIdx.x; i < I->n; i += blockDim.x) {
+    const int64_t g = I->row0 + i;
+    const float xn = B.xn[g];
+    HiLo hl = split_hilo((arow[g] + aoff - I->gC * (double)xn) * kL2E);
+    B.rowA[g] = make_float4(hl.hi, hl.lo, xn, obj ? (float)B.p[g] : 0.f);
+  }
+  for (int64_t j = threadIdx.x; j < I->m; j += blockDim.x) {
+    const int64_t g = I->col0 + j;
+    const float yn = B.yn[g];
+    HiLo hl = split_hilo((bcol[g] - I->gC * (double)yn) * kL2E);
+    B.colA[g] = make_float2(hl.hi, hl.lo);
+    B.colB[g] = make_float2(yn, obj ? (float)B.q[g] : 0.f);
+  }
+}
+
 }  // namespace
 
+void launch_prep_batched(const BatchPass& B, cudaStream_t st) {
+  prep_batched_kernel<<<(unsigned)B.count, 512, 0, st>>>(B);
+}
+
+void launch_pass_simt_batched(const BatchPass& B, cudaStream_t st) {
+  const unsigned g = (unsigned)B.ntiles;
+  switch (B.kind) {
+    case COST_SQEUCLID_BF16: pass_simt_batched_kernel<COST_SQEUCLID_BF16, false><<<g, kThreads, 0, st>>>(B); break;
+    case COST_SQEUCLID_F16: pass_simt_batched_kernel<COST_SQEUCLID_F16, false><<<g, kThreads, 0, st>>>(B); break;
+    default: pass_simt_batched_kernel<COST_SQEUCLID_F32, false><<<g, kThreads, 0, st>>>(B); break;
+  }
+}
+
 SimtLayout simt_layout(int64_t n, int64_t m) {
+  // About four CTAs per SM in total, each streaming as many rows as that
+  // leaves (a multiple of 32: eight warps x chunks of four rows), so the
+  // per-CTA set-up and the column partials are amortised over many rows.
   SimtLayout L;
   L.V = m > 256 ? 2 : 1;
   L.ncolblk = (m + 128 * L.V - 1) / (128 * L.V);
-  int H = 128;
-  while (H > 8 && L.ncolblk * ((n + H - 1) / H) < 1216) H >>= 1;
-  L.H = H;
+  const int64_t target = 4 * 152;
+  int64_t groups = target / L.ncolblk;
+  if (groups < 1) groups = 1;
+  int64_t H = (n + groups - 1) / groups;
+  H = ((H + 31) / 32) * 32;
+  if (H < 32) H = 32;
+  L.H = (int)H;
   L.nrowblk = (n + H - 1) / H;
   return L;
+}
+
+void launch_prep(const PassDesc& P, int64_t n_pad, int64_t m_pad, cudaStream_t st) {
+  const int64_t tot = n_pad + m_pad;
+  prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, n_pad, m_pad);
 }
 
 void launch_pass_simt(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {

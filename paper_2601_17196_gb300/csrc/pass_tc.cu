@@ -334,48 +334,6 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
   }
 }
 
-// Per-pass row / column terms in log2 units (see the file comment).  Rows
-// and columns are padded to multiples of 128 with log-zero terms.
-__global__ void tc_prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad) {
-  if (P.done && *P.done) return;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool use1 = P.sel && *P.sel;
-  const double* arow = use1 ? P.arow1 : P.arow0;
-  const double* bcol = use1 ? P.bcol1 : P.bcol0;
-  const double* aoffp = use1 ? P.aoff1 : P.aoff0;
-  const bool maxmode = P.mode & PASS_MAXCOST;
-  if (t < n_pad) {
-    float4 o = make_float4(POT_NEG_BIGF, 0.f, 0.f, 0.f);
-    if (t < P.n) {
-      const float xn = P.xn[t];
-      if (maxmode) {
-        o = make_float4(xn, 0.f, xn, 0.f);
-      } else {
-        const double a = (arow[t] + (aoffp ? *aoffp : 0.0) - P.gC * (double)xn) * kL2E;
-        HiLo hl = split_hilo(a);
-        o = make_float4(hl.hi, hl.lo, xn, (P.mode & PASS_OBJ) ? (float)P.p[t] : 0.f);
-      }
-    }
-    P.rowA[t] = o;
-  } else if (t < n_pad + m_pad) {
-    const int64_t j = t - n_pad;
-    float2 A = make_float2(POT_NEG_BIGF, 0.f), Bv = make_float2(0.f, 0.f);
-    if (j < P.m) {
-      const float yn = P.yn[j];
-      if (maxmode) {
-        A = make_float2(yn, 0.f);
-      } else {
-        const double b = ((double)bcol[j] - P.gC * (double)yn) * kL2E;
-        HiLo hl = split_hilo(b);
-        A = make_float2(hl.hi, hl.lo);
-        Bv = make_float2(yn, (P.mode & PASS_OBJ) ? (float)P.q[j] : 0.f);
-      }
-    }
-    P.colA[j] = A;
-    P.colB[j] = Bv;
-  }
-}
-
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -471,8 +429,7 @@ bool tc_supported(const PassDesc& P) {
 }
 
 cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st, cudaEvent_t before_main) {
-  const int64_t tot = L.n_pad + L.m_pad;
-  tc_prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, L.n_pad, L.m_pad);
+  launch_prep(P, L.n_pad, L.m_pad, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (before_main && (e = cudaEventRecordWithFlags(before_main, st, cudaEventRecordExternal)) != cudaSuccess) return e;

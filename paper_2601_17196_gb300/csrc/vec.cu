@@ -40,6 +40,51 @@ __device__ __forceinline__ double combine_parts(const float2* part, int64_t nblk
   return ((double)M + log2((double)S)) * kLn2;
 }
 
+// Partials -> FP64 log-sums for rows and / or columns.  Block = 32 entries x
+// 8 slices of the partials (coalesced: a warp reads 32 consecutive entries of
+// one partial row); the slices meet in shared memory.
+__global__ void combine_kernel(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow,
+                               const float2* col_part, int64_t nrowblk, int64_t m, double* lcol, int64_t nbr,
+                               const int* done) {
+  if (done && *done) return;
+  __shared__ float sM[8][32], sS[8][32];
+  const bool is_row = blockIdx.x < nbr;
+  const float2* part = is_row ? row_part : col_part;
+  const int64_t nblk = is_row ? ncolblk : nrowblk;
+  const int64_t len = is_row ? n : m;
+  double* out = is_row ? lrow : lcol;
+  const int64_t blk = is_row ? blockIdx.x : blockIdx.x - nbr;
+  const int jj = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int64_t j = blk * 32 + jj;
+  float M = -INFINITY, S = 0.f;
+  if (j < len) {
+    for (int64_t b = sl; b < nblk; b += 8) {
+      const float2 p = part[b * len + j];
+      if (p.y > 0.f) M = fmaxf(M, p.x);
+    }
+    if (M > -INFINITY)
+      for (int64_t b = sl; b < nblk; b += 8) {
+        const float2 p = part[b * len + j];
+        if (p.y > 0.f) S = fmaf(p.y, ex2(p.x - M), S);
+      }
+  }
+  sM[sl][jj] = M;
+  sS[sl][jj] = S;
+  __syncthreads();
+  if (sl == 0 && j < len) {
+    float Mt = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) Mt = fmaxf(Mt, sM[k][jj]);
+    double St = 0.0;
+    if (Mt > -INFINITY) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (sS[k][jj] > 0.f) St += (double)sS[k][jj] * (double)ex2(sM[k][jj] - Mt);
+    }
+    out[j] = St > 0.0 ? ((double)Mt + log2(St)) * kLn2 : POT_NEG_BIG;
+  }
+}
+
 template <int NV>
 __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* counter, double (&tot)[NV]) {
   __shared__ double sh[NV][kVecThreads / 32];
@@ -262,7 +307,7 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
   double v[3] = {0, 0, 0};   // tot, sum(e^u - u r~) + sum(e^v - v c~), nonfinite
   if (t < V.n) {
     const double ub = V.ub[t];
-    const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);
+    const double R = V.lrow[t];
     const double rB = safe_exp(R), eu = safe_exp(ub);
     const double g = rB + eu - V.rt[t];
     const double un = ub - g / Lth;
@@ -274,7 +319,7 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vb = V.vb[j];
-    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+    const double Cc = V.lcol[j];
     const double cB = safe_exp(Cc), ev = safe_exp(vb);
     const double g = cB + ev - V.ct[j];
     const double vn = vb - g / Lth;
@@ -306,19 +351,19 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
   if (t < V.n) {
     const double ug = V.ug[t];
     if (k == 0) {
-      const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);
+      const double R = V.lrow[t];
       const double uh = V.lrt[t] - softplus(R - ug);
       V.uh[t] = uh;
       v[0] = -uh * V.rt[t];
     } else {
       v[0] = safe_exp(ug) - ug * V.rt[t];
-      if (k == 2) { xr = combine_parts(V.row_part, V.ncolblk, V.n, t); act = true; }
+      if (k == 2) { xr = V.lrow[t]; act = true; }
     }
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vg = V.vg[j];
     if (k == 1) {
-      const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+      const double Cc = V.lcol[j];
       const double vh = V.lct[j] - softplus(Cc - vg);
       V.vh[j] = vh;
       v[1] = -vh * V.ct[j];
@@ -356,7 +401,7 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   bool act = false;
   if (t < V.n) {
     const double uz = take ? uz_hat[t] : V.uc[t];
-    const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);
+    const double R = V.lrow[t];
     xr = R;
     act = true;
     const double rB = safe_exp(R), eu = safe_exp(uz);
@@ -370,7 +415,7 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vz = take ? vz_hat[j] : V.vc[j];
-    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+    const double Cc = V.lcol[j];
     const double cB = safe_exp(Cc), ev = safe_exp(vz);
     v[0] = fabs(cB + ev - V.ct[j]);
     V.vo[j] = vz;
@@ -446,7 +491,7 @@ __global__ void sink_after_rows_kernel(SinkVecs V) {
   bool act = false;
   if (t < V.n) {
     const double u = V.u[t];
-    const double R = combine_parts(V.row_part, V.ncolblk, V.n, t);   // includes u_i
+    const double R = V.lrow[t];   // includes u_i
     const double lsum = V.dcol ? logaddexp(R, u + vd) : R;
     v[0] = fabs(safe_exp(lsum) - V.re[t]);
     V.uprev[t] = u;
@@ -489,7 +534,7 @@ __global__ void sink_after_cols_kernel(SinkVecs V) {
   bool act = false;
   if (t < V.m) {
     const double vj = V.v[t];
-    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, t);   // includes v_j
+    const double Cc = V.lcol[t];   // includes v_j
     const double lsum = V.drow ? logaddexp(Cc, vj + ud) : Cc;
     V.v[t] = clamp_log(V.lce[t] - (lsum - vj));
   } else if (t < V.m + V.n) {
@@ -518,7 +563,7 @@ __global__ void sink_after_cols_kernel(SinkVecs V) {
 __global__ void round_r1_kernel(RoundVecs V) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V.n) return;
-  const double R = combine_parts(V.row_part, V.ncolblk, V.n, i);
+  const double R = V.lrow[i];
   const double lr = V.r[i] > 0.0 ? log(V.r[i]) : POT_NEG_BIG;
   const double la = fmin(0.0, lr - R);
   V.f[i] = clamp_log(V.u[i] + V.S->w_out + la);
@@ -529,7 +574,7 @@ __global__ void round_r2_kernel(RoundVecs V) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[2] = {0, 0};
   if (j < V.m) {
-    const double Cc = combine_parts(V.col_part, V.nrowblk, V.m, j);
+    const double Cc = V.lcol[j];
     const double lc = V.c[j] > 0.0 ? log(V.c[j]) : POT_NEG_BIG;
     const double lb = fmin(0.0, lc - Cc);
     V.g[j] = clamp_log(V.v[j] + lb);
@@ -560,7 +605,7 @@ __global__ void round_r4_kernel(RoundVecs V) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[1] = {0};
   if (i < V.n) {
-    const double R = combine_parts(V.row_part, V.ncolblk, V.n, i);
+    const double R = V.lrow[i];
     const double pi = fmax(V.r[i] - safe_exp(R), 0.0);
     V.p[i] = pi;
     v[0] = pi;
@@ -574,17 +619,16 @@ __global__ void round_r4_kernel(RoundVecs V) {
   }
 }
 
-__global__ void marginals_out_kernel(int64_t n, int64_t m, const float2* row_part, const float2* col_part,
-                                     int64_t ncolblk, int64_t nrowblk, double* lrow, double* lcol, double* red,
-                                     unsigned int* counter, double* tot_out) {
+__global__ void marginals_out_kernel(int64_t n, int64_t m, const double* lrow_in, const double* lcol_in,
+                                     double* lrow, double* lcol, double* red, unsigned int* counter, double* tot_out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[1] = {0};
   if (t < n) {
-    const double R = combine_parts(row_part, ncolblk, n, t);
+    const double R = lrow_in[t];
     if (lrow) lrow[t] = R;
     v[0] = safe_exp(R);
   } else if (t < n + m) {
-    const double Cc = col_part ? combine_parts(col_part, nrowblk, m, t - n) : 0.0;
+    const double Cc = lcol_in ? lcol_in[t - n] : 0.0;
     if (lcol) lcol[t - n] = Cc;
   }
   double tot[1];
@@ -621,6 +665,15 @@ __global__ void dense_plan_kernel(PassDesc P, const double* f, const double* g, 
 }
 
 }  // namespace
+
+void launch_combine(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow, const float2* col_part,
+                    int64_t nrowblk, int64_t m, double* lcol, const int* done, cudaStream_t st) {
+  const int64_t nbr = lrow ? (n + 31) / 32 : 0;
+  const int64_t nbc = lcol ? (m + 31) / 32 : 0;
+  if (nbr + nbc == 0) return;
+  combine_kernel<<<(unsigned)(nbr + nbc), 256, 0, st>>>(row_part, ncolblk, n, lrow, col_part, nrowblk, m, lcol, nbr,
+                                                        done);
+}
 
 void launch_marg_stats(const double* r, const double* c, int64_t n, int64_t m, double* red,
                        unsigned int* counter, double* out6, cudaStream_t st) {
@@ -668,11 +721,10 @@ void launch_round_r3(const RoundVecs& V, cudaStream_t st) {
 void launch_round_r4(const RoundVecs& V, cudaStream_t st) {
   round_r4_kernel<<<vec_blocks(V.n), kVecThreads, 0, st>>>(V);
 }
-void launch_marginals_out(int64_t n, int64_t m, const float2* row_part, const float2* col_part,
-                          int64_t ncolblk, int64_t nrowblk, double* lrow, double* lcol, double* red,
-                          unsigned int* counter, double* tot_out, cudaStream_t st) {
-  marginals_out_kernel<<<vec_blocks(n + m), kVecThreads, 0, st>>>(n, m, row_part, col_part, ncolblk, nrowblk,
-                                                                 lrow, lcol, red, counter, tot_out);
+void launch_marginals_out(int64_t n, int64_t m, const double* lrow_in, const double* lcol_in, double* lrow,
+                          double* lcol, double* red, unsigned int* counter, double* tot_out, cudaStream_t st) {
+  marginals_out_kernel<<<vec_blocks(n + m), kVecThreads, 0, st>>>(n, m, lrow_in, lcol_in, lrow, lcol, red, counter,
+                                                                 tot_out);
 }
 void launch_dense_plan(const PassDesc& P, const double* f, const double* g, const double* p,
                        const double* q, const double* kappa, float* X, int64_t ldx, cudaStream_t st) {

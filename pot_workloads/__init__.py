@@ -24,6 +24,10 @@ is not available; every input here is synthetic):
 * ``batch_3d``      512 instances, n_k,m_k ~ U{64..2048}, 3-D points in
   [0,1]^3, |r|=1, |c| ~ U[1,1.5], s_k ~ U[0.5,0.95], gamma=0.05, eps=1e-3.
   Stands in for the 3-D point-cloud registration problems (Section 4.2).
+* ``scaling_e4``    the appendix's scalability study: two random non-negative
+  weight vectors of masses 5 and 3 on n points each, squared-Euclidean cost
+  between the points scaled to max 1, s = 0.2 min(5, 3) = 0.6, gamma = 1e-3;
+  the points are not specified there, so they are drawn U[0,1]^2 here.
 * ``mix_2d``        n=m=1024, 2-D mixtures of 2-6 Gaussians, masses
   U[1,1.5], s ~ U[0.6,0.95] (below both masses), gamma=0.02,
   eps=1e-3 (learned warm-start data).
@@ -188,6 +192,17 @@ def mix_2d(seed: int = 0, n: int = 1024, m: Optional[int] = None,
     c = wc / wc.sum() * mc
     s = float(g.uniform(0.6, 0.95))          # both masses are >= 1 > s
     return Problem("mix_2d", r, c, s, gamma, eps, X=X, Y=Y, cost_scale=0.0)
+
+
+def scaling_e4(seed: int = 0, n: int = 1000, gamma: float = 1e-3, eps: float = 1e-7) -> Problem:
+    g = np.random.default_rng(seed)
+    X = g.uniform(0.0, 1.0, size=(n, 2))
+    Y = g.uniform(0.0, 1.0, size=(n, 2))
+    C = _normalised_f32(_sqdist(X, Y))
+    wr, wc = g.uniform(0.0, 1.0, size=n), g.uniform(0.0, 1.0, size=n)
+    r = wr / wr.sum() * 5.0
+    c = wc / wc.sum() * 3.0
+    return Problem("scaling_e4", r, c, 0.6, gamma, eps, C=C, X=X, Y=Y, cost_scale=1.0)
 
 
 def tiny(seed: int = 0, n: int = 5, m: int = 6, d: int = 2, mass_r: float = 1.0,
