@@ -75,6 +75,15 @@ Layout make_layout(const pot_problem* P, int flags) {
   Layout L;
   const int64_t n = P->n, m = P->m;
   L.sl = simt_layout(n, m);
+  if (P->kind == POT_COST_DENSE_F32 && (m % 4) == 0 && (P->ldc % 4) == 0 && ((uintptr_t)P->C % 16) == 0) {
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    simt_dense_layout(L.sl, n, m, sms);
+  }
   L.use_tc = wants_tc(P, flags);
   if (L.use_tc) {
     L.tl = tc_layout(n, m, P->d);
@@ -82,7 +91,7 @@ Layout make_layout(const pot_problem* P, int flags) {
     L.nrowblk = L.tl.nrowblk;
   } else {
     L.ncolblk = L.sl.ncolblk;
-    L.nrowblk = L.sl.nrowblk;
+    L.nrowblk = L.sl.dense_fast ? L.sl.nslots : L.sl.nrowblk;
   }
   const int64_t vblk = vec_blocks(n + m + 2);
   const int64_t pass_ctas = std::max<int64_t>(L.sl.ncolblk * L.sl.nrowblk, L.use_tc ? L.tl.v1_units : 0);

@@ -10,8 +10,13 @@
 namespace pot {
 
 // ---------------------------------------------------------------- passes --
-struct SimtLayout { int V; int H; int64_t ncolblk, nrowblk; };
+struct SimtLayout {
+  int V; int H; int64_t ncolblk, nrowblk;   // generic tiles: ncolblk x nrowblk CTAs of H x 128V
+  int dense_fast;                            // persistent dense pass (rows / columns) applies
+  int64_t G, nrg, U, nslots;                 // its CTAs, 32-row units per panel, units, column slots
+};
 SimtLayout simt_layout(int64_t n, int64_t m);
+void simt_dense_layout(SimtLayout& L, int64_t n, int64_t m, int num_sms);
 void launch_pass_simt(const PassDesc& P, const SimtLayout& L, cudaStream_t st);
 // per-pass FP32 hi/lo row and column terms (rowA / colA / colB of the descriptor)
 void launch_prep(const PassDesc& P, int64_t n_pad, int64_t m_pad, cudaStream_t st);

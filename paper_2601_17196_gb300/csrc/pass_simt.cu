@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "pass.h"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace pot {
 
@@ -300,6 +301,196 @@ const bool want_rows = P.mode & PASS_ROWS, want_cols = P.mode & PASS_COLS;
   }
 }
 
+// ------------------------------------------------------------------------
+// Dense FP32 cost, rows / columns / both: the HBM-bound hot pass.
+// Tile = H rows x 256 columns, 8 warps; lane l owns columns 4l..4l+3 and
+// 128+4l..128+4l+3 (two coalesced float4 per row); warp w takes chunks of 4
+// consecutive rows (row0 + 32k + 4w + r).  The next chunk's cost is loaded
+// while the current one is reduced (register double buffer).
+//   rows: the 4 rows' maxima and sums are reduced over the warp together by a
+//         transposing butterfly (10 shuffles for 4 rows instead of 40);
+//   columns: exact running (max, sum) per column, one rescale per chunk.
+// Requires m % 4 == 0, ldc % 4 == 0 and a 16-byte aligned C.
+
+using tcx::pk2; using tcx::upk2; using tcx::add2; using tcx::fma2; using tcx::max3f;
+
+// v[0..3] (one value per row) reduced over the 32 lanes; lane 8r ends with
+// row r's total in v[0].  IS_MAX selects max, else sum.
+template <bool IS_MAX>
+__device__ __forceinline__ void rows4_reduce(float (&v)[4], int lane) {
+  const bool up16 = lane & 16, up8 = lane & 8;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = up16 ? v[k] : v[k + 2];
+    const float keep = up16 ? v[k + 2] : v[k];
+    const float got = __shfl_xor_sync(0xffffffffu, send, 16);
+    v[k] = IS_MAX ? fmaxf(keep, got) : keep + got;
+  }
+  {
+    const float send = up8 ? v[0] : v[1];
+    const float keep = up8 ? v[1] : v[0];
+    const float got = __shfl_xor_sync(0xffffffffu, send, 8);
+    v[0] = IS_MAX ? fmaxf(keep, got) : keep + got;
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const float got = __shfl_xor_sync(0xffffffffu, v[0], o);
+    v[0] = IS_MAX ? fmaxf(v[0], got) : v[0] + got;
+  }
+}
+
+__global__ void clear_parts_kernel(float2* a, int64_t cnt, const int* done) {
+  if (done && *done) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < cnt) a[t] = make_float2(POT_NEG_BIGF, 0.f);
+}
+
+__host__ __device__ __forceinline__ int64_t dense_owner(int64_t u, int64_t G, int64_t U) { return ((u + 1) * G - 1) / U; }
+
+template <int MODE>   // 0: rows + columns, 1: rows, 2: columns
+__global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, SimtLayout DL) {
+  if (P.done && *P.done) return;
+  constexpr bool ROWS = MODE != 2, COLS = MODE != 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float sS[kWarps][256];
+  __shared__ float sM[kWarps][256];
+  const float g2 = (float)(P.gC * kL2E);
+  const unsigned long long NG = pk2(-g2, -g2);
+  // persistent: CTA c owns units [c U / G, (c+1) U / G) of the panel-major
+  // list of (256-column panel, 32-row unit); a run of units of one panel is a
+  // segment with its own column partial slot
+  const int64_t c = blockIdx.x;
+  const int64_t u_end = (c + 1) * DL.U / DL.G;
+  for (int64_t u = c * DL.U / DL.G; u < u_end;) {
+  const int64_t panel = u / DL.nrg;
+  const int64_t seg_end = ((panel + 1) * DL.nrg < u_end) ? (panel + 1) * DL.nrg : u_end;
+  const int64_t slot = c - dense_owner(panel * DL.nrg, DL.G, DL.U);
+  const int64_t col0 = panel * 256;
+  const int64_t row0 = (u - panel * DL.nrg) * 32;
+  const int64_t rlim = (seg_end - panel * DL.nrg) * 32;
+  const int64_t rend = (rlim < P.n) ? rlim : P.n;
+  u = seg_end;
+
+  // column terms (pairs) and validity of the two float4 groups
+  unsigned long long BH[4], BL[4];
+  bool gv[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int64_t j0 = col0 + 128 * k + 4 * lane;
+    gv[k] = j0 < P.m;
+    float2 c0 = make_float2(POT_NEG_BIGF, 0.f), c1 = c0, c2 = c0, c3 = c0;
+    if (gv[k]) { c0 = P.colA[j0]; c1 = P.colA[j0 + 1]; c2 = P.colA[j0 + 2]; c3 = P.colA[j0 + 3]; }
+    BH[2 * k] = pk2(c0.x, c1.x); BH[2 * k + 1] = pk2(c2.x, c3.x);
+    BL[2 * k] = pk2(c0.y, c1.y); BL[2 * k + 1] = pk2(c2.y, c3.y);
+  }
+  float cM[8], cS[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { cM[q] = POT_NEG_BIGF; cS[q] = 0.f; }
+
+  // chunk c of this warp: rows row0 + 32 c + 4 warp + r
+  float4 cur[4][2], nxt[4][2];
+  auto load_chunk = [&](int64_t base, float4 (&dst)[4][2]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t i = base + r;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (i < rend && gv[k]) dst[r][k] = __ldg(reinterpret_cast<const float4*>(P.C + i * P.ldc + col0 + 128 * k + 4 * lane));
+        else dst[r][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
+  int64_t base = row0 + 4 * warp;
+  if (base < rend) load_chunk(base, cur);
+  for (; base < rend; base += 32) {
+    const int64_t nb = base + 32;
+    if (nb < rend) load_chunk(nb, nxt);
+    // logits of the 4 x 8 entries
+    float lg[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t i = base + r;
+      float4 ra = make_float4(POT_NEG_BIGF, 0.f, 0.f, 0.f);
+      if (i < rend) ra = P.rowA[i];
+      const unsigned long long AH = pk2(ra.x, ra.x), AL = pk2(ra.y, ra.y);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float4 c = cur[r][k];
+        const unsigned long long t0 = add2(fma2(NG, pk2(c.x, c.y), add2(AH, BH[2 * k])), add2(AL, BL[2 * k]));
+        const unsigned long long t1 = add2(fma2(NG, pk2(c.z, c.w), add2(AH, BH[2 * k + 1])), add2(AL, BL[2 * k + 1]));
+        upk2(t0, lg[r][4 * k], lg[r][4 * k + 1]);
+        upk2(t1, lg[r][4 * k + 2], lg[r][4 * k + 3]);
+      }
+    }
+    if (ROWS) {
+      float mx[4], sm[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        mx[r] = fmaxf(max3f(lg[r][0], lg[r][1], lg[r][2]), max3f(max3f(lg[r][3], lg[r][4], lg[r][5]), lg[r][6], lg[r][7]));
+      rows4_reduce<true>(mx, lane);
+      float rm[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) rm[r] = __shfl_sync(0xffffffffu, mx[0], 8 * r);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const bool ok = rm[r] > -1.0e29f;
+        const unsigned long long NM = pk2(ok ? -rm[r] : 0.f, ok ? -rm[r] : 0.f);
+        float s = 0.f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          float a, b;
+          upk2(add2(pk2(lg[r][2 * p], lg[r][2 * p + 1]), NM), a, b);
+          s += ex2(a) + ex2(b);
+        }
+        sm[r] = s;
+      }
+      rows4_reduce<false>(sm, lane);
+      if ((lane & 7) == 0) {
+        const int r = lane >> 3;
+        const int64_t i = base + r;
+        if (i < rend) P.row_part[panel * P.n + i] = make_float2(rm[r], rm[r] > -1.0e29f ? sm[0] : 0.f);
+      }
+    }
+    if (COLS) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float cmx = fmaxf(max3f(lg[0][q], lg[1][q], lg[2][q]), lg[3][q]);
+        const float nm = fmaxf(cM[q], cmx);
+        if (nm > -1.0e29f) {
+          const float sc = cM[q] > -1.0e29f ? ex2(cM[q] - nm) : 0.f;
+          cS[q] = cS[q] * sc + ((ex2(lg[0][q] - nm) + ex2(lg[1][q] - nm)) + (ex2(lg[2][q] - nm) + ex2(lg[3][q] - nm)));
+          cM[q] = nm;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { cur[r][0] = nxt[r][0]; cur[r][1] = nxt[r][1]; }
+  }
+  if (COLS) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = 128 * (q >> 2) + 4 * lane + (q & 3);
+      sS[warp][c] = cS[q];
+      sM[warp][c] = cM[q];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += kThreads) {
+      const int64_t j = col0 + t;
+      if (j >= P.m) continue;
+      float Km = POT_NEG_BIGF;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) Km = fmaxf(Km, sM[w][t]);
+      float S = 0.f;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w)
+        if (sM[w][t] > -1.0e29f) S = fmaf(sS[w][t], ex2(sM[w][t] - Km), S);
+      P.col_part[slot * P.m + j] = make_float2(Km, S);
+    }
+    __syncthreads();            // shared memory is reused by the next segment
+  }
+  }
+}
+
 template <int KIND, int V, int DMAX, bool VEC>
 __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) {
   if (P.done && *P.done) return;
@@ -316,6 +507,18 @@ void launch_v(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
 
 template <int KIND>
 void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
+  const bool hot = (P.mode & (PASS_ROWS | PASS_COLS)) && !(P.mode & (PASS_OBJ | PASS_MAXCOST));
+  if (KIND == COST_DENSE_F32 && hot && L.dense_fast) {
+    if (P.mode & PASS_COLS) {     // slots no segment writes must read as empty
+      const int64_t cnt = L.nslots * P.m;
+      clear_parts_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(P.col_part, cnt, P.done);
+    }
+    const unsigned grid = (unsigned)L.G;
+    if ((P.mode & PASS_ROWS) && (P.mode & PASS_COLS)) dense_pass_kernel<0><<<grid, kThreads, 0, st>>>(P, L);
+    else if (P.mode & PASS_ROWS) dense_pass_kernel<1><<<grid, kThreads, 0, st>>>(P, L);
+    else dense_pass_kernel<2><<<grid, kThreads, 0, st>>>(P, L);
+    return;
+  }
   if (KIND == COST_DENSE_F32) {
     if (L.V == 1) launch_v<KIND, 1, 0>(P, L, st); else launch_v<KIND, 2, 0>(P, L, st);
   } else if (P.d <= 4) {
@@ -413,7 +616,25 @@ SimtLayout simt_layout(int64_t n, int64_t m) {
   if (H < 32) H = 32;
   L.H = (int)H;
   L.nrowblk = (n + H - 1) / H;
+  L.dense_fast = 0;
+  L.G = L.nrg = L.U = 0;
+  L.nslots = 0;
   return L;
+}
+
+void simt_dense_layout(SimtLayout& L, int64_t n, int64_t m, int num_sms) {
+  L.dense_fast = (L.V == 2) ? 1 : 0;
+  if (!L.dense_fast) return;
+  L.nrg = (n + 31) / 32;
+  L.U = L.ncolblk * L.nrg;
+  L.G = 2 * (int64_t)num_sms;
+  if (L.G > L.U) L.G = L.U;
+  int64_t slots = 1;
+  for (int64_t p = 0; p < L.ncolblk; ++p) {
+    const int64_t a = dense_owner(p * L.nrg, L.G, L.U), b = dense_owner((p + 1) * L.nrg - 1, L.G, L.U);
+    if (b - a + 1 > slots) slots = b - a + 1;
+  }
+  L.nslots = slots;
 }
 
 void launch_prep(const PassDesc& P, int64_t n_pad, int64_t m_pad, cudaStream_t st) {
