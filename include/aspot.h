@@ -67,6 +67,7 @@ typedef enum {
 #define POT_FLAG_NO_STOP 8        /* run exactly max_iter iterations (fixed-iteration mode) */
 #define POT_FLAG_FORCE_SIMT 16    /* use the CUDA-core pass even where the tcgen05 pass applies */
 #define POT_FLAG_PROFILE 32       /* time every main-loop pass with CUDA events (res->pass_ms, pass_launches) */
+#define POT_FLAG_WARM_CHECK 64    /* with u0 / v0: start from zero instead when E(z_warm) > E(0) (res->warm_used) */
 
 typedef struct {
   int64_t n, m;
@@ -118,6 +119,10 @@ typedef struct {            /* host struct filled by the solvers */
   double pass_ms;           /* POT_FLAG_PROFILE: summed CUDA-event time of the main-loop passes */
   int64_t pass_launches;    /* POT_FLAG_PROFILE: number of passes timed */
   int64_t kernel_launches;  /* kernels this call launched (all of them this library's own) */
+  double err_warm;          /* POT_FLAG_WARM_CHECK: E at the given start (u0, v0, w0) */
+  double err_zero;          /* POT_FLAG_WARM_CHECK: E at the zero start */
+  int32_t warm_used;        /* 1 if the iterations started from (u0, v0, w0) */
+  int32_t pad;
 } pot_result;
 
 /* Bytes of device workspace the solvers / pot_round / pot_objective /

@@ -4,15 +4,17 @@ for ASPOT).  TEST INFRASTRUCTURE ONLY: nothing in the CUDA library imports,
 links or calls this module.
 
 Network (per point, both clouds of one instance together):
-    features  x_p = [coord_1, coord_2, N_side * weight_p / mass_side, side]   (side = +1 rows, -1 columns)
+    features  x_p = [centred coordinates * sqrt(cost_scale), N_side * weight_p / mass_side, side,
+                     soft minimum of the cost to the other cloud's mass at temperature gamma]
+              (side = +1 rows, -1 columns; F = d + 3 inputs)
     a1 = W1 x_p + b1,             h1 = GELU(a1)                         (128)
     ctx_k = mean of h1 over the points of instance k                    (128)
     q_k  = U [ctx_k; |r|/s; |c|/s]                                       (128)
     a2 = W2 h1 + q_k + b2,         h2 = GELU(a2)                         (128)
     y_p = w3 . h2 + b3                                                   (1)
-The target is gamma * u_i for a row point and gamma * v_j for a column point
-(the duals ASPOT converged to); the loss is the mean squared error over all
-points.  GELU(a) = a Phi(a) with the standard normal CDF Phi (erf form).
+The target is gamma (u_i - log r_i) for a row point and gamma (v_j - log c_j)
+for a column point, (u, v) the duals ASPOT converged to (``targets``); the loss
+is the mean squared error over all points.  GELU(a) = a Phi(a) with the standard normal CDF Phi (erf form).
 """
 from __future__ import annotations
 
@@ -22,7 +24,8 @@ import numpy as np
 from scipy.special import erf
 
 H = 128
-F = 4
+EXTRA = 3        # per-point features besides the d coordinates
+F = 2 + EXTRA    # for d = 2
 E = 2            # extra context inputs: |r|_1 / s, |c|_1 / s
 
 
@@ -34,8 +37,9 @@ def gelu_grad(a):
     return 0.5 * (1.0 + erf(a / math.sqrt(2.0))) + a * np.exp(-0.5 * a * a) / math.sqrt(2.0 * math.pi)
 
 
-def init_params(seed: int = 0) -> dict:
+def init_params(seed: int = 0, d: int = 2) -> dict:
     g = np.random.default_rng(seed)
+    F = d + EXTRA
     return {
         "W1": g.normal(0.0, 1.0 / math.sqrt(F), (H, F)),
         "b1": np.zeros(H),
@@ -97,9 +101,114 @@ def backward(P: dict, feats, seg, extra, target, cache) -> dict:
     return g
 
 
-def features(X, Y, r, c, s):
-    """Per-point features and the per-instance extra inputs of one instance."""
+def features(X, Y, r, c, s, gamma: float, cost_scale: float = 0.0):
+    """Per-point features (rows first) and the per-instance extra inputs
+    [|r|_1 / s, |c|_1 / s] of one instance.  Per point:
+      centred coordinates * sqrt(cost_scale)           (mean over all n + m points)
+      n r_i / |r|_1  or  m c_j / |c|_1
+      +1 (row) or -1 (column)
+      gamma log sum_j (c_j / |c|_1) exp(-C_ij / gamma)   (row; a column uses r)
+    with C = cost_scale |x - y|^2 and cost_scale 0 meaning 1 / max |x_i - y_j|^2
+    (the normalisation of Section 4).  Masses below 1e-12 times their mean are
+    floored inside the logarithm."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
     n, m = X.shape[0], Y.shape[0]
-    fr = np.column_stack([X[:, 0], X[:, 1], n * r / r.sum(), np.ones(n)])
-    fc = np.column_stack([Y[:, 0], Y[:, 1], m * c / c.sum(), -np.ones(m)])
+    D = np.empty((n, m))
+    for i in range(n):
+        D[i] = ((X[i][None, :] - Y) ** 2).sum(axis=1)
+    if cost_scale <= 0.0:
+        mx = float(D.max())
+        cost_scale = 1.0 / mx if mx > 0 else 1.0
+    C = D * cost_scale
+    lr = np.log(np.maximum(r, 1e-12 * r.sum() / n) / r.sum())
+    lc = np.log(np.maximum(c, 1e-12 * c.sum() / m) / c.sum())
+    soft_r = np.array([gamma * _lse(lc - C[i] / gamma) for i in range(n)])
+    soft_c = np.array([gamma * _lse(lr - C[:, j] / gamma) for j in range(m)])
+    mu = np.vstack([X, Y]).mean(axis=0)
+    k = math.sqrt(cost_scale)
+    fr = np.column_stack([(X - mu) * k, n * r / r.sum(), np.ones(n), soft_r])
+    fc = np.column_stack([(Y - mu) * k, m * c / c.sum(), -np.ones(m), soft_c])
     return np.vstack([fr, fc]), np.array([r.sum() / s, c.sum() / s])
+
+
+def _lse(a):
+    mx = a.max()
+    return mx + math.log(np.exp(a - mx).sum())
+
+
+def adam_step(P: dict, G: dict, M: dict, V: dict, step: int, lr: float, b1: float = 0.9, b2: float = 0.999,
+              eps: float = 1e-8) -> None:
+    """Adam (Kingma & Ba, 2015, Algorithm 1) in place: moment estimates,
+    bias corrections 1 / (1 - b^step), update lr m_hat / (sqrt(v_hat) + eps)."""
+    for k in P:
+        M[k] = b1 * M[k] + (1.0 - b1) * G[k]
+        V[k] = b2 * V[k] + (1.0 - b2) * G[k] * G[k]
+        mh = M[k] / (1.0 - b1 ** step)
+        vh = V[k] / (1.0 - b2 ** step)
+        P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
+
+
+def targets(u, v, r, c, gamma: float):
+    """gamma (u_i - log r_i), gamma (v_j - log c_j); masses below 1e-12 times
+    their mean are floored there.  At the optimum e^{u_i} is the untransported
+    part r_i - (B1)_i of row i, so the target is gamma times the log of the
+    fraction of r_i left in place."""
+    r = np.asarray(r, dtype=np.float64)
+    c = np.asarray(c, dtype=np.float64)
+    br = np.log(np.maximum(r, 1e-12 * r.sum() / r.size))
+    bc = np.log(np.maximum(c, 1e-12 * c.sum() / c.size))
+    return np.concatenate([gamma * (np.asarray(u) - br), gamma * (np.asarray(v) - bc)])
+
+
+def shift_step(C, gamma, r, c, s, u, v):
+    """Exact minimiser of phi(u + a 1, v + b 1, w) over (a, b, w) for the dual of
+    Section 2 (unsmoothed marginals): setting the three partial derivatives
+    to zero gives e^(a+b+w) |B(u,v,0)|_1 = s, e^a sum e^u = |r| - s,
+    e^b sum e^v = |c| - s (a = 0 when |r| = s, b = 0 when |c| = s)."""
+    from oracle import pot as O
+    L = O.log_gibbs(C, gamma, u, v, 0.0)
+    ltot = _lse(L.reshape(-1))
+    a = math.log(r.sum() - s) - _lse(np.asarray(u)) if r.sum() > s else 0.0
+    b = math.log(c.sum() - s) - _lse(np.asarray(v)) if c.sum() > s else 0.0
+    w = math.log(s) - ltot - a - b
+    return np.asarray(u) + a, np.asarray(v) + b, w
+
+
+def warm_start(P: dict, X, Y, r, c, s, gamma: float, cost_scale: float = 0.0):
+    """The network's start for one problem: features, forward pass,
+    u = y / gamma + log r, v = y / gamma + log c, then the shift step."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    n, m = X.shape[0], Y.shape[0]
+    f, e = features(X, Y, r, c, s, gamma, cost_scale)
+    y, _ = forward(P, f, np.zeros(n + m, dtype=np.int64), e[None, :])
+    br = np.log(np.maximum(r, 1e-12 * r.sum() / n))
+    bc = np.log(np.maximum(c, 1e-12 * c.sum() / m))
+    u, v = y[:n] / gamma + br, y[n:] / gamma + bc
+    D = np.array([((X[i][None, :] - Y) ** 2).sum(axis=1) for i in range(n)])
+    cs = cost_scale if cost_scale > 0 else 1.0 / D.max()
+    return shift_step(D * cs, gamma, np.asarray(r), np.asarray(c), s, u, v)
+
+
+ORDER = ("W1", "b1", "W2", "U", "b2", "w3", "b3")
+
+
+def unflatten(flat, d: int) -> dict:
+    """Parameter dictionary from the flat layout W1[H][F], b1, W2[H][H], U[H][H+2], b2, w3, b3."""
+    F = d + EXTRA
+    shapes = {"W1": (H, F), "b1": (H,), "W2": (H, H), "U": (H, H + E), "b2": (H,), "w3": (H,), "b3": (1,)}
+    out, o = {}, 0
+    flat = np.asarray(flat, dtype=np.float64)
+    for k in ORDER:
+        size = int(np.prod(shapes[k]))
+        out[k] = flat[o:o + size].reshape(shapes[k]).copy()
+        o += size
+    assert o == flat.size
+    return out
+
+
+def flatten(P: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(P[k], dtype=np.float64).reshape(-1) for k in ORDER])

@@ -22,6 +22,7 @@ FLAG_TRACE = 4
 FLAG_NO_STOP = 8
 FLAG_FORCE_SIMT = 16
 FLAG_PROFILE = 32
+FLAG_WARM_CHECK = 64
 
 COST_DENSE_F32 = 0
 COST_SQEUCLID_BF16 = 1
@@ -33,7 +34,9 @@ STATUS = {0: "POT_OK", 1: "POT_EINVAL", 2: "POT_ENOMEM", 3: "POT_ECUDA", 4: "POT
 
 EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_round", "pot_objective",
             "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "pot_workspace_size_batched",
-            "aspot_solve_batched", "pot_last_error"]
+            "aspot_solve_batched", "pot_marginals_static", "pot_ws_param_count", "pot_ws_init",
+            "pot_ws_features_workspace_size", "pot_ws_features", "pot_ws_targets", "pot_ws_workspace_size", "pot_ws_forward", "pot_ws_gradient",
+            "pot_ws_train_step", "pot_ws_warm_workspace_size", "pot_ws_warm_start", "pot_last_error"]
 
 
 class PotError(RuntimeError):
@@ -55,6 +58,15 @@ class _Params(ct.Structure):
                 ("check_every", ct.c_int32), ("u0", ct.c_void_p), ("v0", ct.c_void_p), ("w0", ct.c_double)]
 
 
+class _WsSet(ct.Structure):
+    _fields_ = [("count", ct.c_int64), ("d", ct.c_int32), ("pad", ct.c_int32), ("off", ct.c_void_p),
+                ("feats", ct.c_void_p), ("extra", ct.c_void_p), ("target", ct.c_void_p)]
+
+
+class _WsAdam(ct.Structure):
+    _fields_ = [("lr", ct.c_float), ("beta1", ct.c_float), ("beta2", ct.c_float), ("eps", ct.c_float)]
+
+
 class _Plan(ct.Structure):
     _fields_ = [(k, ct.c_void_p) for k in ("u", "v", "w", "f", "g", "p", "q", "kappa")]
 
@@ -64,7 +76,9 @@ class _Result(ct.Structure):
                 ("err_final", ct.c_double), ("eps_stop", ct.c_double), ("gamma", ct.c_double),
                 ("cost_scale", ct.c_double), ("mass", ct.c_double), ("ms", ct.c_double),
                 ("rounding_branch", ct.c_int32), ("nonfinite", ct.c_int32),
-                ("pass_ms", ct.c_double), ("pass_launches", ct.c_int64), ("kernel_launches", ct.c_int64)]
+                ("pass_ms", ct.c_double), ("pass_launches", ct.c_int64), ("kernel_launches", ct.c_int64),
+                ("err_warm", ct.c_double), ("err_zero", ct.c_double), ("warm_used", ct.c_int32),
+                ("pad", ct.c_int32)]
 
 
 _lib_handle = None
@@ -91,6 +105,19 @@ def lib() -> ct.CDLL:
         L.pot_trace.argtypes = [vp, i32, vp, vp]
         L.pot_workspace_size_batched.argtypes = [P, i32, ct.POINTER(ct.c_size_t)]
         L.aspot_solve_batched.argtypes = [P, i32, Q, vp, ct.c_size_t, PL, R, vp]
+        L.pot_marginals_static.argtypes = [P, dbl, vp, vp, dbl, vp, vp, vp, vp]
+        WS, AD, sz = ct.POINTER(_WsSet), ct.POINTER(_WsAdam), ct.c_size_t
+        L.pot_ws_param_count.argtypes = [i32, ct.POINTER(i64)]
+        L.pot_ws_init.argtypes = [vp, i32, ct.c_uint64, vp]
+        L.pot_ws_features_workspace_size.argtypes = [P, ct.POINTER(sz)]
+        L.pot_ws_features.argtypes = [P, dbl, vp, sz, vp, vp, vp]
+        L.pot_ws_targets.argtypes = [P, dbl, vp, vp, vp, vp, sz, vp]
+        L.pot_ws_workspace_size.argtypes = [WS, i32, ct.POINTER(sz)]
+        L.pot_ws_forward.argtypes = [WS, vp, i32, vp, i32, vp, vp, sz, vp]
+        L.pot_ws_gradient.argtypes = [WS, vp, i32, vp, i32, vp, vp, vp, sz, vp]
+        L.pot_ws_train_step.argtypes = [WS, vp, i32, vp, vp, vp, AD, i64, i32, vp, vp, sz, vp]
+        L.pot_ws_warm_workspace_size.argtypes = [P, ct.POINTER(sz)]
+        L.pot_ws_warm_start.argtypes = [P, dbl, vp, i32, i32, vp, vp, ct.POINTER(dbl), vp, sz, vp]
         L.pot_last_error.restype = ct.c_char_p
         for name in EXPORTED[:-1]:
             getattr(L, name).restype = ct.c_int
@@ -213,6 +240,9 @@ class SolveResult:
     pass_ms: float = 0.0
     pass_launches: int = 0
     kernel_launches: int = 0
+    err_warm: float = 0.0
+    err_zero: float = 0.0
+    warm_used: int = 0
 
 
 _side_streams = {}
@@ -302,7 +332,8 @@ def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w
     _finish(side, cur)
     return SolveResult(st, res.iters, res.objective, res.err_final, res.eps_stop, res.gamma, res.cost_scale,
                        res.mass, res.ms, res.rounding_branch, res.nonfinite, plan, trace,
-                       res.pass_ms, res.pass_launches, res.kernel_launches)
+                       res.pass_ms, res.pass_launches, res.kernel_launches, res.err_warm, res.err_zero,
+                       res.warm_used)
 
 
 def aspot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,

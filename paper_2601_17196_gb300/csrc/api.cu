@@ -532,6 +532,22 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
 
   const double gamma = so.gamma;
   PassDesc d = base_desc(X, gamma);
+  const bool warm_check = (params->flags & POT_FLAG_WARM_CHECK) && (params->u0 || params->v0);
+  if (warm_check) {
+    // E at the given start and at zero; keep the given start only if it is not worse
+    PassDesc pw = d;
+    pw.mode = PASS_ROWS | PASS_COLS; pw.arow0 = V.uc; pw.bcol0 = V.vc; pw.aoff0 = &X.S->w_check;
+    if ((s = run_pass(X, pw)) != POT_OK) return s;
+    launch_aspot_start_eval(V, V.uc, V.vc, 0, X.st);
+    launch_aspot_zero_bar(V, X.st);
+    PassDesc pz = d;
+    pz.mode = PASS_ROWS | PASS_COLS; pz.arow0 = V.ub; pz.bcol0 = V.vb; pz.aoff0 = &X.S->w_bar;
+    if ((s = run_pass(X, pz)) != POT_OK) return s;
+    launch_aspot_start_eval(V, V.ub, V.vb, 1, X.st);
+    launch_aspot_start_select(V, X.st);
+    X.launches += 4;
+    CKL();
+  }
   auto body = [&](int k) -> pot_status {
     pot_status q;
     launch_aspot_extrap(V, X.st); X.launches += 1;
@@ -574,6 +590,13 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   res->pass_ms = X.pass_ms;
   res->pass_launches = X.pass_count;
   res->kernel_launches = X.launches;
+  if (warm_check) {
+    res->err_warm = h.e_start[0];
+    res->err_zero = h.e_start[1];
+    res->warm_used = h.warm_used;
+  } else {
+    res->warm_used = (params->u0 || params->v0 || params->w0 != 0.0) ? 1 : 0;
+  }
   if (h.nonfinite) { res->status = POT_ENONFINITE; return fail(POT_ENONFINITE, "non-finite potentials or sums"); }
   const bool conv = h.E <= h.thr;
   res->status = (conv || (params->flags & POT_FLAG_NO_STOP)) ? POT_OK : POT_ENOCONV;

@@ -51,7 +51,9 @@ struct DevState {
   double sum_rt, sum_ct;
   double m2, sum_p, sum_q, kappa, log_k1, obj;
   double A_over_g;
+  double e_start[2];         // E(z_warm), E(0) for the warm-start check
   int t, take_hat, done, max_iter, nonfinite, tc_err;
+  int warm_used, pad3;
   unsigned int counter;
   unsigned int pad2;
   double trace[4096][4];     // E, phi_z, phi_check, take_hat per iteration (ring)
@@ -144,6 +146,9 @@ void launch_aspot_extrap(const AspotVecs& V, cudaStream_t st);
 void launch_aspot_after_grad(const AspotVecs& V, cudaStream_t st);
 void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st);
 void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st);
+void launch_aspot_start_eval(const AspotVecs& V, const double* u, const double* v, int slot, cudaStream_t st);
+void launch_aspot_zero_bar(const AspotVecs& V, cudaStream_t st);
+void launch_aspot_start_select(const AspotVecs& V, cudaStream_t st);
 
 void launch_sink_init(const SinkVecs& V, const double* r, const double* c, double eps_s, double s,
                       cudaStream_t st);

@@ -451,6 +451,48 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   }
 }
 
+// Warm-start check.  E(z) = |r(B) + e^u - r~|_1 + |c(B) + e^v - c~|_1 + ||B|_1 - s|
+// from the combined log-sums of a two-sided pass at z = (u, v, .); slot 0
+// holds E at the given start, slot 1 E at zero.
+__global__ void aspot_start_eval_kernel(AspotVecs V, const double* u, const double* v, int slot) {
+  DevState* S = V.S;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double x[2] = {0.0, 0.0};   // l1 residual, |B|_1
+  if (t < V.n) {
+    const double rB = safe_exp(V.lrow[t]);
+    x[0] = fabs(rB + safe_exp(u[t]) - V.rt[t]);
+    x[1] = rB;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    x[0] = fabs(safe_exp(V.lcol[j]) + safe_exp(v[j]) - V.ct[j]);
+  }
+  double tot[2];
+  if (reduce_last<2>(x, V.red, V.counter, tot) && threadIdx.x == 0) S->e_start[slot] = tot[0] + fabs(tot[1] - S->s);
+}
+
+// Zero dual point in the z_bar slots (the pass at z = 0 of the check).
+__global__ void aspot_zero_bar_kernel(AspotVecs V) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < V.n) V.ub[t] = 0.0;
+  else if (t < V.n + V.m) V.vb[t - V.n] = 0.0;
+  if (t == 0) V.S->w_bar = 0.0;
+}
+
+// Keep the given start unless E(z_warm) > E(0) (or is not a number).
+__global__ void aspot_start_select_kernel(AspotVecs V) {
+  DevState* S = V.S;
+  const bool warm = S->e_start[0] <= S->e_start[1];
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!warm) {
+    if (t < V.n) { V.ut[t] = 0.0; V.uc[t] = 0.0; V.uo[t] = 0.0; }
+    else if (t < V.n + V.m) { const int64_t j = t - V.n; V.vt[j] = 0.0; V.vc[j] = 0.0; V.vo[j] = 0.0; }
+  }
+  if (t == 0) {
+    if (!warm) { S->w_tilde = 0.0; S->w_check = 0.0; S->w_out = 0.0; S->w_z = 0.0; }
+    S->warm_used = warm ? 1 : 0;
+  }
+}
+
 // ---------------------------------------------------- feasible Sinkhorn ---
 
 __global__ void sink_init_kernel(SinkVecs V, const double* r, const double* c, double eps_s, double s) {
@@ -697,6 +739,15 @@ void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st) {
 }
 void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st) {
   aspot_after_final_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, k);
+}
+void launch_aspot_start_eval(const AspotVecs& V, const double* u, const double* v, int slot, cudaStream_t st) {
+  aspot_start_eval_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, u, v, slot);
+}
+void launch_aspot_zero_bar(const AspotVecs& V, cudaStream_t st) {
+  aspot_zero_bar_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_aspot_start_select(const AspotVecs& V, cudaStream_t st) {
+  aspot_start_select_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
 }
 void launch_sink_init(const SinkVecs& V, const double* r, const double* c, double eps_s, double s,
                       cudaStream_t st) {

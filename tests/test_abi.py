@@ -1,5 +1,5 @@
 """CPU checks of the C-ABI library: it builds, loads and exports exactly the
-entry points that include/aspot.h declares (no compute call: no GPU here)."""
+entry points that include/*.h declare (no compute call: no GPU here)."""
 import os
 import re
 import subprocess
@@ -7,11 +7,12 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "aspot.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if h.endswith(".h")]
 
 
 def _declared():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"POT_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)))
 
 
@@ -62,3 +63,40 @@ def test_argument_checks_run_before_any_launch(libpath):
     assert L.pot_workspace_size(ct.byref(p), None, ct.byref(b)) == 0 and b.value > 0
     p.kind = 7
     assert L.pot_workspace_size(ct.byref(p), None, ct.byref(b)) == 1
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2601_17196_gb300 import binding as B
+    assert sorted(B.EXPORTED) == _declared()
+
+
+def test_warm_start_argument_checks(libpath):
+    """The warm-start entry points reject bad arguments on the host."""
+    import ctypes as ct
+    import numpy as np
+    from paper_2601_17196_gb300 import binding as B
+    L = B.lib()
+    n = ct.c_int64(0)
+    assert L.pot_ws_param_count(0, ct.byref(n)) == 1
+    assert L.pot_ws_param_count(2, ct.byref(n)) == 0
+    H, F = 128, 5
+    assert n.value == H * F + H + H * H + H * (H + 2) + H + H + 1
+    s = B._WsSet()
+    off = np.array([0, 5, 5], dtype=np.int64)          # second instance empty
+    s.count, s.d, s.off, s.feats, s.extra = 2, 2, off.ctypes.data_as(ct.c_void_p), 8, 8
+    b = ct.c_size_t(0)
+    assert L.pot_ws_workspace_size(ct.byref(s), 4, ct.byref(b)) == 1
+    assert b"no points" in L.pot_last_error()
+    off[2] = 9
+    assert L.pot_ws_workspace_size(ct.byref(s), 4, ct.byref(b)) == 0 and b.value > 0
+    s.d = 7
+    assert L.pot_ws_workspace_size(ct.byref(s), 4, ct.byref(b)) == 1
+    s.d = 2
+    idx = np.array([0, 2], dtype=np.int32)               # 2 is out of range
+    assert L.pot_ws_forward(ct.byref(s), idx.ctypes.data_as(ct.c_void_p), 2, 8, 0, 8, 256, b.value, None) == 1
+    assert b"out of range" in L.pot_last_error()
+    idx[1] = 1
+    assert L.pot_ws_forward(ct.byref(s), idx.ctypes.data_as(ct.c_void_p), 2, 8, 5, 8, 256, b.value, None) == 1
+    assert b"mode" in L.pot_last_error()
+    assert L.pot_ws_gradient(ct.byref(s), idx.ctypes.data_as(ct.c_void_p), 2, 8, 0, 8, 8, 256, b.value, None) == 1
+    assert b"target" in L.pot_last_error()
