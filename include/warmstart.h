@@ -9,10 +9,10 @@
  * |B(u, v, w)|_1 = s), and aspot_solve with POT_FLAG_WARM_CHECK keeps the
  * zero start whenever E(z_warm) > E(0) (E = |grad phi|_1 of Algorithm 2).
  *
- * The network's output y is relative to log r_i (log c_j): u_i = y_i / gamma
- * + log r_i, v_j = y_j / gamma + log c_j (see pot_ws_targets).
+ * The network's output y is gamma log K (see pot_ws_targets), and the start
+ * is u_i = log r_i - softplus(y_i / gamma), v_j = log c_j - softplus(y_j / gamma).
  *
- * Network (H = POT_WS_HIDDEN = 128, F = d + 3 inputs per point):
+ * Network (H = POT_WS_HIDDEN = 128, F = d + 5 inputs per point):
  *   a1 = W1 x + b1,  h1 = GELU(a1)                       per point
  *   ctx_k = mean of h1 over the points of instance k     (both clouds)
  *   q_k = U [ctx_k; |r|_1/s; |c|_1/s]
@@ -21,13 +21,15 @@
  *   (point - mean of all n + m points) * sqrt(cost_scale)   d values
  *   n r_i / |r|_1  (rows)  or  m c_j / |c|_1  (columns)
  *   +1 (rows) or -1 (columns)
- *   gamma log sum_j (c_j / |c|_1) exp(-C_ij / gamma)   (rows; columns: with r)
+ *   T log sum_j (c_j / |c|_1) exp(-C_ij / T), T = gamma, 4 gamma, 16 gamma
+ *                                                  (rows; columns: with r)
  * where cost_scale is the problem's (1 / max |x - y|^2 when it is 0) and C
- * the scaled cost.  The last feature, the soft minimum at temperature gamma
- * of a point's cost to the other cloud's mass, is the c-transform of the
- * normalised log-masses: at the optimum u_i of a transported row point is
- * such a soft minimum (of v instead of log c), so the network learns a
- * correction to it.  It costs one pass over the cost (pot_marginals).
+ * the scaled cost.  The last three features, soft minima of a point's cost
+ * to the other cloud's mass, are c-transforms of the normalised log-masses:
+ * at the optimum u_i of a transported row point is such a soft minimum at
+ * temperature gamma (of v instead of log c), so the network learns a
+ * correction to it; the higher temperatures show the mass around the point
+ * at larger scales.  Each costs one pass over the cost (pot_marginals).
  * Training minimises the mean squared error between y and the targets of
  * converged ASPOT runs (pot_ws_targets), with Adam.
  *
@@ -55,7 +57,8 @@ extern "C" {
 
 #define POT_WS_HIDDEN 128
 #define POT_WS_MAX_D 6          /* point dimension limit */
-#define POT_WS_EXTRA 3          /* features per point besides the d coordinates (F = d + 3 <= 9) */
+#define POT_WS_EXTRA 5          /* features per point besides the d coordinates (F = d + 5 <= 11) */
+#define POT_WS_TEMPS 3          /* soft-minimum features at temperatures gamma, 4 gamma, 16 gamma */
 
 #define POT_WS_FP32 0
 #define POT_WS_BF16 1
@@ -68,7 +71,7 @@ typedef struct {
   int32_t d;              /* point dimension, 1 <= d <= POT_WS_MAX_D */
   int32_t pad;
   const int64_t* off;     /* host, count + 1 non-decreasing offsets, off[0] = 0 */
-  const float* feats;     /* [off[count]][d + 3] */
+  const float* feats;     /* [off[count]][d + 5] */
   const float* extra;     /* [count][2]: |r|_1 / s, |c|_1 / s */
   const float* target;    /* [off[count]] from pot_ws_targets; NULL when only predicting */
 } pot_ws_set;
@@ -85,21 +88,24 @@ POT_API pot_status pot_ws_param_count(int32_t d, int64_t* count);
 POT_API pot_status pot_ws_init(float* params, int32_t d, uint64_t seed, void* stream);
 
 /* Features of one squared-Euclidean problem (any point kind, d <= 6) at
- * entropic parameter gamma: feats [(n + m)][d + 3] (rows first) and
+ * entropic parameter gamma: feats [(n + m)][d + 5] (rows first) and
  * extra [2].  Workspace size from pot_ws_features_workspace_size.  Runs the
  * max-cost pass when prob->cost_scale is 0 (and synchronises the stream for
- * it), then one pot_marginals pass. */
+ * it), then three pot_marginals passes. */
 POT_API pot_status pot_ws_features_workspace_size(const pot_problem* prob, size_t* bytes /* host */);
 POT_API pot_status pot_ws_features(const pot_problem* prob, double gamma, void* workspace, size_t ws_bytes,
                                    float* feats, float* extra, void* stream);
 
-/* Training targets from the converged duals (u, v) of `prob`, n + m floats:
- *   target_i = gamma (u_i - log r_i),  target_{n+j} = gamma (v_j - log c_j),
- * the log of the fraction of a point's mass left untransported (e^{u_i} is
- * the row slack r_i - (B1)_i at the optimum), which does not shift with n.
- * Masses below 1e-12 times their mean are floored there.  `workspace` needs
- * 256 bytes.  Enqueued only. */
-POT_API pot_status pot_ws_targets(const pot_problem* prob, double gamma, const double* u, const double* v,
+/* Training targets from the converged duals (u, v, w) of `prob`, n + m floats:
+ *   target_i = gamma log K_i,  K_i = sum_j B_ij / e^{u_i} = e^w sum_j e^{v_j - C_ij/gamma},
+ *   target_{n+j} = gamma log K'_j,  K'_j = sum_i B_ij / e^{v_j},
+ * the log of the ratio of a point's transported mass to its slack at the
+ * optimum (where (B1)_i + e^{u_i} = r_i, so u_i = log r_i - softplus(log K_i)).
+ * gamma log K_i is a smooth function of the point (a soft minimum over the
+ * other cloud); the sharp softplus is applied in closed form by the warm
+ * start.  One pot_marginals pass (and the max pass when prob->cost_scale is
+ * 0, which synchronises the stream); workspace as pot_ws_features. */
+POT_API pot_status pot_ws_targets(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
                                   float* target, void* workspace, size_t ws_bytes, void* stream);
 
 /* Workspace for batches of at most max_batch instances of `set` (the
@@ -132,9 +138,10 @@ POT_API pot_status pot_ws_train_step(const pot_ws_set* set, const int32_t* idx, 
 /* Workspace for pot_ws_warm_start on this problem. */
 POT_API pot_status pot_ws_warm_workspace_size(const pot_problem* prob, size_t* bytes /* host */);
 
-/* Warm start of one problem: features, network prediction, u0 = y / gamma +
- * log r on the rows, v0 = y / gamma + log c on the columns (device FP64, n
- * and m), then the exact minimiser of phi along the three uniform shifts
+/* Warm start of one problem: features, network prediction,
+ * u0 = log r - softplus(y / gamma) on the rows and v0 = log c - softplus(y / gamma)
+ * on the columns (device FP64, n and m; masses below 1e-12 times their mean
+ * floored in the log), then the exact minimiser of phi along the three uniform shifts
  * (u + a 1, v + b 1, w), a closed form from |B(u0, v0, 0)|_1 and the sums of
  * e^{u0}, e^{v0}:
  *   e^a = (|r|_1 - s) / sum e^{u0_i},  e^b = (|c|_1 - s) / sum e^{v0_j},

@@ -5,16 +5,18 @@ links or calls this module.
 
 Network (per point, both clouds of one instance together):
     features  x_p = [centred coordinates * sqrt(cost_scale), N_side * weight_p / mass_side, side,
-                     soft minimum of the cost to the other cloud's mass at temperature gamma]
-              (side = +1 rows, -1 columns; F = d + 3 inputs)
+                     soft minima of the cost to the other cloud's mass at temperatures
+                     gamma, 4 gamma, 16 gamma]
+              (side = +1 rows, -1 columns; F = d + 5 inputs)
     a1 = W1 x_p + b1,             h1 = GELU(a1)                         (128)
     ctx_k = mean of h1 over the points of instance k                    (128)
     q_k  = U [ctx_k; |r|/s; |c|/s]                                       (128)
     a2 = W2 h1 + q_k + b2,         h2 = GELU(a2)                         (128)
     y_p = w3 . h2 + b3                                                   (1)
-The target is gamma (u_i - log r_i) for a row point and gamma (v_j - log c_j)
-for a column point, (u, v) the duals ASPOT converged to (``targets``); the loss
-is the mean squared error over all points.  GELU(a) = a Phi(a) with the standard normal CDF Phi (erf form).
+The target is gamma log K (``targets``) for the duals (u, v, w) ASPOT
+converged to, and the start from a prediction y is u = log r - softplus(y /
+gamma), v = log c - softplus(y / gamma) (``warm_start``); the loss is the mean
+squared error over all points.  GELU(a) = a Phi(a) with the standard normal CDF Phi (erf form).
 """
 from __future__ import annotations
 
@@ -24,7 +26,8 @@ import numpy as np
 from scipy.special import erf
 
 H = 128
-EXTRA = 3        # per-point features besides the d coordinates
+EXTRA = 5        # per-point features besides the d coordinates
+TEMPS = (1.0, 4.0, 16.0)   # soft-minimum temperatures, in units of gamma
 F = 2 + EXTRA    # for d = 2
 E = 2            # extra context inputs: |r|_1 / s, |c|_1 / s
 
@@ -107,7 +110,8 @@ def features(X, Y, r, c, s, gamma: float, cost_scale: float = 0.0):
       centred coordinates * sqrt(cost_scale)           (mean over all n + m points)
       n r_i / |r|_1  or  m c_j / |c|_1
       +1 (row) or -1 (column)
-      gamma log sum_j (c_j / |c|_1) exp(-C_ij / gamma)   (row; a column uses r)
+      T log sum_j (c_j / |c|_1) exp(-C_ij / T)  for T = gamma, 4 gamma, 16 gamma
+                                                 (row; a column uses r)
     with C = cost_scale |x - y|^2 and cost_scale 0 meaning 1 / max |x_i - y_j|^2
     (the normalisation of Section 4).  Masses below 1e-12 times their mean are
     floored inside the logarithm."""
@@ -125,12 +129,12 @@ def features(X, Y, r, c, s, gamma: float, cost_scale: float = 0.0):
     C = D * cost_scale
     lr = np.log(np.maximum(r, 1e-12 * r.sum() / n) / r.sum())
     lc = np.log(np.maximum(c, 1e-12 * c.sum() / m) / c.sum())
-    soft_r = np.array([gamma * _lse(lc - C[i] / gamma) for i in range(n)])
-    soft_c = np.array([gamma * _lse(lr - C[:, j] / gamma) for j in range(m)])
+    soft_r = [np.array([T * gamma * _lse(lc - C[i] / (T * gamma)) for i in range(n)]) for T in TEMPS]
+    soft_c = [np.array([T * gamma * _lse(lr - C[:, j] / (T * gamma)) for j in range(m)]) for T in TEMPS]
     mu = np.vstack([X, Y]).mean(axis=0)
     k = math.sqrt(cost_scale)
-    fr = np.column_stack([(X - mu) * k, n * r / r.sum(), np.ones(n), soft_r])
-    fc = np.column_stack([(Y - mu) * k, m * c / c.sum(), -np.ones(m), soft_c])
+    fr = np.column_stack([(X - mu) * k, n * r / r.sum(), np.ones(n)] + soft_r)
+    fc = np.column_stack([(Y - mu) * k, m * c / c.sum(), -np.ones(m)] + soft_c)
     return np.vstack([fr, fc]), np.array([r.sum() / s, c.sum() / s])
 
 
@@ -151,16 +155,21 @@ def adam_step(P: dict, G: dict, M: dict, V: dict, step: int, lr: float, b1: floa
         P[k] = P[k] - lr * mh / (np.sqrt(vh) + eps)
 
 
-def targets(u, v, r, c, gamma: float):
-    """gamma (u_i - log r_i), gamma (v_j - log c_j); masses below 1e-12 times
-    their mean are floored there.  At the optimum e^{u_i} is the untransported
-    part r_i - (B1)_i of row i, so the target is gamma times the log of the
-    fraction of r_i left in place."""
-    r = np.asarray(r, dtype=np.float64)
-    c = np.asarray(c, dtype=np.float64)
-    br = np.log(np.maximum(r, 1e-12 * r.sum() / r.size))
-    bc = np.log(np.maximum(c, 1e-12 * c.sum() / c.size))
-    return np.concatenate([gamma * (np.asarray(u) - br), gamma * (np.asarray(v) - bc)])
+def targets(C, gamma: float, u, v, w: float):
+    """gamma log K_i = gamma (log sum_j B_ij - u_i) for rows and gamma (log
+    sum_i B_ij - v_j) for columns, B = B(u, v, w) of Section 2: the log of the
+    ratio of a point's transported mass to its slack e^{u_i} at the optimum,
+    where (B1)_i + e^{u_i} = r_i gives u_i = log r_i - softplus(log K_i)."""
+    from oracle import pot as O
+    L = O.log_gibbs(C, gamma, u, v, w)
+    lrow = np.array([_lse(L[i]) for i in range(L.shape[0])])
+    lcol = np.array([_lse(L[:, j]) for j in range(L.shape[1])])
+    return np.concatenate([gamma * (lrow - np.asarray(u)), gamma * (lcol - np.asarray(v))])
+
+
+def softplus(x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x > 0, x + np.log1p(np.exp(-np.abs(x))), np.log1p(np.exp(-np.abs(x))))
 
 
 def shift_step(C, gamma, r, c, s, u, v):
@@ -179,7 +188,8 @@ def shift_step(C, gamma, r, c, s, u, v):
 
 def warm_start(P: dict, X, Y, r, c, s, gamma: float, cost_scale: float = 0.0):
     """The network's start for one problem: features, forward pass,
-    u = y / gamma + log r, v = y / gamma + log c, then the shift step."""
+    u = log r - softplus(y / gamma), v = log c - softplus(y / gamma), then the
+    shift step."""
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
     n, m = X.shape[0], Y.shape[0]
@@ -187,7 +197,7 @@ def warm_start(P: dict, X, Y, r, c, s, gamma: float, cost_scale: float = 0.0):
     y, _ = forward(P, f, np.zeros(n + m, dtype=np.int64), e[None, :])
     br = np.log(np.maximum(r, 1e-12 * r.sum() / n))
     bc = np.log(np.maximum(c, 1e-12 * c.sum() / m))
-    u, v = y[:n] / gamma + br, y[n:] / gamma + bc
+    u, v = br - softplus(y[:n] / gamma), bc - softplus(y[n:] / gamma)
     D = np.array([((X[i][None, :] - Y) ** 2).sum(axis=1) for i in range(n)])
     cs = cost_scale if cost_scale > 0 else 1.0 / D.max()
     return shift_step(D * cs, gamma, np.asarray(r), np.asarray(c), s, u, v)

@@ -111,7 +111,7 @@ def lib() -> ct.CDLL:
         L.pot_ws_init.argtypes = [vp, i32, ct.c_uint64, vp]
         L.pot_ws_features_workspace_size.argtypes = [P, ct.POINTER(sz)]
         L.pot_ws_features.argtypes = [P, dbl, vp, sz, vp, vp, vp]
-        L.pot_ws_targets.argtypes = [P, dbl, vp, vp, vp, vp, sz, vp]
+        L.pot_ws_targets.argtypes = [P, dbl, vp, vp, dbl, vp, vp, sz, vp]
         L.pot_ws_workspace_size.argtypes = [WS, i32, ct.POINTER(sz)]
         L.pot_ws_forward.argtypes = [WS, vp, i32, vp, i32, vp, vp, sz, vp]
         L.pot_ws_gradient.argtypes = [WS, vp, i32, vp, i32, vp, vp, vp, sz, vp]

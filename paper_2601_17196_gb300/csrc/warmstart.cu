@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "../../include/warmstart.h"
+#include "common.cuh"
 #include "ws_common.cuh"
 
 namespace pot {
@@ -130,7 +131,9 @@ __global__ void ws_stats_kernel(int kind, const void* X, const void* Y, int64_t 
 }
 
 // Per point: centred, scaled coordinates, mass ratio, side, and the soft
-// minimum gamma (lrow_i - lu_i) from the pass at (lu, lv) = normalised log-masses.
+// minima T_t (lrow_t,i - lu_i) from the passes at (lu, lv) = normalised
+// log-masses and temperatures T_t = gamma 4^t (lrow, lcol hold POT_WS_TEMPS
+// consecutive vectors).
 __global__ void ws_feat_kernel(int kind, const void* X, const void* Y, int64_t ldx, int64_t ldy, int d,
                                int64_t n, int64_t m, const double* r, const double* c, double s, double sqcs,
                                double gamma, const double* stats, const double* lu, const double* lv,
@@ -148,7 +151,9 @@ __global__ void ws_feat_kernel(int kind, const void* X, const void* Y, int64_t l
     }
     feats[i * F + d] = row ? (float)((double)n * r[q] / sr) : (float)((double)m * c[q] / sc);
     feats[i * F + d + 1] = row ? 1.f : -1.f;
-    feats[i * F + d + 2] = (float)(gamma * (row ? lrow[q] - lu[q] : lcol[q] - lv[q]));
+    double T = gamma;
+    for (int t = 0; t < POT_WS_TEMPS; ++t, T *= 4.0)
+      feats[i * F + d + 2 + t] = (float)(T * (row ? lrow[t * n + q] - lu[q] : lcol[t * m + q] - lv[q]));
   }
   if (i == 0) {
     extra[0] = (float)(sr / s);
@@ -165,28 +170,28 @@ __global__ void ws_logmass_kernel(int64_t n, int64_t m, const double* r, const d
   else if (i < n + m) lv[i - n] = log(fmax(c[i - n], 1e-12 * sc / (double)m) / sc);
 }
 
-// Baseline of the network output: log r_i (rows) or log c_j (columns), the
-// value of u_i, v_j when nothing leaves the point (e^{u_i} = r_i - (B1)_i).
-// Masses below 1e-12 times the mean mass are floored there.
+// log r_i (rows) or log c_j (columns), masses below 1e-12 times their mean
+// floored there.
 __device__ __forceinline__ double ws_base(const double* r, const double* stats, int slot, int64_t cnt, int64_t i) {
   const double floor_ = 1e-12 * stats[slot] / (double)cnt;
   return log(fmax(r[i], floor_));
 }
 
-// target = gamma (u_i - log r_i), gamma (v_j - log c_j)
-__global__ void ws_targets_kernel(int64_t n, int64_t m, double gamma, const double* r, const double* c,
-                                  const double* stats, const double* u, const double* v, float* t) {
+// target = gamma log K: gamma (lrow_i - u_i) for rows, gamma (lcol_j - v_j) for
+// columns, with lrow, lcol the log-sums of B(u, v, w)
+__global__ void ws_targets_kernel(int64_t n, int64_t m, double gamma, const double* lrow, const double* lcol,
+                                  const double* u, const double* v, float* t) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) t[i] = (float)(gamma * (u[i] - ws_base(r, stats, POT_WS_MAX_D, n, i)));
-  else if (i < n + m) t[i] = (float)(gamma * (v[i - n] - ws_base(c, stats, POT_WS_MAX_D + 1, m, i - n)));
+  if (i < n) t[i] = (float)(gamma * (lrow[i] - u[i]));
+  else if (i < n + m) t[i] = (float)(gamma * (lcol[i - n] - v[i - n]));
 }
 
-// u_i = y_i / gamma + log r_i, v_j = y_j / gamma + log c_j
+// u_i = log r_i - softplus(y_i / gamma), v_j = log c_j - softplus(y_j / gamma)
 __global__ void ws_to_duals_kernel(int64_t n, int64_t m, double inv_gamma, const double* r, const double* c,
                                    const double* stats, const float* y, double* u, double* v) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) u[i] = (double)y[i] * inv_gamma + ws_base(r, stats, POT_WS_MAX_D, n, i);
-  else if (i < n + m) v[i - n] = (double)y[i] * inv_gamma + ws_base(c, stats, POT_WS_MAX_D + 1, m, i - n);
+  if (i < n) u[i] = ws_base(r, stats, POT_WS_MAX_D, n, i) - pot::softplus((double)y[i] * inv_gamma);
+  else if (i < n + m) v[i - n] = ws_base(c, stats, POT_WS_MAX_D + 1, m, i - n) - pot::softplus((double)y[i] * inv_gamma);
 }
 
 // Shift step of the warm start (one block): exact minimiser of
@@ -838,7 +843,7 @@ POT_API pot_status pot_ws_init(float* params, int32_t d, uint64_t seed, void* st
   return POT_OK;
 }
 
-// Features workspace: [solver scratch][stats 16][lu n][lv m][lrow n][lcol m]
+// Features workspace: [solver scratch][stats 16][lu n][lv m][lrow TEMPS n][lcol TEMPS m]
 static pot_status feat_layout(const pot_problem* prob, size_t* o_stats, size_t* o_lu, size_t* o_lv, size_t* o_lrow,
                               size_t* o_lcol, size_t* total) {
   pot_status s;
@@ -848,8 +853,8 @@ static pot_status feat_layout(const pot_problem* prob, size_t* o_stats, size_t* 
   *o_stats = x; x = al(x + sizeof(double) * 16);
   *o_lu = x; x = al(x + sizeof(double) * prob->n);
   *o_lv = x; x = al(x + sizeof(double) * prob->m);
-  *o_lrow = x; x = al(x + sizeof(double) * prob->n);
-  *o_lcol = x; x = al(x + sizeof(double) * prob->m);
+  *o_lrow = x; x = al(x + sizeof(double) * prob->n * POT_WS_TEMPS);
+  *o_lcol = x; x = al(x + sizeof(double) * prob->m * POT_WS_TEMPS);
   *total = x;
   return POT_OK;
 }
@@ -889,7 +894,10 @@ POT_API pot_status pot_ws_features(const pot_problem* prob, double gamma, void* 
   ws_stats_kernel<<<1, 1024, 0, st>>>(q.kind, q.X, q.Y, q.ldx, q.ldy, q.d, q.n, q.m, q.r, q.c, stats);
   ws_logmass_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(q.n, q.m, q.r, q.c, stats, lu, lv);
   WCKL();
-  if ((s = pot_marginals(&q, gamma, lu, lv, 0.0, base, o_stats, lrow, lcol, nullptr, stream)) != POT_OK) return s;
+  double T = gamma;
+  for (int t = 0; t < POT_WS_TEMPS; ++t, T *= 4.0)
+    if ((s = pot_marginals(&q, T, lu, lv, 0.0, base, o_stats, lrow + t * q.n, lcol + t * q.m, nullptr, stream)) != POT_OK)
+      return s;
   ws_feat_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(q.kind, q.X, q.Y, q.ldx, q.ldy, q.d, q.n, q.m, q.r,
                                                                q.c, q.s, sqrt(q.cost_scale), gamma, stats, lu, lv,
                                                                lrow, lcol, feats, extra);
@@ -897,19 +905,30 @@ POT_API pot_status pot_ws_features(const pot_problem* prob, double gamma, void* 
   return POT_OK;
 }
 
-POT_API pot_status pot_ws_targets(const pot_problem* prob, double gamma, const double* u, const double* v,
+POT_API pot_status pot_ws_targets(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
                                   float* target, void* workspace, size_t ws_bytes, void* stream) {
-  if (!prob || prob->n < 1 || prob->m < 1 || !prob->r || !prob->c)
-    return wfail(POT_EINVAL, "problem needs n, m >= 1 and device r, c");
+  pot_status s;
+  if ((s = check_points_problem(prob)) != POT_OK) return s;
   if (!(gamma > 0.0) || !isfinite(gamma)) return wfail(POT_EINVAL, "gamma must be finite and > 0");
+  if (!isfinite(w)) return wfail(POT_EINVAL, "w must be finite");
   if (!u || !v || !target) return wfail(POT_EINVAL, "u, v and target must be non-NULL");
-  if (!workspace || ws_bytes < 256) return wfail(POT_ENOMEM, "workspace needs 256 bytes");
-  cudaStream_t st = (cudaStream_t)stream;
-  double* stats = static_cast<double*>(workspace);
-  const int64_t n = prob->n, m = prob->m;
-  ws_mass_kernel<<<1, 1024, 0, st>>>(n, m, prob->r, prob->c, stats);
-  ws_targets_kernel<<<(unsigned)((n + m + 255) / 256), 256, 0, st>>>(n, m, gamma, prob->r, prob->c, stats, u, v,
-                                                                     target);
+  size_t o_stats, o_lu, o_lv, o_lrow, o_lcol, need;
+  if ((s = feat_layout(prob, &o_stats, &o_lu, &o_lv, &o_lrow, &o_lcol, &need)) != POT_OK) return s;
+  if (!workspace || ws_bytes < need) return wfail(POT_ENOMEM, "workspace too small (%zu < %zu)", ws_bytes, need);
+  char* base = static_cast<char*>(workspace);
+  if (((uintptr_t)base & 255) != 0) return wfail(POT_EINVAL, "workspace must be 256-byte aligned");
+  pot_problem q = *prob;
+  if (!(q.cost_scale > 0.0)) {
+    double mx = 0.0;
+    if ((s = pot_cost_max(prob, base, o_stats, &mx, stream)) != POT_OK) return s;
+    q.cost_scale = mx > 0.0 ? 1.0 / mx : 1.0;
+  }
+  double* lrow = reinterpret_cast<double*>(base + o_lrow);
+  double* lcol = reinterpret_cast<double*>(base + o_lcol);
+  if ((s = pot_marginals(&q, gamma, u, v, w, base, o_stats, lrow, lcol, nullptr, stream)) != POT_OK) return s;
+  const int64_t n = q.n, m = q.m;
+  ws_targets_kernel<<<(unsigned)((n + m + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, m, gamma, lrow, lcol, u,
+                                                                                        v, target);
   WCKL();
   return POT_OK;
 }

@@ -16,7 +16,7 @@ import torch
 from . import binding as B
 
 HIDDEN = 128
-EXTRA = 3          # features per point besides the coordinates
+EXTRA = 5          # features per point besides the coordinates
 MODE_FP32 = 0
 MODE_BF16 = 1
 
@@ -49,7 +49,7 @@ def offsets(d: int) -> dict:
 
 @dataclasses.dataclass
 class FeatureSet:
-    """Instances in feature form: ``feats`` [N][d+3], ``extra`` [K][2] and
+    """Instances in feature form: ``feats`` [N][d+5], ``extra`` [K][2] and
     ``target`` [N] on the device, ``off`` (K+1 point offsets) on the host."""
     d: int
     feats: torch.Tensor
@@ -111,21 +111,20 @@ def features(probs: Sequence[B.DeviceProblem], gamma: float) -> FeatureSet:
     return FeatureSet(d, feats, extra, off, None, np.asarray([p.n for p in probs], dtype=np.int64))
 
 
-_scratch = {}
-
-
 def targets_into(fs: FeatureSet, k: int, prob: B.DeviceProblem, gamma: float, u: torch.Tensor,
-                 v: torch.Tensor) -> None:
+                 v: torch.Tensor, w: float, ws: Optional[torch.Tensor] = None) -> None:
     """target[off[k]:off[k+1]] from the converged duals (pot_ws_targets)."""
     if fs.target is None:
         fs.target = torch.zeros(int(fs.off[-1]), dtype=torch.float32, device=fs.feats.device)
-    dev = fs.feats.device
-    if dev not in _scratch:
-        _scratch[dev] = _aligned(256, dev)
+    L = B.lib()
+    if ws is None:
+        b = ct.c_size_t(0)
+        B._check(L.pot_ws_features_workspace_size(ct.byref(prob.struct()), ct.byref(b)))
+        ws = _aligned(int(b.value), fs.feats.device)
     side, cur = B._stream()
-    B._check(B.lib().pot_ws_targets(ct.byref(prob.struct()), float(gamma), ct.c_void_p(u.data_ptr()),
-                                    ct.c_void_p(v.data_ptr()), ct.c_void_p(fs.target[int(fs.off[k]):].data_ptr()),
-                                    ct.c_void_p(_scratch[dev].data_ptr()), 256, ct.c_void_p(side.cuda_stream)))
+    B._check(L.pot_ws_targets(ct.byref(prob.struct()), float(gamma), ct.c_void_p(u.data_ptr()),
+                              ct.c_void_p(v.data_ptr()), float(w), ct.c_void_p(fs.target[int(fs.off[k]):].data_ptr()),
+                              ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(side.cuda_stream)))
     B._finish(side, cur)
 
 
@@ -135,12 +134,19 @@ def build_training_set(probs: Sequence[B.DeviceProblem], gamma: float, eps: floa
     ASPOT converges to (pot_ws_targets).  Returns (set, iterations array)."""
     fs = features(probs, gamma)
     iters = np.zeros(len(probs), dtype=np.int64)
+    L = B.lib()
+    ws = None
     for a in range(0, len(probs), batch):
         chunk = list(probs[a:a + batch])
         res = B.aspot_solve_batched(chunk, gamma, eps, max_iter=max_iter)
+        ws_w = torch.cat([r.plan.w for r in res]).cpu().numpy()
         for j, r in enumerate(res):
             iters[a + j] = r.iters
-            targets_into(fs, a + j, chunk[j], gamma, r.plan.u, r.plan.v)
+            b = ct.c_size_t(0)
+            B._check(L.pot_ws_features_workspace_size(ct.byref(chunk[j].struct()), ct.byref(b)))
+            if ws is None or ws.numel() < b.value:
+                ws = _aligned(int(b.value), fs.feats.device)
+            targets_into(fs, a + j, chunk[j], gamma, r.plan.u, r.plan.v, float(ws_w[j]), ws)
     return fs, iters
 
 
@@ -244,8 +250,8 @@ class WarmStartNet:
         return hist
 
     def warm_start(self, prob: B.DeviceProblem, gamma: float):
-        """(u0, v0, w0) for aspot_solve: network prediction / gamma + log r
-        (log c), then the exact w-step (pot_ws_warm_start)."""
+        """(u0, v0, w0) for aspot_solve: u0 = log r - softplus(y / gamma),
+        v0 likewise, then the shift step (pot_ws_warm_start)."""
         L = B.lib()
         b = ct.c_size_t(0)
         B._check(L.pot_ws_warm_workspace_size(ct.byref(prob.struct()), ct.byref(b)))

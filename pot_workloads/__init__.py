@@ -233,11 +233,11 @@ WS_HIDDEN = 128
 
 def ws_params(d: int = 2, seed: int = 0, bias_scale: float = 0.1) -> np.ndarray:
     """Flat FP32 parameter vector in the library's layout W1[H][F], b1[H],
-    W2[H][H], U[H][H+2], b2[H], w3[H], b3[1] (F = d + 3): weights
+    W2[H][H], U[H][H+2], b2[H], w3[H], b3[1] (F = d + 5): weights
     N(0, 1/fan_in), biases N(0, bias_scale^2) so that every block is
     exercised by a gradient check."""
     g = np.random.default_rng(seed)
-    H, F = WS_HIDDEN, d + 3
+    H, F = WS_HIDDEN, d + 5
     parts = [g.normal(0, 1 / np.sqrt(F), H * F), g.normal(0, bias_scale, H),
              g.normal(0, 1 / np.sqrt(H), H * H), g.normal(0, 1 / np.sqrt(H + 2), H * (H + 2)),
              g.normal(0, bias_scale, H), g.normal(0, 1 / np.sqrt(H), H), g.normal(0, bias_scale, 1)]
@@ -245,12 +245,12 @@ def ws_params(d: int = 2, seed: int = 0, bias_scale: float = 0.1) -> np.ndarray:
 
 
 def ws_batch(sizes, d: int = 2, seed: int = 0):
-    """Random feature sets: per instance `size` points with F = d + 3 features
-    (coordinates N(0, 0.3^2), weight ratio U[0.5, 1.5], side +-1, soft
-    minimum U[-0.5, 0]), extra inputs U[1, 2] and targets N(-0.05, 0.05^2).
+    """Random feature sets: per instance `size` points with F = d + 5 features
+    (coordinates N(0, 0.3^2), weight ratio U[0.5, 1.5], side +-1, three soft
+    minima U[-0.5, 0]), extra inputs U[1, 2] and targets N(-0.05, 0.05^2).
     Returns (feats [N][F] f32, extra [K][2] f32, target [N] f32, off [K+1] int64)."""
     g = np.random.default_rng(seed)
-    F = d + 3
+    F = d + 5
     off = np.zeros(len(sizes) + 1, dtype=np.int64)
     off[1:] = np.cumsum(sizes)
     N = int(off[-1])
@@ -258,7 +258,7 @@ def ws_batch(sizes, d: int = 2, seed: int = 0):
     feats[:, :d] = g.normal(0, 0.3, size=(N, d))
     feats[:, d] = g.uniform(0.5, 1.5, size=N)
     feats[:, d + 1] = np.where(g.uniform(size=N) < 0.5, 1.0, -1.0)
-    feats[:, d + 2] = g.uniform(-0.5, 0.0, size=N)
+    feats[:, d + 2:] = g.uniform(-0.5, 0.0, size=(N, 3))
     extra = g.uniform(1.0, 2.0, size=(len(sizes), 2)).astype(np.float32)
     target = g.normal(-0.05, 0.05, size=N).astype(np.float32)
     return feats, extra, target, off

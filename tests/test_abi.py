@@ -79,7 +79,7 @@ def test_warm_start_argument_checks(libpath):
     n = ct.c_int64(0)
     assert L.pot_ws_param_count(0, ct.byref(n)) == 1
     assert L.pot_ws_param_count(2, ct.byref(n)) == 0
-    H, F = 128, 5
+    H, F = 128, 7
     assert n.value == H * F + H + H * H + H * (H + 2) + H + H + 1
     s = B._WsSet()
     off = np.array([0, 5, 5], dtype=np.int64)          # second instance empty

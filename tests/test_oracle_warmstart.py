@@ -25,7 +25,7 @@ def test_backward_matches_finite_differences():
     P = WS.init_params(1)
     # two instances of different sizes, all four feature kinds
     seg = np.array([0] * 5 + [1] * 7)
-    feats = rng.normal(size=(12, 5))
+    feats = rng.normal(size=(12, 7))
     extra = rng.uniform(1, 2, size=(2, 2))
     target = rng.normal(size=12)
     y, cache = WS.forward(P, feats, seg, extra)
@@ -47,7 +47,7 @@ def test_backward_matches_finite_differences():
 def test_context_is_the_instance_mean():
     P = WS.init_params(2)
     rng = np.random.default_rng(3)
-    feats = rng.normal(size=(6, 5))
+    feats = rng.normal(size=(6, 7))
     seg = np.array([0, 0, 0, 1, 1, 1])
     extra = np.ones((2, 2))
     # permuting points inside an instance permutes the outputs the same way
@@ -69,10 +69,11 @@ def test_features_hand_example_and_invariances():
     np.testing.assert_allclose(f[:, 0], [-0.5, 0.0, 0.5])
     np.testing.assert_allclose(f[:, 1], [2 * 0.25, 2 * 0.75, 1.0])
     np.testing.assert_allclose(f[:, 2], [1, 1, -1])
-    # one column: a row's soft minimum is its cost to that column
-    np.testing.assert_allclose(f[:2, 3], [-1.0, -0.25], rtol=1e-14)
-    col = g * math.log(0.25 * math.exp(-1.0 / g) + 0.75 * math.exp(-0.25 / g))
-    assert f[2, 3] == pytest.approx(col, rel=1e-13)
+    # one column: a row's soft minimum is its cost to that column at every temperature
+    for t, T in enumerate((g, 4 * g, 16 * g)):
+        np.testing.assert_allclose(f[:2, 3 + t], [-1.0, -0.25], rtol=1e-13)
+        col = T * math.log(0.25 * math.exp(-1.0 / T) + 0.75 * math.exp(-0.25 / T))
+        assert f[2, 3 + t] == pytest.approx(col, rel=1e-13)
     np.testing.assert_allclose(e, [2.0, 3.0])
     # translating both clouds or scaling them leaves the features unchanged
     rng = np.random.default_rng(0)
@@ -86,8 +87,12 @@ def test_features_hand_example_and_invariances():
     # the soft minimum lies between the smallest cost and the mass-weighted mean cost
     C = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
     C = C / C.max()
-    assert np.all(f0[:7, 4] >= -C.max(axis=1) - 1e-12) and np.all(f0[:7, 4] <= -C.min(axis=1) + 1e-12)
-    assert np.all(f0[:7, 4] >= -(C * (c / c.sum())).sum(axis=1) - 1e-12)   # Jensen
+    for t in range(3):
+        sm = f0[:7, 4 + t]
+        assert np.all(sm >= -C.max(axis=1) - 1e-12) and np.all(sm <= -C.min(axis=1) + 1e-12)
+        assert np.all(sm >= -(C * (c / c.sum())).sum(axis=1) - 1e-12)   # Jensen
+    # a higher temperature gives a softer (lower) minimum
+    assert np.all(f0[:7, 5] <= f0[:7, 4] + 1e-12) and np.all(f0[:7, 6] <= f0[:7, 5] + 1e-12)
     # an explicit cost scale is used as given
     f3, _ = WS.features(X, Y, r, c, 0.3, 0.05, cost_scale=4.0)
     mu = np.vstack([X, Y]).mean(axis=0)
@@ -107,7 +112,7 @@ def test_adam_first_step_is_lr_times_sign():
 def test_flat_layout_round_trip():
     P = WS.init_params(4, d=3)
     flat = WS.flatten(P)
-    assert flat.size == 128 * 6 + 128 + 128 * 128 + 128 * 130 + 128 + 128 + 1
+    assert flat.size == 128 * 8 + 128 + 128 * 128 + 128 * 130 + 128 + 128 + 1
     Q = WS.unflatten(flat, 3)
     for k in P:
         np.testing.assert_array_equal(Q[k], P[k])
@@ -135,3 +140,23 @@ def test_shift_step_zeroes_the_three_shift_derivatives():
     np.testing.assert_allclose(u2, u1, atol=1e-12)
     np.testing.assert_allclose(v2, v1, atol=1e-12)
     assert w2 == pytest.approx(w1, abs=1e-12)
+
+
+def test_targets_invert_the_start_at_the_optimum():
+    """At the entropic optimum (B1)_i + e^{u_i} = r_i, so u_i = log r_i -
+    softplus(log K_i): the start formula recovers the duals from the targets."""
+    from oracle import pot as O
+    import pot_workloads as W
+    pb = W.tiny(3, n=6, m=5, mass_r=1.1, mass_c=1.4, s=0.8)
+    C = np.asarray(pb.C, dtype=np.float64)
+    res = O.aspot(C, pb.r, pb.c, pb.s, 1e-9, 0.1, max_iter=200000, smooth=False, stop_raw_eps=True)
+    z = res.z
+    t = WS.targets(C, 0.1, z.u, z.v, z.w)
+    u = np.log(pb.r) - WS.softplus(t[:6] / 0.1)
+    v = np.log(pb.c) - WS.softplus(t[6:] / 0.1)
+    np.testing.assert_allclose(u, z.u, atol=1e-6)
+    np.testing.assert_allclose(v, z.v, atol=1e-6)
+    # softplus closed forms
+    assert WS.softplus(0.0) == pytest.approx(math.log(2.0))
+    assert WS.softplus(-50.0) == pytest.approx(math.exp(-50.0), rel=1e-12)
+    assert WS.softplus(50.0) == pytest.approx(50.0, rel=1e-15)
