@@ -347,6 +347,21 @@ __global__ void clear_parts_kernel(float2* a, int64_t cnt, const int* done) {
 
 __host__ __device__ __forceinline__ int64_t dense_owner(int64_t u, int64_t G, int64_t U) { return ((u + 1) * G - 1) / U; }
 
+// Per-warp shared-memory ring of cost chunks filled with cp.async (16 bytes
+// per lane and copy); kDStages chunks of 4 rows x 256 columns per warp, so
+// kDStages - 1 loads are in flight while one chunk is reduced.  Each lane
+// reads back exactly the 16-byte slots it copied, so the ring needs no
+// synchronisation beyond the lane's own cp.async.wait_group.
+constexpr int kDStages = 3;
+constexpr size_t kDenseRingBytes = (size_t)kWarps * kDStages * 4 * 256 * sizeof(float);
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_ring() { asm volatile("cp.async.wait_group %0;" ::"n"(kDStages - 1) : "memory"); }
+
 template <int MODE>   // 0: rows + columns, 1: rows, 2: columns
 __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, SimtLayout DL) {
   if (P.done && *P.done) return;
@@ -354,6 +369,8 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ float sS[kWarps][256];
   __shared__ float sM[kWarps][256];
+  extern __shared__ float4 dring[];                      // [kWarps][kDStages][4 rows][64]
+  float4* ring = dring + (size_t)warp * kDStages * 4 * 64;
   const float g2 = (float)(P.gC * kL2E);
   const unsigned long long NG = pk2(-g2, -g2);
   // persistent: CTA c owns units [c U / G, (c+1) U / G) of the panel-major
@@ -387,24 +404,41 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
 #pragma unroll
   for (int q = 0; q < 8; ++q) { cM[q] = POT_NEG_BIGF; cS[q] = 0.f; }
 
-  // chunk c of this warp: rows row0 + 32 c + 4 warp + r
-  float4 cur[4][2], nxt[4][2];
-  auto load_chunk = [&](int64_t base, float4 (&dst)[4][2]) {
+  // chunk ci of this warp: rows row0 + 4 warp + 32 ci + r, in ring stage ci % kDStages
+  auto issue = [&](int64_t b, int st) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int64_t i = base + r;
+      const int64_t i = b + r;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        if (i < rend && gv[k]) dst[r][k] = __ldg(reinterpret_cast<const float4*>(P.C + i * P.ldc + col0 + 128 * k + 4 * lane));
-        else dst[r][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4* dst = ring + (st * 4 + r) * 64 + k * 32 + lane;
+        if (i < rend && gv[k]) cp_async16(dst, P.C + i * P.ldc + col0 + 128 * k + 4 * lane);
+        else *dst = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+    cp_commit();
   };
-  int64_t base = row0 + 4 * warp;
-  if (base < rend) load_chunk(base, cur);
-  for (; base < rend; base += 32) {
-    const int64_t nb = base + 32;
-    if (nb < rend) load_chunk(nb, nxt);
+  const int64_t first = row0 + 4 * warp;
+  const int64_t nchunks = first < rend ? (rend - first + 31) / 32 : 0;
+#pragma unroll
+  for (int st = 0; st < kDStages - 1; ++st) {
+    if (st < nchunks) issue(first + 32 * st, st);
+    else cp_commit();
+  }
+  for (int64_t ci = 0; ci < nchunks; ++ci) {
+    const int64_t base = first + 32 * ci;
+    const int64_t nci = ci + kDStages - 1;
+    if (nci < nchunks) issue(first + 32 * nci, (int)(nci % kDStages));
+    else cp_commit();
+    cp_wait_ring();                                      // chunk ci has landed
+    float4 cur[4][2];
+    {
+      const int st = (int)(ci % kDStages);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) cur[r][k] = ring[(st * 4 + r) * 64 + k * 32 + lane];
+    }
     // logits of the 4 x 8 entries
     float lg[4][8];
 #pragma unroll
@@ -463,8 +497,6 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
         }
       }
     }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) { cur[r][0] = nxt[r][0]; cur[r][1] = nxt[r][1]; }
   }
   if (COLS) {
 #pragma unroll
@@ -514,9 +546,19 @@ void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
       clear_parts_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(P.col_part, cnt, P.done);
     }
     const unsigned grid = (unsigned)L.G;
-    if ((P.mode & PASS_ROWS) && (P.mode & PASS_COLS)) dense_pass_kernel<0><<<grid, kThreads, 0, st>>>(P, L);
-    else if (P.mode & PASS_ROWS) dense_pass_kernel<1><<<grid, kThreads, 0, st>>>(P, L);
-    else dense_pass_kernel<2><<<grid, kThreads, 0, st>>>(P, L);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(dense_pass_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseRingBytes);
+      cudaFuncSetAttribute(dense_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseRingBytes);
+      cudaFuncSetAttribute(dense_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseRingBytes);
+      cudaFuncSetAttribute(dense_pass_kernel<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(dense_pass_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(dense_pass_kernel<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      attr_set = true;
+    }
+    if ((P.mode & PASS_ROWS) && (P.mode & PASS_COLS)) dense_pass_kernel<0><<<grid, kThreads, kDenseRingBytes, st>>>(P, L);
+    else if (P.mode & PASS_ROWS) dense_pass_kernel<1><<<grid, kThreads, kDenseRingBytes, st>>>(P, L);
+    else dense_pass_kernel<2><<<grid, kThreads, kDenseRingBytes, st>>>(P, L);
     return;
   }
   if (KIND == COST_DENSE_F32) {
