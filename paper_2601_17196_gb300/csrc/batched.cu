@@ -293,9 +293,11 @@ __global__ void b_after_final_kernel(BVecs V, int k) {
     V.uo[g] = uz;
     const double un = (k == 0) ? V.lrt[g] - softplus(R - uz) : uz;
     V.uc[g] = un;
-    v[2] += (k == 0) ? -un * V.rt[g] : sexp(un) - un * V.rt[g];
+    v[2] += (k == 0) ? -un * V.rt[g] : eu - un * V.rt[g];     // un = uz unless k = 0
     if (!isfinite(R) && R != POT_NEG_BIG) v[3] = 1.0;
-    if (R > acc) { ssum = ssum * exp(acc - R) + 1.0; acc = R; } else ssum += exp(R - acc);
+    if (k == 2) {                       // log |B|_1 is needed by the w step only
+      if (R > acc) { ssum = ssum * exp(acc - R) + 1.0; acc = R; } else ssum += exp(R - acc);
+    }
   }
   for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
     const int64_t g = I.col0 + j;
@@ -307,11 +309,11 @@ __global__ void b_after_final_kernel(BVecs V, int k) {
     V.vo[g] = vz;
     const double vn = (k == 1) ? V.lct[g] - softplus(Cc - vz) : vz;
     V.vc[g] = vn;
-    v[2] += (k == 1) ? -vn * V.ct[g] : sexp(vn) - vn * V.ct[g];
+    v[2] += (k == 1) ? -vn * V.ct[g] : ev - vn * V.ct[g];     // vn = vz unless k = 1
     if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[3] = 1.0;
   }
   block_sums<4>(v);
-  const double lt = block_lse(acc > -INFINITY ? acc + log(ssum) : POT_NEG_BIG, acc > -INFINITY);
+  const double lt = (k == 2) ? block_lse(acc > -INFINITY ? acc + log(ssum) : POT_NEG_BIG, acc > -INFINITY) : 0.0;
   if (threadIdx.x == 0) {
     const double s = I.s;
     const double E = fabs(v[1] - s) + v[0];

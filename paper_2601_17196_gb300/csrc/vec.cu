@@ -150,21 +150,27 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   sm = warp_sum_d(sm);
   if (lane == 0) { smx[warp] = mx; ssm[warp] = sm; }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
+    // block (max, sum) of the NW warp partials: one exp per lane, not a serial chain
+    const double wm = (lane < NW && ssm[lane] > 0.0) ? smx[lane] : -INFINITY;
+    double bm = wm;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double a = 0.0;
-      for (int w = 0; w < NW; ++w) a += sh[k][w];
-      part[(int64_t)blockIdx.x * NP + k] = a;
+    for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    double bs = (wm > -INFINITY) ? ssm[lane] * exp(wm - bm) : 0.0;
+    bs = warp_sum_d(bs);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double a = 0.0;
+        for (int w = 0; w < NW; ++w) a += sh[k][w];
+        part[(int64_t)blockIdx.x * NP + k] = a;
+      }
+      part[(int64_t)blockIdx.x * NP + NV] = bs > 0.0 ? bm : -INFINITY;
+      part[(int64_t)blockIdx.x * NP + NV + 1] = bs;
+      __threadfence();
+      const unsigned prev = atomicAdd(counter, 1u);
+      amlast = (prev == gridDim.x - 1);
     }
-    Lse l;
-    l.init();
-    for (int w = 0; w < NW; ++w) if (ssm[w] > 0.0) l.add(smx[w], ssm[w]);
-    part[(int64_t)blockIdx.x * NP + NV] = l.m;
-    part[(int64_t)blockIdx.x * NP + NV + 1] = l.s;
-    __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
-    amlast = (prev == gridDim.x - 1);
   }
   __syncthreads();
   if (!amlast) return false;
@@ -175,14 +181,29 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
     a = warp_sum_d(a);
     if (lane == 0) st[warp] = a;
   }
-  if (threadIdx.x == 32 * NW - 1) {
-    Lse l;
-    l.init();
-    for (int b2 = 0; b2 < (int)gridDim.x; ++b2) {
+  // grid log-sum-exp of the block partials, in parallel over the block's threads
+  double gm = -INFINITY;
+  for (int b2 = threadIdx.x; b2 < (int)gridDim.x; b2 += blockDim.x)
+    if (__ldcg(part + (int64_t)b2 * NP + NV + 1) > 0.0) gm = fmax(gm, __ldcg(part + (int64_t)b2 * NP + NV));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  if (lane == 0) smx[warp] = gm;
+  __syncthreads();
+  gm = -INFINITY;
+  for (int w = 0; w < NW; ++w) gm = fmax(gm, smx[w]);
+  double gs = 0.0;
+  if (gm > -INFINITY)
+    for (int b2 = threadIdx.x; b2 < (int)gridDim.x; b2 += blockDim.x) {
       const double ss = __ldcg(part + (int64_t)b2 * NP + NV + 1);
-      if (ss > 0.0) l.add(__ldcg(part + (int64_t)b2 * NP + NV), ss);
+      if (ss > 0.0) gs += ss * exp(__ldcg(part + (int64_t)b2 * NP + NV) - gm);
     }
-    slse = l.value();
+  gs = warp_sum_d(gs);
+  if (lane == 0) ssm[warp] = gs;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < NW; ++w) a += ssm[w];
+    slse = (gm > -INFINITY && a > 0.0) ? gm + log(a) : POT_NEG_BIG;
   }
   __syncthreads();
 #pragma unroll
@@ -403,14 +424,14 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     const double uz = take ? uz_hat[t] : V.uc[t];
     const double R = V.lrow[t];
     xr = R;
-    act = true;
+    act = k == 2;                      // log |B|_1 is needed by the w step only
     const double rB = safe_exp(R), eu = safe_exp(uz);
     v[0] = fabs(rB + eu - V.rt[t]);
     v[1] = rB;
     V.uo[t] = uz;
     const double un = (k == 0) ? V.lrt[t] - softplus(R - uz) : uz;
     V.uc[t] = un;
-    v[2] = (k == 0) ? -un * V.rt[t] : safe_exp(un) - un * V.rt[t];
+    v[2] = (k == 0) ? -un * V.rt[t] : eu - un * V.rt[t];    // un = uz unless k = 0
     if (!isfinite(R) && R != POT_NEG_BIG) v[3] = 1;
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
@@ -421,7 +442,7 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     V.vo[j] = vz;
     const double vn = (k == 1) ? V.lct[j] - softplus(Cc - vz) : vz;
     V.vc[j] = vn;
-    v[2] = (k == 1) ? -vn * V.ct[j] : safe_exp(vn) - vn * V.ct[j];
+    v[2] = (k == 1) ? -vn * V.ct[j] : ev - vn * V.ct[j];    // vn = vz unless k = 1
     if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[3] = 1;
   }
   double tot[4], ltot = 0.0;
