@@ -45,10 +45,13 @@ def _args():
     ap.add_argument("--mode", default="solve", choices=["solve", "pass"],
                     help="'pass': time only the fused row+column pass (for ncu captures of that kernel)")
     ap.add_argument("--workload", default="cloud_32k",
-                    choices=["cloud_32k", "dense_4096", "scaling_e4", "batch_3d", "warmstart"],
+                    choices=["cloud_32k", "dense_4096", "scaling_e4", "batch_3d", "warmstart", "small_dense",
+                             "registration"],
                     help="cloud_32k: the headline line; dense_4096: the FP32 dense-cost path (gamma sweep, "
                          "HBM roofline of the CUDA-core pass); scaling_e4: the appendix's runtime-vs-n study; "
-                         "batch_3d: 512 uneven 3-D instances; warmstart: the learned warm start (train + held-out)")
+                         "batch_3d: 512 uneven 3-D instances; warmstart: the learned warm start (train + held-out); "
+                         "small_dense: the 256-point configuration with the tuned-gamma Sinkhorn p sweep; "
+                         "registration: batched rigid registration of 64 partial 3-D clouds")
     ap.add_argument("--ws-train", type=int, default=20000, help="warmstart: training instances")
     ap.add_argument("--ws-eval", type=int, default=1000, help="warmstart: held-out seeds")
     ap.add_argument("--ws-epochs", type=int, default=12, help="warmstart: training epochs")
@@ -438,6 +441,91 @@ def run_batched(args):
           flush=True)
 
 
+def run_small(args):
+    """The 256-point configuration (X ~ U[0,1]^2, Y ~ N((.5,.5), 0.1^2 I),
+    masses 1.0 / 1.2, s = 0.8, gamma = 0.05, eps = 1e-3, dense FP32 cost):
+    ASPOT and the feasible Sinkhorn baseline to their thresholds, and the
+    tuned-gamma Sinkhorn of Theorem 2 for p in {1, 1.5, 2, 3, 4} (gamma =
+    (2 eps / (49 H_min))^(1/p), eps' = H_min gamma^p), iterations, time to
+    epsilon and <C, X>; the FP64 oracle's ASPOT on the same instance beside it."""
+    import torch
+    import paper_2601_17196_gb300 as pkg
+    import pot_workloads as W
+    from oracle import pot as O
+    pb = W.small_dense(0)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    stream = torch.cuda.Stream()
+    rows = []
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / args.steps
+
+    r, ms = timed(lambda: pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter))
+    rows.append({"solver": "aspot", "gamma": r.gamma, "iters": r.iters, "time_to_eps_ms": ms,
+                 "objective": r.objective, "converged": r.status == 0})
+    r, ms = timed(lambda: pkg.sinkhorn_pot_solve(dp, pb.gamma, pb.eps, max_iter=200000))
+    rows.append({"solver": "sinkhorn", "gamma": r.gamma, "iters": r.iters, "time_to_eps_ms": ms,
+                 "objective": r.objective, "converged": r.status == 0})
+    for p in (1.0, 1.5, 2.0, 3.0, 4.0):
+        r, ms = timed(lambda: pkg.sinkhorn_pot_solve(dp, 0.0, pb.eps, max_iter=200000, p_tune=p))
+        rows.append({"solver": f"tuned sinkhorn p={p}", "gamma": r.gamma, "eps_prime": r.eps_stop, "iters": r.iters,
+                     "time_to_eps_ms": ms, "objective": r.objective, "converged": r.status == 0})
+    t0 = time.time()
+    C = O.sqeuclid_cost(pb.X, pb.Y, pb.cost_scale) if pb.C is None else pb.C.astype("float64")
+    ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma)
+    cpu_ms = (time.time() - t0) * 1e3
+    print(json.dumps({"workload": "small_dense n=m=256 gamma=0.05 eps=1e-3 (masses 1.0/1.2, s=0.8)", "rows": rows,
+                      "oracle_aspot": {"iters": ora.iters, "ms": cpu_ms, "objective": ora.objective, "cores": 1,
+                                       "kind": "oracle"},
+                      "objective_rel_diff_gpu_vs_oracle": abs(rows[0]["objective"] - ora.objective) / ora.objective}),
+          flush=True)
+
+
+def run_registration(args):
+    """Batched rigid registration (appendix, point cloud registration) of 64
+    synthetic partial clouds: target n = 1024 points on three ellipsoid
+    surfaces, source = half of it moved by up to 0.25 rad and 0.08, alpha =
+    0.6, gamma 0.02 annealed by 0.83 to 0.002, eps = 1e-3; every outer step is
+    one batched ASPOT solve of the pairs still moving plus the plan-moment /
+    Procrustes kernel."""
+    import numpy as np
+    import torch
+    from paper_2601_17196_gb300 import registration as PR
+    import pot_workloads as W
+    K = 64
+    pairs, truth = [], []
+    for seed in range(K):
+        X, Y0, Rt, tt = W.registration_3d(seed, n=1024, frac=0.5, max_angle=0.25, max_shift=0.08)
+        pairs.append((X, Y0))
+        truth.append((Rt, tt))
+    PR.register_batched(pairs[:2], alpha=0.6, max_reg=2)          # warm-up (build, caches)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    out = PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=40)
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    err = np.array([max(np.abs(r.R - Rt).max(), np.abs(r.t - tt).max()) for r, (Rt, tt) in zip(out, truth)])
+    regs = np.array([r.registrations for r in out])
+    inner = np.array([r.inner_iterations for r in out])
+    print(json.dumps({"workload": "registration: 64 pairs, target n=1024 (3 ellipsoid surfaces), source = half, "
+                                  "<=0.25 rad, <=0.08 shift, alpha=0.6, gamma 0.02*0.83^k >= 0.002, eps=1e-3",
+                      "wall_s": wall, "pairs": K, "registrations_mean": float(regs.mean()),
+                      "registrations_max": int(regs.max()), "aspot_iters_per_registration": float(inner.sum() / regs.sum()),
+                      "converged_pairs": int(sum(r.converged for r in out)),
+                      "motion_error_median": float(np.median(err)), "motion_error_p90": float(np.quantile(err, 0.9)),
+                      "pairs_within_0.06": int((err < 0.06).sum())}), flush=True)
+
+
 def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batch: int = 32, lr: float = 3e-3,
                      device="cuda") -> dict:
     """Learned warm start on the 2-D mixture workload (n = m = 1024, 2-6
@@ -513,6 +601,12 @@ def main():
     args = _args()
     if args.workload == "warmstart":
         run_warmstart(args)
+        return
+    if args.workload == "small_dense":
+        run_small(args)
+        return
+    if args.workload == "registration":
+        run_registration(args)
         return
     if args.mode == "pass":
         run_pass_only(args)

@@ -36,7 +36,8 @@ EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_roun
             "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "pot_workspace_size_batched",
             "aspot_solve_batched", "pot_marginals_static", "pot_ws_param_count", "pot_ws_init",
             "pot_ws_features_workspace_size", "pot_ws_features", "pot_ws_targets", "pot_ws_workspace_size", "pot_ws_forward", "pot_ws_gradient",
-            "pot_ws_train_step", "pot_ws_warm_workspace_size", "pot_ws_warm_start", "pot_last_error"]
+            "pot_ws_train_step", "pot_ws_warm_workspace_size", "pot_ws_warm_start", "pot_rigid_workspace_size",
+            "pot_rigid_fit", "pot_rigid_apply", "pot_last_error"]
 
 
 class PotError(RuntimeError):
@@ -118,6 +119,9 @@ def lib() -> ct.CDLL:
         L.pot_ws_train_step.argtypes = [WS, vp, i32, vp, vp, vp, AD, i64, i32, vp, vp, sz, vp]
         L.pot_ws_warm_workspace_size.argtypes = [P, ct.POINTER(sz)]
         L.pot_ws_warm_start.argtypes = [P, dbl, vp, i32, i32, vp, vp, ct.POINTER(dbl), vp, sz, vp]
+        L.pot_rigid_workspace_size.argtypes = [i32, ct.POINTER(sz)]
+        L.pot_rigid_fit.argtypes = [P, i32, PL, dbl, vp, vp, vp, sz, vp]
+        L.pot_rigid_apply.argtypes = [P, i32, vp, vp, vp, sz, vp]
         L.pot_last_error.restype = ct.c_char_p
         for name in EXPORTED[:-1]:
             getattr(L, name).restype = ct.c_int

@@ -262,3 +262,53 @@ def ws_batch(sizes, d: int = 2, seed: int = 0):
     extra = g.uniform(1.0, 2.0, size=(len(sizes), 2)).astype(np.float32)
     target = g.normal(-0.05, 0.05, size=N).astype(np.float32)
     return feats, extra, target, off
+
+
+def registration_3d(seed: int = 0, n: int = 1024, frac: float = 0.5, max_angle: float = 0.5,
+                    max_shift: float = 0.1, noise: float = 0.0):
+    """A target cloud and a misaligned partial source (stand-in for the 3-D
+    registration clouds of Section 4.2): the target is n points on three
+    random ellipsoid surfaces in [0.15, 0.85]^3; the source is a fraction
+    `frac` of it (one contiguous half-space side, so the overlap is partial),
+    moved by a random rotation of angle <= max_angle about a random axis and a
+    shift of norm <= max_shift, plus Gaussian noise.  Returns
+    (X [n,3], Y0 [m,3], R_true, t_true) with R_true Y0 + t_true = the chosen
+    target points (before noise)."""
+    g = np.random.default_rng(seed)
+    k = 3
+    centres = g.uniform(0.35, 0.65, size=(k, 3))
+    radii = g.uniform(0.08, 0.2, size=(k, 3))
+    lab = g.integers(0, k, size=n)
+    dirs = g.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    X = centres[lab] + dirs * radii[lab]
+    normal = g.normal(size=3)
+    normal /= np.linalg.norm(normal)
+    proj = (X - X.mean(axis=0)) @ normal
+    keep = np.argsort(proj)[: int(round(frac * n))]
+    axis = g.normal(size=3)
+    axis /= np.linalg.norm(axis)
+    angle = g.uniform(0.3, 1.0) * max_angle
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    R_true = np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * K @ K
+    shift = g.normal(size=3)
+    t_true = shift / np.linalg.norm(shift) * g.uniform(0.3, 1.0) * max_shift
+    # R_true y0 + t_true = x  =>  y0 = R_true^T (x - t_true)
+    Y0 = (X[keep] - t_true) @ R_true
+    if noise > 0:
+        Y0 = Y0 + g.normal(scale=noise, size=Y0.shape)
+    X = X.astype(np.float32).astype(np.float64)
+    Y0 = Y0.astype(np.float32).astype(np.float64)
+    return X, Y0, R_true, t_true
+
+
+def plan_params(n: int, m: int, seed: int = 0, gamma: float = 0.05):
+    """Random implicit-plan parameters (f, g, p, q, kappa) for checks of plan
+    moment kernels: f, g ~ U[-2, 0] + log(1/n), p, q ~ U[0, 1/n], kappa
+    U[0.5, 2]."""
+    g = np.random.default_rng(seed)
+    f = g.uniform(-2.0, 0.0, size=n) + np.log(1.0 / n)
+    gg = g.uniform(-2.0, 0.0, size=m) + np.log(1.0 / m)
+    p = g.uniform(0.0, 1.0 / n, size=n)
+    q = g.uniform(0.0, 1.0 / m, size=m)
+    return f, gg, p, q, float(g.uniform(0.5, 2.0))
