@@ -222,9 +222,9 @@ PassDesc base_desc(const Ctx& X, double gamma) {
   return d;
 }
 
-pot_status run_pass(Ctx& X, const PassDesc& d) {
+pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (X.prof && X.in_loop) {
+  if (X.prof && X.in_loop && profile) {
     const size_t need = 2 * (size_t)(X.pass_ord + 1);
     while (X.ev.size() < need) {
       cudaEvent_t e;
@@ -251,7 +251,7 @@ pot_status run_pass(Ctx& X, const PassDesc& d) {
   if (e1) CK(cudaEventRecordWithFlags(e1, X.st, cudaEventRecordExternal));
   if (d.mode & (PASS_ROWS | PASS_COLS)) {
     launch_combine(X.rowp, X.L.ncolblk, d.n, (d.mode & PASS_ROWS) ? X.lrow : nullptr, X.colp, X.L.nrowblk, d.m,
-                   (d.mode & PASS_COLS) ? X.lcol : nullptr, d.done, X.st);
+                   (d.mode & PASS_COLS) ? X.lcol : nullptr, d.done, X.st, d.skip, d.skip_if);
     X.launches += 1;
   }
   CKL();
@@ -336,8 +336,9 @@ pot_status read_state(Ctx& X, DevState& h) {
 // Run `body` (one iteration per call, k = iteration index mod 3) until the
 // device stop flag is set.  With a capturable stream the iterations are
 // captured into a CUDA graph of `per` iterations.
-template <class Body>
-pot_status drive(Ctx& X, int per, int max_iter, int passes_per_iter, Body body) {
+// passes_per_iter(k): timed passes of an iteration with block k
+template <class Body, class PassesPerIter>
+pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, Body body) {
   cudaStreamCaptureStatus cs;
   CK(cudaStreamIsCapturing(X.st, &cs));
   if (cs != cudaStreamCaptureStatusNone) return fail(POT_EINVAL, "the stream is being captured");
@@ -384,7 +385,9 @@ pot_status drive(Ctx& X, int per, int max_iter, int passes_per_iter, Body body) 
     if (X.prof) {
       // passes of the iterations that ran in this launch (later ones returned at once)
       const int ran = std::min(flags3[0] - t_prev, per);
-      const int npass = std::min<int>(ran * passes_per_iter, (int)X.ev.size() / 2);
+      int npass = 0;
+      for (int it = 0; it < ran; ++it) npass += passes_per_iter(it % 3);
+      npass = std::min<int>(npass, (int)X.ev.size() / 2);
       for (int k = 0; k < npass; ++k) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, X.ev[2 * k], X.ev[2 * k + 1]) == cudaSuccess) { X.pass_ms += ms; X.pass_count++; }
@@ -555,24 +558,40 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
     p1.mode = PASS_ROWS | PASS_COLS; p1.arow0 = V.ub; p1.bcol0 = V.vb; p1.aoff0 = &X.S->w_bar; p1.done = &X.S->done;
     if ((q = run_pass(X, p1)) != POT_OK) return q;
     launch_aspot_after_grad(V, X.st); X.launches += 1;
-    PassDesc p2 = d;                       // Greenkhorn pass at z_grave (one side)
-    p2.mode = (k == 1) ? PASS_COLS : PASS_ROWS; p2.arow0 = V.ug; p2.bcol0 = V.vg; p2.aoff0 = &X.S->w_grave;
+    // Greenkhorn pass at z_grave: the side of block k (both sides for the w-step,
+    // whose column sums give those of z^ in closed form)
+    PassDesc p2 = d;
+    p2.mode = (k == 1) ? PASS_COLS : (k == 2 ? (PASS_ROWS | PASS_COLS) : PASS_ROWS);
+    p2.arow0 = V.ug; p2.bcol0 = V.vg; p2.aoff0 = &X.S->w_grave;
     p2.done = &X.S->done;
     if ((q = run_pass(X, p2)) != POT_OK) return q;
     launch_aspot_after_greenkhorn(V, k, X.st); X.launches += 1;
-    PassDesc p3 = d;                       // pass at z^t = argmin (both sides)
-    p3.mode = PASS_ROWS | PASS_COLS;
+    // pass at z^t = argmin.  When the argmin keeps z^ (take_hat), the sums of
+    // the side block k just updated follow from the Greenkhorn pass in closed
+    // form (u-step: log r(B(z^))_i = log r(B(z_grave))_i + u^_i - u_grave_i;
+    // w-step: both sides shift by w^ - w_grave), so P3a computes only the other
+    // side (nothing for k = 2) and P3b the remaining ones only when z^t = z_check.
+    PassDesc p3 = d;
     p3.arow0 = V.uc; p3.bcol0 = V.vc; p3.aoff0 = &X.S->w_check;
     p3.arow1 = (k == 0) ? V.uh : V.ug; p3.bcol1 = (k == 1) ? V.vh : V.vg; p3.aoff1 = &X.S->w_hat;
     p3.sel = &X.S->take_hat; p3.done = &X.S->done;
-    if ((q = run_pass(X, p3)) != POT_OK) return q;
+    if (k != 2) {
+      PassDesc p3a = p3;
+      p3a.mode = (k == 0) ? PASS_COLS : PASS_ROWS;
+      if ((q = run_pass(X, p3a)) != POT_OK) return q;
+    }
+    PassDesc p3b = p3;
+    p3b.mode = (k == 0) ? PASS_ROWS : (k == 1 ? PASS_COLS : (PASS_ROWS | PASS_COLS));
+    p3b.skip = &X.S->take_hat; p3b.skip_if = 1;
+    if ((q = run_pass(X, p3b, false)) != POT_OK) return q;
     launch_aspot_after_final(V, k, X.st); X.launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
     return POT_OK;
   };
   const int per = params->check_every > 0 ? params->check_every : 24;
-  if ((s = drive(X, per, params->max_iter, 3, body)) != POT_OK) return s;
+  auto aspot_passes = [](int k) { return k == 2 ? 2 : 3; };      // P1, P2 (, P3a); P3b is not timed
+  if ((s = drive(X, per, params->max_iter, aspot_passes, body)) != POT_OK) return s;
   if ((s = read_state(X, h)) != POT_OK) return s;
   CK(cudaMemcpyAsync(plan->w, &X.S->w_out, sizeof(double), cudaMemcpyDeviceToDevice, X.st));
   res->iters = h.t;
@@ -668,7 +687,7 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
     return POT_OK;
   };
   const int per = params->check_every > 0 ? params->check_every : 24;
-  if ((s = drive(X, per, params->max_iter, 2, body)) != POT_OK) return s;
+  if ((s = drive(X, per, params->max_iter, [](int) { return 2; }, body)) != POT_OK) return s;
   if ((s = read_state(X, h)) != POT_OK) return s;
   // final duals: the first n / m extended potentials, w = 0
   CK(cudaMemcpyAsync(plan->u, V.u, sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));

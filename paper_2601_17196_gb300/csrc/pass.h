@@ -36,9 +36,17 @@ struct PassDesc {
   double* red_part;      // objective / max-cost partials, one per CTA
   const double* p; const double* q; const double* kappa;   // objective rank-one term
   const int* done;       // when non-null and *done != 0 the pass returns at once
+  const int* skip;       // when non-null and *skip == skip_if the pass returns at once
+  int skip_if;
   // tensor-core path only: per-pass row / column terms (padded) and an error flag
   float4* rowA; float2* colA; float2* colB;
   int* err;
 };
+
+// True when the pass must not run (the solve has stopped, or its skip
+// condition holds); every kernel of a pass returns at once then.
+__host__ __device__ inline bool pass_off(const PassDesc& P) {
+  return (P.done && *P.done) || (P.skip && *P.skip == P.skip_if);
+}
 
 }  // namespace pot

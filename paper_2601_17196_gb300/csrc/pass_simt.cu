@@ -50,7 +50,7 @@ __device__ __forceinline__ float load_pt(const void* base, int64_t idx) {
 // (no norm terms for a dense cost).  Entries past n / m (padding) are log 0.
 // In max-cost mode the tensor-core pass reads the norms through the same slots.
 __global__ void prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad) {
-  if (P.done && *P.done) return;
+  if (pass_off(P)) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool use1 = P.sel && *P.sel;
   const double* arow = use1 ? P.arow1 : P.arow0;
@@ -339,8 +339,8 @@ __device__ __forceinline__ void rows4_reduce(float (&v)[4], int lane) {
   }
 }
 
-__global__ void clear_parts_kernel(float2* a, int64_t cnt, const int* done) {
-  if (done && *done) return;
+__global__ void clear_parts_kernel(float2* a, int64_t cnt, const int* done, const int* skip, int skip_if) {
+  if ((done && *done) || (skip && *skip == skip_if)) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < cnt) a[t] = make_float2(POT_NEG_BIGF, 0.f);
 }
@@ -364,7 +364,7 @@ __device__ __forceinline__ void cp_wait_ring() { asm volatile("cp.async.wait_gro
 
 template <int MODE>   // 0: rows + columns, 1: rows, 2: columns
 __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, SimtLayout DL) {
-  if (P.done && *P.done) return;
+  if (pass_off(P)) return;
   constexpr bool ROWS = MODE != 2, COLS = MODE != 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ float sS[kWarps][256];
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
 
 template <int KIND, int V, int DMAX, bool VEC>
 __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) {
-  if (P.done && *P.done) return;
+  if (pass_off(P)) return;
   simt_tile<KIND, V, DMAX, VEC>(P, H, blockIdx.x, blockIdx.y, P.n, P.m, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
 
@@ -543,7 +543,7 @@ void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
   if (KIND == COST_DENSE_F32 && hot && L.dense_fast) {
     if (P.mode & PASS_COLS) {     // slots no segment writes must read as empty
       const int64_t cnt = L.nslots * P.m;
-      clear_parts_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(P.col_part, cnt, P.done);
+      clear_parts_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(P.col_part, cnt, P.done, P.skip, P.skip_if);
     }
     const unsigned grid = (unsigned)L.G;
     static bool attr_set = false;

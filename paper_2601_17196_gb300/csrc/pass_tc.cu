@@ -85,7 +85,7 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
   volatile int* s_abort = (volatile int*)(smem + SL.misc_off + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (P.done && *P.done) return;
+  if (pass_off(P)) return;
 
   const int64_t unit = blockIdx.x;
   const int64_t rb = unit / TL.nchunks, ch = unit % TL.nchunks;

@@ -88,7 +88,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
   float4* sCA = (float4*)(smem + SL.ca_off);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (P.done && *P.done) return;
+  if (pass_off(P)) return;
 
   const int64_t G = TL.G, T = TL.T, ntiles = TL.ntiles2;
   const int64_t c = blockIdx.x;

@@ -45,8 +45,8 @@ __device__ __forceinline__ double combine_parts(const float2* part, int64_t nblk
 // one partial row); the slices meet in shared memory.
 __global__ void combine_kernel(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow,
                                const float2* col_part, int64_t nrowblk, int64_t m, double* lcol, int64_t nbr,
-                               const int* done) {
-  if (done && *done) return;
+                               const int* done, const int* skip, int skip_if) {
+  if ((done && *done) || (skip && *skip == skip_if)) return;
   __shared__ float sM[8][32], sS[8][32];
   const bool is_row = blockIdx.x < nbr;
   const float2* part = is_row ? row_part : col_part;
@@ -420,9 +420,14 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   double v[4] = {0, 0, 0, 0};   // Eu+Ev, tot, phi parts, nonfinite
   double xr = 0.0;
   bool act = false;
+  // z^t = z^: the sums of block k's side come from the Greenkhorn pass at
+  // z_grave in closed form (the other side was computed at z^ by P3a)
+  const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
   if (t < V.n) {
     const double uz = take ? uz_hat[t] : V.uc[t];
-    const double R = V.lrow[t];
+    double R = V.lrow[t];
+    if (take && k == 0) R = clamp_log(R + (V.uh[t] - V.ug[t]));
+    else if (take && k == 2) R = clamp_log(R + dw);
     xr = R;
     act = k == 2;                      // log |B|_1 is needed by the w step only
     const double rB = safe_exp(R), eu = safe_exp(uz);
@@ -436,7 +441,9 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vz = take ? vz_hat[j] : V.vc[j];
-    const double Cc = V.lcol[j];
+    double Cc = V.lcol[j];
+    if (take && k == 1) Cc = clamp_log(Cc + (V.vh[j] - V.vg[j]));
+    else if (take && k == 2) Cc = clamp_log(Cc + dw);
     const double cB = safe_exp(Cc), ev = safe_exp(vz);
     v[0] = fabs(cB + ev - V.ct[j]);
     V.vo[j] = vz;
@@ -730,12 +737,13 @@ __global__ void dense_plan_kernel(PassDesc P, const double* f, const double* g, 
 }  // namespace
 
 void launch_combine(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow, const float2* col_part,
-                    int64_t nrowblk, int64_t m, double* lcol, const int* done, cudaStream_t st) {
+                    int64_t nrowblk, int64_t m, double* lcol, const int* done, cudaStream_t st, const int* skip,
+                    int skip_if) {
   const int64_t nbr = lrow ? (n + 31) / 32 : 0;
   const int64_t nbc = lcol ? (m + 31) / 32 : 0;
   if (nbr + nbc == 0) return;
   combine_kernel<<<(unsigned)(nbr + nbc), 256, 0, st>>>(row_part, ncolblk, n, lrow, col_part, nrowblk, m, lcol, nbr,
-                                                        done);
+                                                        done, skip, skip_if);
 }
 
 void launch_marg_stats(const double* r, const double* c, int64_t n, int64_t m, double* red,
