@@ -30,8 +30,13 @@
  * temperature gamma (of v instead of log c), so the network learns a
  * correction to it; the higher temperatures show the mass around the point
  * at larger scales.  Each costs one pass over the cost (pot_marginals).
- * Training minimises the mean squared error between y and the targets of
- * converged ASPOT runs (pot_ws_targets), with Adam.
+ * Training minimises the weighted mean squared error
+ *   L = (1/N) sum_p omega_p (y_p - target_p)^2
+ * over the N points of a batch, against the targets of converged ASPOT runs
+ * (pot_ws_targets), with Adam.  The weight omega = sigmoid(log K)^2 (the
+ * squared transported fraction of the point) is the factor by which an
+ * output error reaches the duals (du_i = sigmoid(y_i / gamma) dy_i / gamma), so
+ * L measures the start's distance to z*, the constant of Lemma 2.
  *
  * Parameters are one FP32 device array (pot_ws_param_count floats), row-major:
  *   W1[H][F], b1[H], W2[H][H], U[H][H+2], b2[H], w3[H], b3[1].
@@ -74,6 +79,7 @@ typedef struct {
   const float* feats;     /* [off[count]][d + 5] */
   const float* extra;     /* [count][2]: |r|_1 / s, |c|_1 / s */
   const float* target;    /* [off[count]] from pot_ws_targets; NULL when only predicting */
+  const float* weight;    /* [off[count]] loss weights from pot_ws_targets, or NULL (all 1) */
 } pot_ws_set;
 
 typedef struct {           /* Adam (Kingma & Ba, 2015) */
@@ -103,10 +109,12 @@ POT_API pot_status pot_ws_features(const pot_problem* prob, double gamma, void* 
  * optimum (where (B1)_i + e^{u_i} = r_i, so u_i = log r_i - softplus(log K_i)).
  * gamma log K_i is a smooth function of the point (a soft minimum over the
  * other cloud); the sharp softplus is applied in closed form by the warm
- * start.  One pot_marginals pass (and the max pass when prob->cost_scale is
- * 0, which synchronises the stream); workspace as pot_ws_features. */
+ * start.  `weight` (may be NULL) receives the loss weights
+ * sigmoid(log K)^2.  One pot_marginals pass (and the max pass when
+ * prob->cost_scale is 0, which synchronises the stream); workspace as
+ * pot_ws_features. */
 POT_API pot_status pot_ws_targets(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
-                                  float* target, void* workspace, size_t ws_bytes, void* stream);
+                                  float* target, float* weight, void* workspace, size_t ws_bytes, void* stream);
 
 /* Workspace for batches of at most max_batch instances of `set` (the
  * largest ones are assumed). */
@@ -119,7 +127,7 @@ POT_API pot_status pot_ws_workspace_size(const pot_ws_set* set, int32_t max_batc
 POT_API pot_status pot_ws_forward(const pot_ws_set* set, const int32_t* idx, int32_t nb, const float* params,
                                   int32_t mode, float* y, void* workspace, size_t ws_bytes, void* stream);
 
-/* Mean squared error of the batch (device scalar `loss`) and its gradient
+/* Weighted mean squared error of the batch (device scalar `loss`) and its gradient
  * with respect to every parameter (`grad`, pot_ws_param_count floats, same
  * layout as the parameters).  Needs set->target.  Enqueued only. */
 POT_API pot_status pot_ws_gradient(const pot_ws_set* set, const int32_t* idx, int32_t nb, const float* params,

@@ -75,16 +75,19 @@ def forward(P: dict, feats, seg, extra):
     return y, dict(a1=a1, h1=h1, cin=cin, a2=a2, h2=h2, npts=npts)
 
 
-def mse(y, target) -> float:
+def mse(y, target, weight=None) -> float:
+    """(1/N) sum_p omega_p (y_p - target_p)^2 (omega = 1 when weight is None)."""
     d = y - target
-    return float((d * d).mean())
+    w = np.ones_like(d) if weight is None else np.asarray(weight, dtype=np.float64)
+    return float((w * d * d).mean())
 
 
-def backward(P: dict, feats, seg, extra, target, cache) -> dict:
-    """Gradients of the mean squared error by the chain rule, written out."""
+def backward(P: dict, feats, seg, extra, target, cache, weight=None) -> dict:
+    """Gradients of the (weighted) mean squared error by the chain rule, written out."""
     count = extra.shape[0]
     Np = feats.shape[0]
-    dy = 2.0 * (cache["h2"] @ P["w3"] + P["b3"][0] - target) / Np
+    w = np.ones(Np) if weight is None else np.asarray(weight, dtype=np.float64)
+    dy = 2.0 * w * (cache["h2"] @ P["w3"] + P["b3"][0] - target) / Np
     g = {}
     g["w3"] = cache["h2"].T @ dy
     g["b3"] = np.array([dy.sum()])
@@ -165,6 +168,15 @@ def targets(C, gamma: float, u, v, w: float):
     lrow = np.array([_lse(L[i]) for i in range(L.shape[0])])
     lcol = np.array([_lse(L[:, j]) for j in range(L.shape[1])])
     return np.concatenate([gamma * (lrow - np.asarray(u)), gamma * (lcol - np.asarray(v))])
+
+
+def target_weights(C, gamma: float, u, v, w: float):
+    """Loss weights sigmoid(log K)^2 of the points (K from ``targets``): the
+    squared factor by which an output error reaches the duals,
+    du_i = sigmoid(y_i / gamma) dy_i / gamma at u_i = log r_i - softplus(y_i / gamma)."""
+    lk = targets(C, gamma, u, v, w) / gamma
+    sg = np.where(lk >= 0, 1.0 / (1.0 + np.exp(-np.abs(lk))), np.exp(-np.abs(lk)) / (1.0 + np.exp(-np.abs(lk))))
+    return sg * sg
 
 
 def softplus(x):

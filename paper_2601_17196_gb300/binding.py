@@ -61,7 +61,7 @@ class _Params(ct.Structure):
 
 class _WsSet(ct.Structure):
     _fields_ = [("count", ct.c_int64), ("d", ct.c_int32), ("pad", ct.c_int32), ("off", ct.c_void_p),
-                ("feats", ct.c_void_p), ("extra", ct.c_void_p), ("target", ct.c_void_p)]
+                ("feats", ct.c_void_p), ("extra", ct.c_void_p), ("target", ct.c_void_p), ("weight", ct.c_void_p)]
 
 
 class _WsAdam(ct.Structure):
@@ -112,7 +112,7 @@ def lib() -> ct.CDLL:
         L.pot_ws_init.argtypes = [vp, i32, ct.c_uint64, vp]
         L.pot_ws_features_workspace_size.argtypes = [P, ct.POINTER(sz)]
         L.pot_ws_features.argtypes = [P, dbl, vp, sz, vp, vp, vp]
-        L.pot_ws_targets.argtypes = [P, dbl, vp, vp, dbl, vp, vp, sz, vp]
+        L.pot_ws_targets.argtypes = [P, dbl, vp, vp, dbl, vp, vp, vp, sz, vp]
         L.pot_ws_workspace_size.argtypes = [WS, i32, ct.POINTER(sz)]
         L.pot_ws_forward.argtypes = [WS, vp, i32, vp, i32, vp, vp, sz, vp]
         L.pot_ws_gradient.argtypes = [WS, vp, i32, vp, i32, vp, vp, vp, sz, vp]

@@ -178,12 +178,17 @@ __device__ __forceinline__ double ws_base(const double* r, const double* stats, 
 }
 
 // target = gamma log K: gamma (lrow_i - u_i) for rows, gamma (lcol_j - v_j) for
-// columns, with lrow, lcol the log-sums of B(u, v, w)
+// columns, with lrow, lcol the log-sums of B(u, v, w); weight = sigmoid(log K)^2
 __global__ void ws_targets_kernel(int64_t n, int64_t m, double gamma, const double* lrow, const double* lcol,
-                                  const double* u, const double* v, float* t) {
+                                  const double* u, const double* v, float* t, float* wt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) t[i] = (float)(gamma * (lrow[i] - u[i]));
-  else if (i < n + m) t[i] = (float)(gamma * (lcol[i - n] - v[i - n]));
+  if (i >= n + m) return;
+  const double lk = (i < n) ? lrow[i] - u[i] : lcol[i - n] - v[i - n];
+  t[i] = (float)(gamma * lk);
+  if (wt) {
+    const double sg = lk >= 0.0 ? 1.0 / (1.0 + exp(-lk)) : exp(lk) / (1.0 + exp(lk));
+    wt[i] = (float)(sg * sg);
+  }
 }
 
 // u_i = log r_i - softplus(y_i / gamma), v_j = log c_j - softplus(y_j / gamma)
@@ -407,10 +412,13 @@ __global__ void __launch_bounds__(256, 1) ws_main_kernel(WsArgs A) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int p = ty + 16 * i;
-      float dd = 0.f;
-      if (p < cnt) dd = yp[i] + b3 - A.target[tl.start + p];
-      dy[i] = 2.f * dd * A.invN;
-      if (tx == 0) { dys[p] = dy[i]; ls[p] = dd * dd * A.invN; }
+      float dd = 0.f, wt = 0.f;
+      if (p < cnt) {
+        dd = yp[i] + b3 - A.target[tl.start + p];
+        wt = A.weight ? A.weight[tl.start + p] : 1.f;
+      }
+      dy[i] = 2.f * wt * dd * A.invN;
+      if (tx == 0) { dys[p] = dy[i]; ls[p] = wt * dd * dd * A.invN; }
     }
     float pw3[8], pdq[8];
 #pragma unroll
@@ -751,7 +759,7 @@ pot_status run_batch(const pot_ws_set* S, const int32_t* idx, int32_t nb, const 
   A.o = offsets(S->d);
   A.tiles = reinterpret_cast<const WsTile*>(base + L.o_tiles);
   A.binfo = reinterpret_cast<const WsInst*>(base + L.o_binfo);
-  A.feats = S->feats; A.extra = S->extra; A.target = S->target; A.P = params;
+  A.feats = S->feats; A.extra = S->extra; A.target = S->target; A.weight = S->weight; A.P = params;
   A.ctxp = reinterpret_cast<float*>(base + L.o_ctxp);
   A.cin = reinterpret_cast<float*>(base + L.o_cin);
   A.q = reinterpret_cast<float*>(base + L.o_q);
@@ -906,7 +914,7 @@ POT_API pot_status pot_ws_features(const pot_problem* prob, double gamma, void* 
 }
 
 POT_API pot_status pot_ws_targets(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
-                                  float* target, void* workspace, size_t ws_bytes, void* stream) {
+                                  float* target, float* weight, void* workspace, size_t ws_bytes, void* stream) {
   pot_status s;
   if ((s = check_points_problem(prob)) != POT_OK) return s;
   if (!(gamma > 0.0) || !isfinite(gamma)) return wfail(POT_EINVAL, "gamma must be finite and > 0");
@@ -928,7 +936,7 @@ POT_API pot_status pot_ws_targets(const pot_problem* prob, double gamma, const d
   if ((s = pot_marginals(&q, gamma, u, v, w, base, o_stats, lrow, lcol, nullptr, stream)) != POT_OK) return s;
   const int64_t n = q.n, m = q.m;
   ws_targets_kernel<<<(unsigned)((n + m + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, m, gamma, lrow, lcol, u,
-                                                                                        v, target);
+                                                                                        v, target, weight);
   WCKL();
   return POT_OK;
 }

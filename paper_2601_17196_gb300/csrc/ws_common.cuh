@@ -58,6 +58,7 @@ struct WsArgs {
   const float* feats;
   const float* extra;
   const float* target;
+  const float* weight;   // loss weights or nullptr (all 1)
   const float* P;
   float* ctxp;     // [T][H] per-tile sums of H1
   float* cin;      // [B][H+2] context inputs

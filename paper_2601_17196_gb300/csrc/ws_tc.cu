@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(kThreads, 1) ws_tc_kernel(WsArgs A) {
       continue;
     }
     const float dd = live ? y - A.target[tl.start + p] : 0.f;
-    const float dy = 2.f * dd * A.invN;
+    const float wt = live ? (A.weight ? A.weight[tl.start + p] : 1.f) : 0.f;
+    const float dy = 2.f * wt * dd * A.invN;
     // sweep 2: D2 = dy w3 GELU'(A2)
 #pragma unroll 1
     for (int ch = 0; ch < 4; ++ch) {
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1) ws_tc_kernel(WsArgs A) {
       }
     }
     if (PASS == 1) {
-      const float sdy = warp_sum(dy), sl = warp_sum(dd * dd * A.invN);
+      const float sdy = warp_sum(dy), sl = warp_sum(wt * dd * dd * A.invN);
       if (lane == 0) { wsm[warp] = sdy; wsm[4 + warp] = sl; }
     }
     fence_async_smem();

@@ -57,6 +57,7 @@ class FeatureSet:
     off: np.ndarray
     target: Optional[torch.Tensor] = None
     n_rows: Optional[np.ndarray] = None
+    weight: Optional[torch.Tensor] = None
 
     @property
     def count(self) -> int:
@@ -68,6 +69,7 @@ class FeatureSet:
         s.off = self.off.ctypes.data_as(ct.c_void_p)
         s.feats, s.extra = self.feats.data_ptr(), self.extra.data_ptr()
         s.target = None if self.target is None else self.target.data_ptr()
+        s.weight = None if self.weight is None else self.weight.data_ptr()
         return s
 
     def subset(self, idx: Sequence[int]) -> "FeatureSet":
@@ -79,10 +81,12 @@ class FeatureSet:
             if self.target is not None:
                 tparts.append(self.target[a:b])
             off.append(off[-1] + b - a)
+        wparts = [self.weight[int(self.off[k]):int(self.off[k + 1])] for k in idx] if self.weight is not None else []
         return FeatureSet(self.d, torch.cat(parts).contiguous(), self.extra[torch.as_tensor(idx, device=self.extra.device)].contiguous(),
                           np.asarray(off, dtype=np.int64),
                           torch.cat(tparts).contiguous() if tparts else None,
-                          None if self.n_rows is None else self.n_rows[idx])
+                          None if self.n_rows is None else self.n_rows[idx],
+                          torch.cat(wparts).contiguous() if wparts else None)
 
 
 def features(probs: Sequence[B.DeviceProblem], gamma: float) -> FeatureSet:
@@ -113,9 +117,11 @@ def features(probs: Sequence[B.DeviceProblem], gamma: float) -> FeatureSet:
 
 def targets_into(fs: FeatureSet, k: int, prob: B.DeviceProblem, gamma: float, u: torch.Tensor,
                  v: torch.Tensor, w: float, ws: Optional[torch.Tensor] = None) -> None:
-    """target[off[k]:off[k+1]] from the converged duals (pot_ws_targets)."""
+    """target[off[k]:off[k+1]] and the loss weights from the converged duals (pot_ws_targets)."""
     if fs.target is None:
         fs.target = torch.zeros(int(fs.off[-1]), dtype=torch.float32, device=fs.feats.device)
+    if fs.weight is None:
+        fs.weight = torch.ones(int(fs.off[-1]), dtype=torch.float32, device=fs.feats.device)
     L = B.lib()
     if ws is None:
         b = ct.c_size_t(0)
@@ -124,7 +130,8 @@ def targets_into(fs: FeatureSet, k: int, prob: B.DeviceProblem, gamma: float, u:
     side, cur = B._stream()
     B._check(L.pot_ws_targets(ct.byref(prob.struct()), float(gamma), ct.c_void_p(u.data_ptr()),
                               ct.c_void_p(v.data_ptr()), float(w), ct.c_void_p(fs.target[int(fs.off[k]):].data_ptr()),
-                              ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(side.cuda_stream)))
+                              ct.c_void_p(fs.weight[int(fs.off[k]):].data_ptr()), ct.c_void_p(ws.data_ptr()),
+                              ws.numel(), ct.c_void_p(side.cuda_stream)))
     B._finish(side, cur)
 
 

@@ -264,6 +264,11 @@ def ws_batch(sizes, d: int = 2, seed: int = 0):
     return feats, extra, target, off
 
 
+def ws_weights(n: int, seed: int = 0) -> np.ndarray:
+    """Random loss weights U[0, 1] (FP32) for weighted-loss checks."""
+    return np.random.default_rng(seed).uniform(0.0, 1.0, size=n).astype(np.float32)
+
+
 def registration_3d(seed: int = 0, n: int = 1024, frac: float = 0.5, max_angle: float = 0.5,
                     max_shift: float = 0.1, noise: float = 0.0):
     """A target cloud and a misaligned partial source (stand-in for the 3-D

@@ -22,14 +22,15 @@ def _set(sizes, d, seed):
     return fs, feats, extra, target, off
 
 
-def _oracle(P, feats, extra, target, off, idx):
+def _oracle(P, feats, extra, target, off, idx, weight=None):
     fe = np.vstack([feats[off[k]:off[k + 1]] for k in idx]).astype(np.float64)
     tg = np.concatenate([target[off[k]:off[k + 1]] for k in idx]).astype(np.float64)
+    wt = None if weight is None else np.concatenate([weight[off[k]:off[k + 1]] for k in idx]).astype(np.float64)
     seg = np.concatenate([np.full(off[k + 1] - off[k], b) for b, k in enumerate(idx)])
     ex = extra[idx].astype(np.float64)
     y, cache = OW.forward(P, fe, seg, ex)
-    g = OW.backward(P, fe, seg, ex, tg, cache)
-    return y, OW.mse(y, tg), g
+    g = OW.backward(P, fe, seg, ex, tg, cache, wt)
+    return y, OW.mse(y, tg, wt), g
 
 
 # ragged tiles (300 = 2 x 128 + 44), a one-point instance, exactly one tile
@@ -42,17 +43,21 @@ SIZES = [300, 77, 129, 128, 1, 513]
 TOL = {WS.MODE_FP32: (2e-5, 1e-4, 1e-4), WS.MODE_BF16: (1e-2, 2e-2, 2e-2)}
 
 
+@pytest.mark.parametrize("weighted", [False, True])
 @pytest.mark.parametrize("mode", [WS.MODE_FP32, WS.MODE_BF16])
 @pytest.mark.parametrize("d", [2, 3])
-def test_forward_and_gradient_match_oracle(d, mode):
+def test_forward_and_gradient_match_oracle(d, mode, weighted):
     fs, feats, extra, target, off = _set(SIZES, d, 1)
+    wts = W.ws_weights(int(off[-1]), 7) if weighted else None
+    if weighted:
+        fs.weight = torch.from_numpy(wts).cuda()
     flat = W.ws_params(d, 2)
     net = WS.WarmStartNet(d, params=torch.from_numpy(flat), mode=mode)
     idx = [2, 0, 4, 5, 1]                     # a shuffled subset
     y = net.forward(fs, idx).cpu().numpy().astype(np.float64)
     g, loss = net.gradient(fs, idx)
     P = OW.unflatten(flat.astype(np.float64), d)
-    yo, lo, go = _oracle(P, feats, extra, target, off, idx)
+    yo, lo, go = _oracle(P, feats, extra, target, off, idx, wts)
     ty, tl, tg = TOL[mode]
     assert np.abs(y - yo).max() <= ty * max(1.0, np.abs(yo).max())
     assert abs(loss.item() - lo) <= tl * lo
@@ -65,7 +70,7 @@ def test_forward_and_gradient_match_oracle(d, mode):
 
 def _scale(go, k, y, t):
     """Size of a gradient block's terms: its largest entry, except for db3 =
-    (2/N) sum (y - t), whose terms cancel; its scale is (2/N) sum |y - t|."""
+    (2/N) sum w (y - t), whose terms cancel; its scale is (2/N) sum |y - t|."""
     if k == "b3":
         return 2.0 * np.abs(y - t).mean()
     return np.abs(go[k]).max()
@@ -208,6 +213,8 @@ def test_targets_match_oracle():
     to = OW.targets(C, 0.02, u, v, w)
     # FP32 pass log-sums (5e-6 + 2e-7 |lse|) times gamma
     assert np.abs(t - to).max() <= 0.02 * (5e-6 + 2e-7 * np.abs(to / 0.02).max()) + 1e-7
+    wo = OW.target_weights(C, 0.02, u, v, w)
+    assert np.abs(fs.weight.cpu().numpy() - wo).max() <= 2e-5
 
 
 @pytest.mark.parametrize("cost_scale", [0.0, 0.7])

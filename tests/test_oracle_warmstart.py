@@ -20,7 +20,8 @@ def test_gelu_closed_forms():
     assert WS.gelu_grad(np.array([0.0]))[0] == pytest.approx(0.5)
 
 
-def test_backward_matches_finite_differences():
+@pytest.mark.parametrize("weighted", [False, True])
+def test_backward_matches_finite_differences(weighted):
     rng = np.random.default_rng(0)
     P = WS.init_params(1)
     # two instances of different sizes, all four feature kinds
@@ -28,8 +29,9 @@ def test_backward_matches_finite_differences():
     feats = rng.normal(size=(12, 7))
     extra = rng.uniform(1, 2, size=(2, 2))
     target = rng.normal(size=12)
+    wt = rng.uniform(0.0, 1.0, size=12) if weighted else None
     y, cache = WS.forward(P, feats, seg, extra)
-    G = WS.backward(P, feats, seg, extra, target, cache)
+    G = WS.backward(P, feats, seg, extra, target, cache, wt)
     h = 1e-6
     for name in ("W1", "b1", "W2", "U", "b2", "w3", "b3"):
         flat = P[name].reshape(-1)
@@ -37,9 +39,9 @@ def test_backward_matches_finite_differences():
         for k in idx:
             old = flat[k]
             flat[k] = old + h
-            fp = WS.mse(WS.forward(P, feats, seg, extra)[0], target)
+            fp = WS.mse(WS.forward(P, feats, seg, extra)[0], target, wt)
             flat[k] = old - h
-            fm = WS.mse(WS.forward(P, feats, seg, extra)[0], target)
+            fm = WS.mse(WS.forward(P, feats, seg, extra)[0], target, wt)
             flat[k] = old
             assert G[name].reshape(-1)[k] == pytest.approx((fp - fm) / (2 * h), rel=1e-6, abs=1e-9)
 
@@ -160,3 +162,17 @@ def test_targets_invert_the_start_at_the_optimum():
     assert WS.softplus(0.0) == pytest.approx(math.log(2.0))
     assert WS.softplus(-50.0) == pytest.approx(math.exp(-50.0), rel=1e-12)
     assert WS.softplus(50.0) == pytest.approx(50.0, rel=1e-15)
+
+
+def test_target_weights_are_the_squared_transported_fraction():
+    """At the optimum sigmoid(log K_i) = (B1)_i / r_i: the fraction of r_i that
+    is transported; its square is the weight."""
+    from oracle import pot as O
+    import pot_workloads as W
+    pb = W.tiny(5, n=6, m=5, mass_r=1.1, mass_c=1.4, s=0.8)
+    C = np.asarray(pb.C, dtype=np.float64)
+    z = O.aspot(C, pb.r, pb.c, pb.s, 1e-9, 0.1, max_iter=200000, smooth=False, stop_raw_eps=True).z
+    wts = WS.target_weights(C, 0.1, z.u, z.v, z.w)
+    B = np.exp(O.log_gibbs(C, 0.1, z.u, z.v, z.w))
+    np.testing.assert_allclose(np.sqrt(wts[:6]), B.sum(1) / pb.r, atol=1e-6)
+    np.testing.assert_allclose(np.sqrt(wts[6:]), B.sum(0) / pb.c, atol=1e-6)
