@@ -166,6 +166,24 @@ def run_reference(args, rank, world):
 
 # -------------------------------------------------------------- GPU arm --
 
+def reduce_replicas(maxes, sums, device="cpu"):
+    """Whole-job figures of independent replicas: the slowest rank's times
+    (max over ranks) and the work of all ranks (sum over ranks).  Needs an
+    initialised process group (nccl on GPUs, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x) for x in maxes], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=device)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], [float(x) for x in s]
+
+
+def replica_throughput(total_units: float, max_ms: float) -> float:
+    """value = units all ranks processed / the slowest rank's time."""
+    return total_units / (max_ms / 1000.0)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -255,12 +273,8 @@ def run_ours(args, rank, world, local_rank):
 
     # ---------------- reduce over ranks (replicas) -------------------------
     if world > 1:
-        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        s = torch.tensor([iters, e2e_iters, launches], dtype=torch.float64, device=dev)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        ms, e2e_ms = float(t[0]), float(t[1])
-        iters, e2e_iters, launches = int(s[0]), int(s[1]), int(s[2])
+        (ms, e2e_ms), (iters, e2e_iters, launches) = reduce_replicas([ms, e2e_ms], [iters, e2e_iters, launches], dev)
+        iters, e2e_iters, launches = int(iters), int(e2e_iters), int(launches)
     if rank != 0:
         return
 
@@ -269,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
     flop_per_pass = 2.0 * n * n * D_FULL
     avg_pass_ms = pass_ms / max(pass_n, 1)
     achieved = flop_per_pass / (avg_pass_ms * 1e-3) / 1e12 if pass_n else None
-    value = iters / (ms / 1000.0)
+    value = replica_throughput(iters, ms)
     line = {
         "metric": "ASPOT iterations/s at n=32k (time-to-epsilon alongside)",
         "value": value, "unit": "it/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
