@@ -94,3 +94,52 @@ def test_profiled_solve_times_every_pass():
     assert a.kernel_launches >= 40 * 10
     np.testing.assert_array_equal(_np(a.plan.u), _np(b.plan.u))
     assert a.objective == b.objective
+
+
+def _rows_lse(X, Y, rows, cs, gamma, u, v, w):
+    """Oracle log-sums of sampled rows (and, transposed, columns) of B at full size."""
+    out = np.empty(len(rows))
+    for k, i in enumerate(rows):
+        c = cs * ((X[i][None, :] - Y) ** 2).sum(axis=1)
+        out[k] = O.logsumexp(u[i] + v + w - c / gamma)
+    return out
+
+
+def test_cloud_32k_full_size_sampled():
+    """The bench's workload at its full size (n = m = 32768, d = 128 BF16) in the
+    launch configuration the bench times: (1) one fused pass with given
+    potentials, 256 sampled rows and 256 sampled columns against the oracle in
+    FP64; (2) a whole solve, whose rounded plan is checked for feasibility on
+    sampled rows and columns in FP64 and whose E_t meets the threshold."""
+    pb = W.cloud_32k(0)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    X, Y = W.from_bf16_bits(pb.X_bf16), W.from_bf16_bits(pb.Y_bf16)
+    n, m = X.shape[0], Y.shape[0]
+    g = np.random.default_rng(5)
+    rows = np.sort(g.choice(n, 256, replace=False))
+    cols = np.sort(g.choice(m, 256, replace=False))
+    # (1) one pass with an explicit cost scale (an input, like the potentials)
+    cs, gam = 1.0 / 4000.0, pb.gamma
+    u, v, w = g.uniform(-14, -10, n), g.uniform(-14, -10, m), 3.0
+    dp.cost_scale = cs
+    lr, lc, _ = pkg.pot_marginals(dp, gam, _t(u), _t(v), w)
+    er = _rows_lse(X, Y, rows, cs, gam, u, v, w)
+    ec = _rows_lse(Y, X, cols, cs, gam, v, u, w)
+    assert np.abs(_np(lr)[rows] - er).max() <= 3e-5 + 2e-7 * np.abs(er).max()
+    assert np.abs(_np(lc)[cols] - ec).max() <= 3e-5 + 2e-7 * np.abs(ec).max()
+    # (2) the solve the bench times (cost normalised by its maximum, computed on the GPU)
+    dp.cost_scale = 0.0
+    res = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=20000)
+    assert res.status == 0 and res.err_final <= res.eps_stop and res.nonfinite == 0
+    assert res.mass == pytest.approx(pb.s)
+    f, gg, p, q = (_np(t) for t in (res.plan.f, res.plan.g, res.plan.p, res.plan.q))
+    kap = float(res.plan.kappa.item())
+    csr = res.cost_scale
+    for i in rows[:64]:
+        c = csr * ((X[i][None, :] - Y) ** 2).sum(axis=1)
+        xi = np.exp(f[i] + gg - c / res.gamma).sum() + kap * p[i] * q.sum()
+        assert xi <= pb.r[i] * (1 + 1e-5) + 1e-15
+    for j in cols[:64]:
+        c = csr * ((Y[j][None, :] - X) ** 2).sum(axis=1)
+        xj = np.exp(f + gg[j] - c / res.gamma).sum() + kap * p.sum() * q[j]
+        assert xj <= pb.c[j] * (1 + 1e-5) + 1e-15
