@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 N_FULL = 32768
 D_FULL = 128
 CPU_SAMPLE_N = 2048
+# ncu DRAM bytes per launch of the current kernels (null once a kernel changes):
+# dense_pass_kernel<0>, n = m = 16384 FP32 cost: 1.075126 GB read + 11.26 MB written
+DENSE_16K_TRAFFIC = 1.075126e9 + 11.25888e6
+# tc2_pass_kernel<0> (rows + columns), n = m = 32768, d = 128: 17.62 MB read (the BF16
+# points) + 5 KB written; the column partials (33.5 MB) stay in L2
+TC2_32K_TRAFFIC = 17618944.0 + 5120.0
 
 
 def _args():
@@ -46,12 +52,13 @@ def _args():
                     help="'pass': time only the fused row+column pass (for ncu captures of that kernel)")
     ap.add_argument("--workload", default="cloud_32k",
                     choices=["cloud_32k", "dense_4096", "scaling_e4", "batch_3d", "warmstart", "small_dense",
-                             "registration"],
+                             "registration", "ws_train"],
                     help="cloud_32k: the headline line; dense_4096: the FP32 dense-cost path (gamma sweep, "
                          "HBM roofline of the CUDA-core pass); scaling_e4: the appendix's runtime-vs-n study; "
                          "batch_3d: 512 uneven 3-D instances; warmstart: the learned warm start (train + held-out); "
                          "small_dense: the 256-point configuration with the tuned-gamma Sinkhorn p sweep; "
-                         "registration: batched rigid registration of 64 partial 3-D clouds")
+                         "registration: batched rigid registration of 64 partial 3-D clouds; "
+                         "ws_train: training-step throughput of the warm-start network kernels")
     ap.add_argument("--ws-train", type=int, default=20000, help="warmstart: training instances")
     ap.add_argument("--ws-eval", type=int, default=1000, help="warmstart: held-out seeds")
     ap.add_argument("--ws-epochs", type=int, default=12, help="warmstart: training epochs")
@@ -303,7 +310,9 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "roofline": {"kernel": "tc_pass_kernel (tcgen05 on-the-fly log-sum-exp pass)", "bound": "tensor",
                      "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
-                     "frac": (achieved / sustained) if achieved else None, "traffic": None,
+                     "frac": (achieved / sustained) if achieved else None,
+                     "traffic": TC2_32K_TRAFFIC if n == N_FULL else None,
+                     "traffic_note": "ncu dram bytes of one two-sided launch at n=32768 (read + write)",
                      "peak_source": f"{src} bf16 dense, sustained (kernel timed inside a long step)",
                      "flop_per_launch": flop_per_pass, "avg_launch_ms": avg_pass_ms, "launches": pass_n},
     }
@@ -385,10 +394,16 @@ def run_dense(args):
             it = sum(r.iters for r in res) / args.steps
             pms = sum(r.pass_ms for r in res) / max(sum(r.pass_launches for r in res), 1)
             gbs = 4.0 * n * n / (pms * 1e-3) / 1e9
-            out["rows"].append({"n": n, "gamma": gam, "iters": it, "time_to_eps_ms": ms, "it_per_s": it / (ms / 1e3),
-                                "pass_ms": pms, "pass_GBps": gbs, "hbm_frac": gbs / hbm, "hbm_peak": hbm,
-                                "l2_note": "64 MiB cost fits in L2" if n == 4096 else "1 GiB cost > L2",
-                                "objective": res[-1].objective, "converged": all(r.status == 0 for r in res)})
+            row = {"n": n, "gamma": gam, "iters": it, "time_to_eps_ms": ms, "it_per_s": it / (ms / 1e3),
+                   "pass_ms": pms, "pass_GBps": gbs, "hbm_frac": gbs / hbm, "hbm_peak": hbm,
+                   "l2_note": "64 MiB cost fits in L2" if n == 4096 else "1 GiB cost > L2",
+                   "objective": res[-1].objective, "converged": all(r.status == 0 for r in res)}
+            if n == 16384:
+                # DRAM bytes of one two-sided dense_pass_kernel launch at this size, from one ncu
+                # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum)
+                row["traffic_bytes_per_launch"] = DENSE_16K_TRAFFIC
+                row["algorithmic_bytes_per_launch"] = 4.0 * n * n
+            out["rows"].append(row)
             del dp
             torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
@@ -540,6 +555,48 @@ def run_registration(args):
                       "pairs_within_0.06": int((err < 0.06).sum())}), flush=True)
 
 
+def run_ws_train(args):
+    """Training-step throughput of the warm-start network kernels: Adam steps
+    on batches of 32 instances of 2048 points (random features of the
+    network's shape, pot_workloads.ws_batch), BF16 tcgen05 and FP32 CUDA-core
+    modes.  Tensor-core work per point and step: the 128 x 128 products of
+    the forward pass, of training pass A (forward, dW2) and of pass B
+    (forward, dH1) plus the N = 16 product of dW1: 2 * 128 * (5 * 128 + 16)
+    FLOP."""
+    import numpy as np
+    import torch
+    from paper_2601_17196_gb300 import warmstart as WS
+    import pot_workloads as W
+    burst, sustained, hbm, src = _peaks()
+    K, npts = 256, 2048
+    feats, extra, target, off = W.ws_batch([npts] * K, d=2, seed=0)
+    fs = WS.FeatureSet(2, torch.from_numpy(feats).cuda(), torch.from_numpy(extra).cuda(), off,
+                       torch.from_numpy(target).cuda())
+    rows = []
+    stream = torch.cuda.Stream()
+    for mode in (WS.MODE_BF16, WS.MODE_FP32):
+        net = WS.WarmStartNet(2, seed=0, mode=mode)
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup):
+                net.train_step(fs, list(range(32 * (k % 8), 32 * (k % 8) + 32)), lr=1e-3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            steps = max(args.steps, 20)
+            e0.record(stream)
+            for k in range(steps):
+                net.train_step(fs, list(range(32 * (k % 8), 32 * (k % 8) + 32)), lr=1e-3)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        flop = 32 * npts * 2.0 * 128 * (5 * 128 + 16)
+        rows.append({"mode": "bf16 tcgen05" if mode == WS.MODE_BF16 else "fp32 cuda cores", "ms_per_step": ms,
+                     "points_per_step": 32 * npts, "points_per_s": 32 * npts / (ms / 1e3),
+                     "contraction_tflops": flop / (ms * 1e-3) / 1e12,
+                     "frac_of_bf16_peak": flop / (ms * 1e-3) / 1e12 / burst})
+    print(json.dumps({"workload": "warm-start network training: Adam steps of 32 instances x 2048 points",
+                      "rows": rows, "peak_bf16_tflops": burst, "peak_source": src}), flush=True)
+
+
 def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batch: int = 32, lr: float = 3e-3,
                      device="cuda") -> dict:
     """Learned warm start on the 2-D mixture workload (n = m = 1024, 2-6
@@ -621,6 +678,9 @@ def main():
         return
     if args.workload == "registration":
         run_registration(args)
+        return
+    if args.workload == "ws_train":
+        run_ws_train(args)
         return
     if args.mode == "pass":
         run_pass_only(args)
