@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--n", type=int, default=N_FULL, help="problem size (default: the 32k workload)")
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-greedy", action="store_true",
+                    help="headline: skip the greedy-block-rule solves measured beside the cyclic ones")
     ap.add_argument("--mode", default="solve", choices=["solve", "pass"],
                     help="'pass': time only the fused row+column pass (for ncu captures of that kernel)")
     ap.add_argument("--workload", default="cloud_32k",
@@ -286,6 +288,39 @@ def run_ours(args, rank, world, local_rank):
             e2e_ms += e0.elapsed_time(e1)
             e2e_iters += r2.iters
 
+        # ---------------- the greedy block rule, same workload and timing ---
+        greedy = None
+        if world == 1 and not args.no_greedy:
+            def solve_greedy(prob):
+                return pkg.aspot_solve(prob, pb.gamma, pb.eps, max_iter=args.max_iter, flags=flags, check_every=24,
+                                       block_rule=pkg.BLOCK_GREEDY)
+            for _ in range(args.warmup):
+                solve_greedy(dp)
+            torch.cuda.synchronize()
+            gclk = Clocks(local_rank)
+            gclk.start()
+            gev, g_iters, g_conv, g_pass_ms, g_pass_n = [], 0, 0, 0.0, 0
+            for _ in range(args.steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rg = solve_greedy(dp)
+                e1.record(stream)
+                gev.append((e0, e1))
+                g_iters += rg.iters
+                g_conv += int(rg.status == 0)
+                g_pass_ms += rg.pass_ms
+                g_pass_n += rg.pass_launches
+            torch.cuda.synchronize()
+            g_clocks = gclk.stop()
+            g_ms = sum(a.elapsed_time(b) for a, b in gev)
+            greedy = {"block_rule": "greedy (the block with the largest exact decrease of phi, scored from a "
+                                    "two-sided pass at z_grave and again at z^t)",
+                      "value": g_iters / (g_ms / 1000.0), "unit": "it/s",
+                      "time_to_eps_ms": g_ms / args.steps, "iters_per_solve": g_iters / args.steps,
+                      "converged_steps": g_conv, "objective": rg.objective, "E_final": rg.err_final,
+                      "avg_pass_ms": g_pass_ms / max(g_pass_n, 1), "clocks": g_clocks}
+
     # ---------------- reduce over ranks (replicas) -------------------------
     if world > 1:
         (ms, e2e_ms), (iters, e2e_iters, launches) = reduce_replicas([ms, e2e_ms], [iters, e2e_iters, launches], dev)
@@ -324,6 +359,9 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": f"{src} bf16 dense, sustained (kernel timed inside a long step)",
                      "flop_per_launch": flop_per_pass, "avg_launch_ms": avg_pass_ms, "launches": pass_n},
     }
+    if greedy is not None:
+        greedy["time_to_eps_vs_cyclic"] = greedy["time_to_eps_ms"] / (ms / args.steps)
+        line["greedy_rule"] = greedy
     if world == 1 and args.ws_small > 0:
         # learned warm start vs cold start, small configuration (the full one: --workload warmstart)
         line["warm_vs_cold"] = warm_start_study(args.ws_small, 64, epochs=max(1, 100 * 1024 // args.ws_small),
@@ -407,6 +445,22 @@ def run_dense(args):
                    "pass_ms": pms, "pass_GBps": gbs, "hbm_frac": gbs / hbm, "hbm_peak": hbm,
                    "l2_note": "64 MiB cost fits in L2" if n == 4096 else "1 GiB cost > L2",
                    "objective": res[-1].objective, "converged": all(r.status == 0 for r in res)}
+            if not args.no_greedy:
+                with torch.cuda.stream(stream):
+                    for _ in range(args.warmup):
+                        pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, block_rule=pkg.BLOCK_GREEDY)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    rg = [pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, block_rule=pkg.BLOCK_GREEDY)
+                          for _ in range(args.steps)]
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                gms = e0.elapsed_time(e1) / args.steps
+                git = sum(r.iters for r in rg) / args.steps
+                row["greedy_rule"] = {"iters": git, "time_to_eps_ms": gms, "it_per_s": git / (gms / 1e3),
+                                      "objective": rg[-1].objective, "converged": all(r.status == 0 for r in rg),
+                                      "time_to_eps_vs_cyclic": gms / ms}
             if n == 16384:
                 # DRAM bytes of one two-sided dense_pass_kernel launch at this size, from one ncu
                 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum)

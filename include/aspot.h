@@ -86,7 +86,10 @@ typedef struct {
   double eps;          /* accuracy; stop threshold eps~ = eps / (8 max C) (Algorithm 2 setup) */
   double p_tune;       /* feasible Sinkhorn only: >= 1 => gamma = (2 eps/(49 H_min))^(1/p), eps' = H_min gamma^p (Theorem 2) */
   int32_t max_iter;    /* iteration cap (> 0) */
-  int32_t block_rule;  /* ASPOT Greenkhorn block choice: 0 = cyclic t mod 3 (Algorithm 1) */
+  int32_t block_rule;  /* ASPOT Greenkhorn block choice: 0 = cyclic t mod 3 (Algorithm 1); 1 = greedy,
+                          the block whose step decreases phi the most (the choice of Theorem 3's proof),
+                          scored exactly from a two-sided pass (P2 then costs a full pass); ASPOT only,
+                          aspot_solve_batched takes 0 only */
   int32_t flags;       /* POT_FLAG_* */
   int32_t check_every; /* iterations per captured CUDA graph between host polls of the stop flag (0 => 24) */
   const double* u0;    /* optional warm start of ASPOT (device FP64 [n]) or NULL */
@@ -198,7 +201,9 @@ POT_API pot_status pot_plan_dense(const pot_problem* prob, const pot_plan* plan,
 
 /* Per-iteration record of the last solve that set POT_FLAG_TRACE, copied
  * into host `out` as [iters][4] doubles (E_t, phi(z^t), phi(z_check^{t+1}),
- * argmin took z^).  Keeps the last 4096 iterations. */
+ * argmin took z^; with the greedy block rule the last entry is
+ * took + 2 k + 8 k2, k the block of the step at z_grave and k2 that of the
+ * step at z^t).  Keeps the last 4096 iterations. */
 POT_API pot_status pot_trace(void* workspace, int32_t iters, double* out /* host */, void* stream);
 
 /* Thread-local message of the last failure ("" if none). */

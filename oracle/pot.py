@@ -270,6 +270,8 @@ def dual_radius(r, c, s, gamma, cinf) -> float:
 @dataclasses.dataclass
 class AspotTrace:
     k: List[int] = dataclasses.field(default_factory=list)          # block of iteration t
+    k2: List[int] = dataclasses.field(default_factory=list)         # block of the step at z^t
+    dec: List[tuple] = dataclasses.field(default_factory=list)      # greedy: block decreases at z_grave, at z^t
     took_hat: List[bool] = dataclasses.field(default_factory=list)  # argmin picked z^
     E: List[float] = dataclasses.field(default_factory=list)
     theta: List[float] = dataclasses.field(default_factory=list)
@@ -302,7 +304,8 @@ def _choose_block(rule: str, t: int, C, gamma, r, c, s, z: Dual) -> int:
 def aspot(C, r, c, s, eps, gamma: Optional[float] = None, max_iter: int = 10000,
           block_rule: str = "cyclic", stop_raw_eps: bool = False, smooth: bool = True,
           z0: Optional[Dual] = None, forced_hat: Optional[Sequence[bool]] = None,
-          record: bool = False, cmax: Optional[float] = None, no_stop: bool = False) -> SolveResult:
+          record: bool = False, cmax: Optional[float] = None, no_stop: bool = False,
+          forced_blocks: Optional[Sequence[tuple]] = None) -> SolveResult:
     """Algorithm 2 (Accelerated Sinkhorn for POT), main loop.
 
     Per iteration t (theta_0 = 1, z~^0 = z_check^0 = 0 or the warm start):
@@ -316,8 +319,9 @@ def aspot(C, r, c, s, eps, gamma: Optional[float] = None, max_iter: int = 10000,
       theta  = theta (sqrt(theta^2+4) - theta)/2
     and it stops once E_t <= eps~ (or E_t <= eps with ``stop_raw_eps``).
 
-    ``forced_hat`` replays a given sequence of argmin decisions (used when a
-    run in another precision took a near-tie the other way)."""
+    ``forced_hat`` replays a given sequence of argmin decisions, and
+    ``forced_blocks`` a sequence of (k, k2) block choices of the greedy rule
+    (used when a run in another precision took a near-tie the other way)."""
     C = np.asarray(C, dtype=np.float64)
     n, m = C.shape
     cm = float(C.max()) if cmax is None else cmax
@@ -340,6 +344,8 @@ def aspot(C, r, c, s, eps, gamma: Optional[float] = None, max_iter: int = 10000,
         z_grave = z_bar.axpby(1.0, z_new.axpby(1.0, z_tilde, -1.0), theta)
         z_tilde = z_new
         k = _choose_block(block_rule, t, C, g, rt, ct, s, z_grave)
+        if forced_blocks is not None and t < len(forced_blocks):
+            k = int(forced_blocks[t][0])
         z_hat = greenkhorn_step(C, g, rt, ct, s, z_grave, k)
         phi_hat = phi(C, g, rt, ct, s, z_hat)
         if forced_hat is not None and t < len(forced_hat):
@@ -350,10 +356,15 @@ def aspot(C, r, c, s, eps, gamma: Optional[float] = None, max_iter: int = 10000,
         phi_z = phi_hat if take else phi_check
         E = feas_error(C, g, rt, ct, s, z)
         k2 = k if block_rule == "cyclic" else _choose_block(block_rule, t, C, g, rt, ct, s, z)
+        if forced_blocks is not None and t < len(forced_blocks):
+            k2 = int(forced_blocks[t][1])
         z_check = greenkhorn_step(C, g, rt, ct, s, z, k2)
         phi_check = phi(C, g, rt, ct, s, z_check)
         if record:
             trace.k.append(k)
+            trace.k2.append(k2)
+            if block_rule == "greedy":
+                trace.dec.append((block_decreases(C, g, rt, ct, s, z_grave), block_decreases(C, g, rt, ct, s, z)))
             trace.took_hat.append(take)
             trace.E.append(E)
             trace.theta.append(theta)

@@ -32,4 +32,6 @@ from .binding import (  # noqa: F401
     COST_SQEUCLID_BF16,
     COST_SQEUCLID_F16,
     COST_SQEUCLID_F32,
+    BLOCK_CYCLIC,
+    BLOCK_GREEDY,
 )

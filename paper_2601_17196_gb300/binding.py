@@ -28,6 +28,8 @@ COST_DENSE_F32 = 0
 COST_SQEUCLID_BF16 = 1
 COST_SQEUCLID_F16 = 2
 COST_SQEUCLID_F32 = 3
+BLOCK_CYCLIC = 0
+BLOCK_GREEDY = 1
 
 STATUS = {0: "POT_OK", 1: "POT_EINVAL", 2: "POT_ENOMEM", 3: "POT_ECUDA", 4: "POT_ENOCONV",
           5: "POT_ENONFINITE", 6: "POT_ETIMEOUT"}
@@ -307,20 +309,21 @@ def _workspace(prob: DeviceProblem, flags: int, ws: Optional[torch.Tensor]):
     return buf[off:], need
 
 
-def _params(gamma, eps, max_iter, flags, check_every, p_tune=0.0, u0=None, v0=None, w0=0.0) -> _Params:
+def _params(gamma, eps, max_iter, flags, check_every, p_tune=0.0, u0=None, v0=None, w0=0.0,
+            block_rule=0) -> _Params:
     pa = _Params()
     pa.gamma, pa.eps, pa.p_tune = float(gamma), float(eps), float(p_tune)
-    pa.max_iter, pa.block_rule, pa.flags, pa.check_every = int(max_iter), 0, int(flags), int(check_every)
+    pa.max_iter, pa.block_rule, pa.flags, pa.check_every = int(max_iter), int(block_rule), int(flags), int(check_every)
     pa.u0, pa.v0, pa.w0 = _ptr(u0), _ptr(v0), float(w0)
     return pa
 
 
 def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, plan, ws,
-           allow_noconv) -> SolveResult:
+           allow_noconv, block_rule=0) -> SolveResult:
     L = lib()
     plan = plan or Plan.empty(prob.n, prob.m, prob.r.device)
     ws, need = _workspace(prob, flags, ws)
-    pa = _params(gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0)
+    pa = _params(gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, block_rule)
     res = _Result()
     side, cur = _stream()
     st = _check(getattr(L, fn)(ct.byref(prob.struct()), ct.byref(pa), ct.c_void_p(ws.data_ptr()), need,
@@ -342,9 +345,12 @@ def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w
 
 def aspot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
                 check_every: int = 0, u0=None, v0=None, w0: float = 0.0, plan: Optional[Plan] = None,
-                ws: Optional[torch.Tensor] = None, allow_noconv: bool = True) -> SolveResult:
+                ws: Optional[torch.Tensor] = None, allow_noconv: bool = True,
+                block_rule: int = BLOCK_CYCLIC) -> SolveResult:
+    """ASPOT (Algorithm 2).  block_rule: BLOCK_CYCLIC (t mod 3, Algorithm 1) or
+    BLOCK_GREEDY (the block with the largest decrease of phi)."""
     return _solve("aspot_solve", prob, gamma, eps, max_iter, flags, check_every, 0.0, u0, v0, w0, plan, ws,
-                  allow_noconv)
+                  allow_noconv, block_rule)
 
 
 def sinkhorn_pot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 100000, flags: int = 0,

@@ -95,7 +95,7 @@ Layout make_layout(const pot_problem* P, int flags) {
   }
   const int64_t vblk = vec_blocks(n + m + 2);
   const int64_t pass_ctas = std::max<int64_t>(L.sl.ncolblk * L.sl.nrowblk, L.use_tc ? L.tl.v1_units : 0);
-  L.red_doubles = std::max<int64_t>(vblk * 8, pass_ctas) + 64;
+  L.red_doubles = std::max<int64_t>(vblk * 12, pass_ctas) + 64;   // up to 9 sums + (max, sum) per block
   size_t o = 0;
   L.off_state = o; o = align_up(o + sizeof(DevState));
   L.off_red = o; o = align_up(o + sizeof(double) * L.red_doubles);
@@ -178,7 +178,7 @@ pot_status check_params(const pot_params* Q) {
   if (!(Q->eps > 0.0) || !isfinite(Q->eps)) return fail(POT_EINVAL, "eps must be finite and > 0");
   if (!isfinite(Q->gamma)) return fail(POT_EINVAL, "gamma must be finite");
   if (Q->max_iter < 1) return fail(POT_EINVAL, "max_iter must be >= 1");
-  if (Q->block_rule != 0) return fail(POT_EINVAL, "only the cyclic block rule (0) is implemented on the GPU");
+  if (Q->block_rule != 0 && Q->block_rule != 1) return fail(POT_EINVAL, "block_rule must be 0 (cyclic) or 1 (greedy)");
   if (Q->check_every < 0) return fail(POT_EINVAL, "check_every must be >= 0");
   if (!isfinite(Q->w0)) return fail(POT_EINVAL, "w0 must be finite");
   return POT_OK;
@@ -589,9 +589,48 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
     if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
     return POT_OK;
   };
+  // Greedy block rule: k is chosen on the device from a two-sided pass at
+  // z_grave (P2); at z^t one of three passes runs, selected by device flags:
+  // both sides at z_check, rows after a v-step, columns after a u-step
+  // (nothing after a w-step, whose sums follow in closed form).
+  auto body_greedy = [&](int) -> pot_status {
+    pot_status q;
+    launch_aspot_extrap(V, X.st); X.launches += 1;
+    PassDesc p1 = d;
+    p1.mode = PASS_ROWS | PASS_COLS; p1.arow0 = V.ub; p1.bcol0 = V.vb; p1.aoff0 = &X.S->w_bar; p1.done = &X.S->done;
+    if ((q = run_pass(X, p1)) != POT_OK) return q;
+    launch_aspot_after_grad(V, X.st); X.launches += 1;
+    PassDesc p2 = d;
+    p2.mode = PASS_ROWS | PASS_COLS; p2.arow0 = V.ug; p2.bcol0 = V.vg; p2.aoff0 = &X.S->w_grave;
+    p2.done = &X.S->done;
+    if ((q = run_pass(X, p2)) != POT_OK) return q;
+    launch_aspot_greedy_pick(V, X.st);
+    launch_aspot_after_greenkhorn(V, -1, X.st); X.launches += 2;
+    PassDesc p3 = d;
+    p3.arow0 = V.uc; p3.bcol0 = V.vc; p3.aoff0 = &X.S->w_check;
+    p3.arow1 = V.uh; p3.bcol1 = V.vh; p3.aoff1 = &X.S->w_hat;
+    p3.sel = &X.S->take_hat; p3.done = &X.S->done;
+    PassDesc p3z = p3;                     // z^t = z_check: both sides
+    p3z.mode = PASS_ROWS | PASS_COLS; p3z.skip = &X.S->take_hat; p3z.skip_if = 1;
+    if ((q = run_pass(X, p3z, false)) != POT_OK) return q;
+    PassDesc p3r = p3;                     // z^t = z^ after a v-step: rows
+    p3r.mode = PASS_ROWS; p3r.skip = &X.S->run_r3; p3r.skip_if = 0;
+    if ((q = run_pass(X, p3r, false)) != POT_OK) return q;
+    PassDesc p3c = p3;                     // z^t = z^ after a u-step: columns
+    p3c.mode = PASS_COLS; p3c.skip = &X.S->run_c3; p3c.skip_if = 0;
+    if ((q = run_pass(X, p3c, false)) != POT_OK) return q;
+    launch_aspot_greedy_final(V, X.st);
+    launch_aspot_greedy_apply(V, X.st); X.launches += 2;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
+    return POT_OK;
+  };
   const int per = params->check_every > 0 ? params->check_every : 24;
   auto aspot_passes = [](int k) { return k == 2 ? 2 : 3; };      // P1, P2 (, P3a); P3b is not timed
-  if ((s = drive(X, per, params->max_iter, aspot_passes, body)) != POT_OK) return s;
+  auto greedy_passes = [](int) { return 2; };                     // P1, P2; the passes at z^t are not timed
+  if (params->block_rule == 1) s = drive(X, per, params->max_iter, greedy_passes, body_greedy);
+  else s = drive(X, per, params->max_iter, aspot_passes, body);
+  if (s != POT_OK) return s;
   if ((s = read_state(X, h)) != POT_OK) return s;
   CK(cudaMemcpyAsync(plan->w, &X.S->w_out, sizeof(double), cudaMemcpyDeviceToDevice, X.st));
   res->iters = h.t;

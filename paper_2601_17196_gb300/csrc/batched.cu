@@ -516,6 +516,7 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   if (s != POT_OK) return s;
   if (!params || !(params->eps > 0.0) || params->max_iter < 1 || !isfinite(params->gamma))
     return bfail(POT_EINVAL, "batched: bad params");
+  if (params->block_rule != 0) return bfail(POT_EINVAL, "batched: only the cyclic block rule (0)");
   if (!plans || !res) return bfail(POT_EINVAL, "batched: plans and results must be host arrays of count entries");
   for (int k = 0; k < count; ++k) {
     const pot_plan& pl = plans[k];

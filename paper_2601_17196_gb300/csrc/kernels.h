@@ -56,6 +56,8 @@ struct DevState {
   int warm_used, pad3;
   unsigned int counter;
   unsigned int pad2;
+  int kg, k2;                // greedy rule: block of the step at z_grave / at z^t
+  int run_r3, run_c3;        // greedy rule: one-sided passes needed at z^t = z^
   double trace[4096][4];     // E, phi_z, phi_check, take_hat per iteration (ring)
 };
 
@@ -146,6 +148,9 @@ void launch_aspot_extrap(const AspotVecs& V, cudaStream_t st);
 void launch_aspot_after_grad(const AspotVecs& V, cudaStream_t st);
 void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st);
 void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st);
+void launch_aspot_greedy_pick(const AspotVecs& V, cudaStream_t st);
+void launch_aspot_greedy_final(const AspotVecs& V, cudaStream_t st);
+void launch_aspot_greedy_apply(const AspotVecs& V, cudaStream_t st);
 void launch_aspot_start_eval(const AspotVecs& V, const double* u, const double* v, int slot, cudaStream_t st);
 void launch_aspot_zero_bar(const AspotVecs& V, cudaStream_t st);
 void launch_aspot_start_select(const AspotVecs& V, cudaStream_t st);

@@ -111,11 +111,11 @@ __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* c
   __syncthreads();
   if (!amlast) return false;
   __threadfence();
-  if (warp < NV) {
+  for (int k = warp; k < NV; k += kVecThreads / 32) {
     double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (int64_t)b * NV + warp);
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (int64_t)b * NV + k);
     s = warp_sum_d(s);
-    if (lane == 0) st[warp] = s;
+    if (lane == 0) st[k] = s;
   }
   __syncthreads();
 #pragma unroll
@@ -175,11 +175,11 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   __syncthreads();
   if (!amlast) return false;
   __threadfence();
-  if (warp < NV) {
+  for (int k = warp; k < NV; k += NW) {
     double a = 0.0;
-    for (int b2 = lane; b2 < (int)gridDim.x; b2 += 32) a += __ldcg(part + (int64_t)b2 * NP + warp);
+    for (int b2 = lane; b2 < (int)gridDim.x; b2 += 32) a += __ldcg(part + (int64_t)b2 * NP + k);
     a = warp_sum_d(a);
-    if (lane == 0) st[warp] = a;
+    if (lane == 0) st[k] = a;
   }
   // grid log-sum-exp of the block partials, in parallel over the block's threads
   double gm = -INFINITY;
@@ -361,10 +361,14 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
 }
 
 // After the one-sided pass at z_grave: Greenkhorn step (Algorithm 1) for block
-// k, closed-form phi(z^), argmin against phi(z_check).
+// k, closed-form phi(z^), argmin against phi(z_check).  k < 0: the greedy
+// rule's block S->kg (the pass was two-sided); z^ is then written whole to
+// (uh, vh), and the flags of the one-sided passes at z^t are set.
 __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
   DevState* S = V.S;
   if (S->done) return;
+  const bool greedy = k < 0;
+  if (greedy) k = S->kg;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[2] = {0, 0};      // phi parts
   double xr = 0.0;           // log row sum (w step: log |B|_1 = LSE_i of these)
@@ -379,6 +383,7 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
     } else {
       v[0] = safe_exp(ug) - ug * V.rt[t];
       if (k == 2) { xr = V.lrow[t]; act = true; }
+      if (greedy) V.uh[t] = ug;
     }
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
@@ -390,6 +395,7 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
       v[1] = -vh * V.ct[j];
     } else {
       v[1] = safe_exp(vg) - vg * V.ct[j];
+      if (greedy) V.vh[j] = vg;
     }
   }
   double tot[2], ltot = 0.0;
@@ -405,6 +411,13 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
     S->take_hat = take;
     S->phi_z = take ? ph : S->phi_check;
     S->w_z = take ? wh : S->w_check;
+    if (greedy) {
+      // at z^t = z^ the side of block k follows in closed form: a rows pass
+      // is needed after a v-step, a columns pass after a u-step, none after a
+      // w-step; at z^t = z_check both sides are computed
+      S->run_r3 = take && k == 1;
+      S->run_c3 = take && k == 0;
+    }
   }
 }
 
@@ -476,6 +489,150 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     S->t = it + 1;
     if (tot[3] != 0.0 || !isfinite(E)) S->nonfinite = 1;
     if (E <= S->thr || it + 1 >= S->max_iter || S->nonfinite) S->done = 1;
+  }
+}
+
+// ------------------------------------------------- greedy block rule ---
+// The block choice of Theorem 3's analysis: the block whose Greenkhorn step
+// decreases phi the most.  Those decreases are exact in closed form,
+//   D_u = sum_i rho(r~_i, r_i(B) + e^{u_i}),  D_v = sum_j rho(c~_j, c_j(B) + e^{v_j}),
+//   D_w = rho(s, |B|_1),                       rho(a, b) = b - a + a log(a / b),
+// so one two-sided pass at the point scores all three.  Ties go to the lower
+// block index.
+
+// rho(a, b) from log a and log b
+__device__ __forceinline__ double rho_log(double a, double la, double lb) {
+  return safe_exp(lb) - a + (a > 0.0 ? a * (la - lb) : 0.0);
+}
+__device__ __forceinline__ int pick_block(double du, double dv, double dw) {
+  int k = 0;
+  double best = du;
+  if (dv > best) { k = 1; best = dv; }
+  if (dw > best) k = 2;
+  return k;
+}
+
+// After the two-sided pass at z_grave: S->kg = argmax of the decreases there.
+__global__ void aspot_greedy_pick_kernel(AspotVecs V) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  double xr = 0.0;
+  bool act = false;
+  if (t < V.n) {
+    const double R = V.lrow[t];
+    v[0] = rho_log(V.rt[t], V.lrt[t], logaddexp(R, V.ug[t]));
+    xr = R;
+    act = true;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    v[1] = rho_log(V.ct[j], V.lct[j], logaddexp(V.lcol[j], V.vg[j]));
+  }
+  double tot[2], ltot = 0.0;
+  if (reduce_last_lse<2>(v, xr, act, V.red, V.counter, tot, &ltot) && threadIdx.x == 0)
+    S->kg = pick_block(tot[0], tot[1], rho_log(S->s, S->log_s, ltot));
+}
+
+// Sums of B(z^t) on both sides: from the passes at z^t, or in closed form
+// from the pass at z_grave for the side of the block just stepped (as in
+// aspot_after_final_kernel).
+__device__ __forceinline__ double greedy_row_sum(const AspotVecs& V, int64_t i, int k, int take, double dw) {
+  double R = V.lrow[i];
+  if (take && k == 0) R = clamp_log(R + (V.uh[i] - V.ug[i]));
+  else if (take && k == 2) R = clamp_log(R + dw);
+  return R;
+}
+__device__ __forceinline__ double greedy_col_sum(const AspotVecs& V, int64_t j, int k, int take, double dw) {
+  double Cc = V.lcol[j];
+  if (take && k == 1) Cc = clamp_log(Cc + (V.vh[j] - V.vg[j]));
+  else if (take && k == 2) Cc = clamp_log(Cc + dw);
+  return Cc;
+}
+
+// After the passes at z^t (greedy rule): E_t, the block k2 of the second
+// Greenkhorn step (argmax of the decreases at z^t), phi(z_check^{t+1}) for
+// that block, theta update and the stop test.  z^t is written to (uo, vo);
+// aspot_greedy_apply_kernel then forms z_check^{t+1}.
+__global__ void aspot_greedy_final_kernel(AspotVecs V) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const int k = S->kg, take = S->take_hat;
+  const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // E parts, |B|_1, D_u, D_v, phi parts: rows stepped / kept, columns stepped / kept, nonfinite
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double xr = 0.0;
+  bool act = false;
+  if (t < V.n) {
+    const double uz = take ? V.uh[t] : V.uc[t];
+    const double R = greedy_row_sum(V, t, k, take, dw);
+    xr = R;
+    act = true;
+    const double rB = safe_exp(R), eu = safe_exp(uz), a = V.rt[t];
+    v[0] = fabs(rB + eu - a);
+    v[1] = rB;
+    v[2] = rho_log(a, V.lrt[t], logaddexp(R, uz));
+    v[4] = -(V.lrt[t] - softplus(R - uz)) * a;
+    v[5] = eu - uz * a;
+    V.uo[t] = uz;
+    if (!isfinite(R) && R != POT_NEG_BIG) v[8] = 1;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    const double vz = take ? V.vh[j] : V.vc[j];
+    const double Cc = greedy_col_sum(V, j, k, take, dw);
+    const double cB = safe_exp(Cc), ev = safe_exp(vz), c = V.ct[j];
+    v[0] = fabs(cB + ev - c);
+    v[3] = rho_log(c, V.lct[j], logaddexp(Cc, vz));
+    v[6] = -(V.lct[j] - softplus(Cc - vz)) * c;
+    v[7] = ev - vz * c;
+    V.vo[j] = vz;
+    if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[8] = 1;
+  }
+  double tot[9], ltot = 0.0;
+  if (reduce_last_lse<9>(v, xr, act, V.red, V.counter, tot, &ltot) && threadIdx.x == 0) {
+    const double s = S->s;
+    const double E = fabs(tot[1] - s) + tot[0];
+    const int k2 = pick_block(tot[2], tot[3], rho_log(s, S->log_s, ltot));
+    const double wz = S->w_z;
+    S->w_out = wz;
+    double wc = wz, ph;
+    if (k2 == 0) ph = S->sum_rt + tot[4] + tot[7] - wz * s;
+    else if (k2 == 1) ph = S->sum_ct + tot[5] + tot[6] - wz * s;
+    else { wc = wz + S->log_s - ltot; ph = s + tot[5] + tot[7] - wc * s; }
+    S->k2 = k2;
+    S->w_check = wc;
+    S->phi_check = ph;
+    S->E = E;
+    S->tot = tot[1];
+    const int it = S->t;
+    if (V.trace) {
+      double* tr = S->trace[it & 4095];
+      tr[0] = E; tr[1] = S->phi_z; tr[2] = ph; tr[3] = (double)(take + 2 * k + 8 * k2);
+    }
+    const double th = S->theta;
+    S->theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
+    S->t = it + 1;
+    if (tot[8] != 0.0 || !isfinite(E)) S->nonfinite = 1;
+    if (E <= S->thr || it + 1 >= S->max_iter || S->nonfinite) S->done = 1;
+  }
+}
+
+// z_check^{t+1} = Greenkhorn_{k2}(z^t) (greedy rule); w_check was set by the
+// final kernel.  Skipped once the solve has stopped (z_check is not used then).
+__global__ void aspot_greedy_apply_kernel(AspotVecs V) {
+  DevState* S = V.S;
+  if (S->done) return;
+  const int k = S->kg, take = S->take_hat, k2 = S->k2;
+  const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < V.n) {
+    const double uz = V.uo[t];
+    V.uc[t] = (k2 == 0) ? V.lrt[t] - softplus(greedy_row_sum(V, t, k, take, dw) - uz) : uz;
+  } else if (t < V.n + V.m) {
+    const int64_t j = t - V.n;
+    const double vz = V.vo[j];
+    V.vc[j] = (k2 == 1) ? V.lct[j] - softplus(greedy_col_sum(V, j, k, take, dw) - vz) : vz;
   }
 }
 
@@ -765,6 +922,15 @@ void launch_aspot_after_grad(const AspotVecs& V, cudaStream_t st) {
 }
 void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st) {
   aspot_after_greenkhorn_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, k);
+}
+void launch_aspot_greedy_pick(const AspotVecs& V, cudaStream_t st) {
+  aspot_greedy_pick_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_aspot_greedy_final(const AspotVecs& V, cudaStream_t st) {
+  aspot_greedy_final_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+}
+void launch_aspot_greedy_apply(const AspotVecs& V, cudaStream_t st) {
+  aspot_greedy_apply_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
 }
 void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st) {
   aspot_after_final_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, k);

@@ -117,6 +117,88 @@ def test_aspot_fixed_iterations_match_oracle():
     np.testing.assert_allclose(res.trace[:, 0], ora.trace.E, rtol=1e-3, atol=1e-7)
 
 
+def _greedy_codes(trace):
+    code = np.rint(trace[:, 3]).astype(np.int64)
+    return (code & 1) > 0, (code >> 1) & 3, (code >> 3) & 3
+
+
+def _near_tie(dec, k, mass=1.5, delta=1e-5):
+    """The decrease of block k is within the GPU's error of the largest one.
+    Each decrease D = sum rho(a, b), rho(a, b) = b - a + a log(a/b), is formed
+    from FP32-pass sums b with relative error <= delta; to first order that
+    moves D by delta sum|b - a| <= delta sqrt(2 D sum a) (Cauchy-Schwarz with
+    rho(a, b) ~ (b - a)^2 / (2a)), which near convergence is of the size of D
+    itself, so block choices there are near-ties."""
+    dec = np.asarray(dec, dtype=np.float64)
+    dmax = dec.max()
+    err = delta * (np.sqrt(2 * max(dmax, 0.0) * mass) + np.sqrt(2 * max(dec[k], 0.0) * mass))
+    return dmax - dec[k] <= 1e-12 + 2 * err
+
+
+def test_aspot_greedy_fixed_iterations_match_oracle():
+    """Greedy block rule (the choice in Theorem 3's proof): 60 iterations with
+    the oracle replaying the GPU's argmin and block decisions; every decision
+    the free FP64 run takes differently before the runs part is a near-tie."""
+    pb = W.small_dense(3, n=200, m=233)
+    C = pb.C.astype(np.float64)
+    K = 60
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_TRACE,
+                          check_every=9, block_rule=pkg.BLOCK_GREEDY)
+    assert res.iters == K
+    took, k, k2 = _greedy_codes(res.trace)
+    assert set(k.tolist()) <= {0, 1, 2} and set(k2.tolist()) <= {0, 1, 2}
+    assert len(set(k.tolist())) >= 2            # the rule is not a fixed block on this instance
+    ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, forced_hat=took,
+                  forced_blocks=list(zip(k, k2)), block_rule="greedy", record=True)
+    free = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, block_rule="greedy",
+                   record=True)
+    assert _first_split_is_near_tie(free, took, k, k2)
+    assert ora.trace.k == k.tolist() and ora.trace.k2 == k2.tolist()
+    u, v, w = _np(res.plan.u), _np(res.plan.v), float(res.plan.w.item())
+    np.testing.assert_allclose(u, ora.z.u, rtol=0, atol=2e-5 * (1 + np.abs(ora.z.u).max()))
+    np.testing.assert_allclose(v, ora.z.v, rtol=0, atol=2e-5 * (1 + np.abs(ora.z.v).max()))
+    assert w == pytest.approx(ora.z.w, abs=2e-5 * (1 + abs(ora.z.w)))
+    np.testing.assert_allclose(res.trace[:, 0], ora.trace.E, rtol=1e-3, atol=1e-7)
+
+
+def _first_split_is_near_tie(free, took, k, k2):
+    """Up to the first iteration where the free FP64 greedy run decides
+    differently from the GPU, the decisions agree; that one is a near-tie."""
+    for t in range(min(len(took), len(free.trace.k))):
+        if free.trace.k[t] != k[t]:
+            return _near_tie(free.trace.dec[t][0], k[t])
+        if free.trace.took_hat[t] != took[t]:
+            return abs(free.trace.phi_hat[t] - free.trace.phi_check_next[max(t - 1, 0)]) < 1e-6
+        if free.trace.k2[t] != k2[t]:
+            return _near_tie(free.trace.dec[t][1], k2[t])
+    return True
+
+
+def test_aspot_greedy_converged_matches_oracle():
+    """Greedy rule to the stop threshold on the 256-point workload.  The
+    oracle replays the GPU's decisions for the GPU's iteration count: the
+    objectives agree to 1e-5 relative, the oracle's E_t is below the
+    threshold there too, the plan is feasible, and the free FP64 run parts
+    from the GPU's decisions only at a near-tie."""
+    pb = W.small_dense(0)
+    C = pb.C.astype(np.float64)
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=5000, flags=pkg.FLAG_TRACE,
+                          block_rule=pkg.BLOCK_GREEDY)
+    assert res.status == 0
+    assert res.err_final <= res.eps_stop
+    took, k, k2 = _greedy_codes(res.trace)
+    ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=res.iters, no_stop=True,
+                        block_rule="greedy", forced_hat=took, forced_blocks=list(zip(k, k2)))
+    assert ora.E <= res.eps_stop * (1 + 1e-3)
+    assert abs(res.err_final - ora.E) <= 1e-3 * ora.E
+    assert abs(res.objective - ora.objective) <= 1e-5 * abs(ora.objective)
+    X = _plan_fp64(C, res.plan, res.gamma, res.cost_scale)
+    _check_feasible(X, pb.r, pb.c, pb.s)
+    free = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=res.iters, no_stop=True,
+                   block_rule="greedy", record=True)
+    assert _first_split_is_near_tie(free, took, k, k2)
+
+
 @pytest.mark.parametrize("solver", ["aspot", "sinkhorn"])
 def test_converged_small_dense(solver):
     """The 256-point workload (Section 4.1 stand-in) to the stop threshold."""

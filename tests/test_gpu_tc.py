@@ -82,6 +82,25 @@ def test_tc_fixed_iterations_match_oracle_and_simt():
     assert tc.objective == pytest.approx(si.objective, rel=1e-5)
 
 
+def test_tc_greedy_fixed_iterations_match_oracle():
+    """Greedy block rule on the tcgen05 pass (several tiles, ragged edges):
+    the oracle replays the GPU's argmin and block decisions."""
+    pb, Dm = _cloud(9, 300, 420)
+    C = Dm * pb.cost_scale
+    K = 30
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    res = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_TRACE,
+                          check_every=6, block_rule=pkg.BLOCK_GREEDY)
+    code = np.rint(res.trace[:, 3]).astype(np.int64)
+    took, k, k2 = (code & 1) > 0, (code >> 1) & 3, (code >> 3) & 3
+    ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, forced_hat=took,
+                  forced_blocks=list(zip(k, k2)), block_rule="greedy")
+    u, v = _np(res.plan.u), _np(res.plan.v)
+    np.testing.assert_allclose(u, ora.z.u, rtol=0, atol=2e-4 * (1 + np.abs(ora.z.u).max()))
+    np.testing.assert_allclose(v, ora.z.v, rtol=0, atol=2e-4 * (1 + np.abs(ora.z.v).max()))
+    assert float(res.plan.w.item()) == pytest.approx(ora.z.w, abs=2e-4 * (1 + abs(ora.z.w)))
+
+
 def test_profiled_solve_times_every_pass():
     """POT_FLAG_PROFILE: every main-loop pass timed, results unchanged."""
     pb, Dm = _cloud(11, 200, 260)
