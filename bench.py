@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 N_FULL = 32768
 D_FULL = 128
 CPU_SAMPLE_N = 4096
-CPU_SAMPLE_ITERS = 4        # about 10 s of single-core FP64 work
+CPU_SAMPLE_ITERS = 8        # about 10 s of single-core FP64 work on the GPU host
 # ncu DRAM bytes per launch of the current kernels (null once a kernel changes):
 # dense_pass_kernel<0>, n = m = 16384 FP32 cost: 1.075126 GB read + 11.26 MB written
 DENSE_16K_TRAFFIC = 1.075126e9 + 11.25888e6
