@@ -68,6 +68,8 @@ typedef enum {
 #define POT_FLAG_FORCE_SIMT 16    /* use the CUDA-core pass even where the tcgen05 pass applies */
 #define POT_FLAG_PROFILE 32       /* time every main-loop pass with CUDA events (res->pass_ms, pass_launches) */
 #define POT_FLAG_WARM_CHECK 64    /* with u0 / v0: start from zero instead when E(z_warm) > E(0) (res->warm_used) */
+#define POT_FLAG_AUTOTUNE 128     /* aspot_solve_batched: tile shape of the batched pass from the autotune cache,
+                                     else the fastest candidate timed on this batch (then cached) */
 
 typedef struct {
   int64_t n, m;
@@ -125,7 +127,11 @@ typedef struct {            /* host struct filled by the solvers */
   double err_warm;          /* POT_FLAG_WARM_CHECK: E at the given start (u0, v0, w0) */
   double err_zero;          /* POT_FLAG_WARM_CHECK: E at the zero start */
   int32_t warm_used;        /* 1 if the iterations started from (u0, v0, w0) */
+  int32_t tile_rows;        /* aspot_solve_batched: rows x columns of the batched pass's tiles */
+  int32_t tile_cols;
   int32_t pad;
+  double tune_ms;           /* aspot_solve_batched, POT_FLAG_AUTOTUNE: device time spent timing candidates
+                               (0 when the shape came from the cache) */
 } pot_result;
 
 /* Bytes of device workspace the solvers / pot_round / pot_objective /
@@ -179,6 +185,28 @@ POT_API pot_status pot_workspace_size_batched(const pot_problem* probs, int32_t 
 POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, const pot_params* params,
                                        void* workspace, size_t ws_bytes, pot_plan* plans, pot_result* res,
                                        void* stream);
+
+/* Autotuner of the batched pass.  A tile is tile_rows x tile_cols entries of
+ * one instance, handled by one CTA; the candidates are 32, 64, 128, 256 rows
+ * x 128, 256 columns (default 32 x 256).  With POT_FLAG_AUTOTUNE,
+ * aspot_solve_batched takes the shape cached for the batch's signature (cost
+ * kind, largest d, count, total and largest n and m) or, on a miss, times
+ * every candidate on one two-sided pass of this batch (CUDA events, three
+ * repetitions after a warm-up; the call synchronises its stream) and caches
+ * the fastest.  The cache lives in the process; access is thread-safe.
+ *   pot_autotune_set:    pin a shape for the signature of `probs` (POT_EINVAL
+ *                        for a shape outside the candidates);
+ *   pot_autotune_lookup: the cached shape (host outs), 0 x 0 when none;
+ *   pot_autotune_clear:  drop every entry;
+ *   pot_autotune_save / _load: the cache as text lines "signature rows cols"
+ *                        (load merges; POT_EINVAL for an unreadable or
+ *                        malformed file, which then leaves the cache as it was). */
+POT_API pot_status pot_autotune_set(const pot_problem* probs, int32_t count, int32_t tile_rows, int32_t tile_cols);
+POT_API pot_status pot_autotune_lookup(const pot_problem* probs, int32_t count, int32_t* tile_rows /* host */,
+                                       int32_t* tile_cols /* host */);
+POT_API pot_status pot_autotune_clear(void);
+POT_API pot_status pot_autotune_save(const char* path);
+POT_API pot_status pot_autotune_load(const char* path);
 
 /* pot_marginals without a workspace, for callers that cannot allocate
  * device memory (for example while a framework's caching allocator owns the

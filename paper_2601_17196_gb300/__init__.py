@@ -28,6 +28,13 @@ from .binding import (  # noqa: F401
     FLAG_NO_STOP,
     FLAG_FORCE_SIMT,
     FLAG_PROFILE,
+    FLAG_WARM_CHECK,
+    FLAG_AUTOTUNE,
+    autotune_set,
+    autotune_lookup,
+    autotune_clear,
+    autotune_save,
+    autotune_load,
     COST_DENSE_F32,
     COST_SQEUCLID_BF16,
     COST_SQEUCLID_F16,

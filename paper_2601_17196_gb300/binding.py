@@ -23,6 +23,7 @@ FLAG_NO_STOP = 8
 FLAG_FORCE_SIMT = 16
 FLAG_PROFILE = 32
 FLAG_WARM_CHECK = 64
+FLAG_AUTOTUNE = 128
 
 COST_DENSE_F32 = 0
 COST_SQEUCLID_BF16 = 1
@@ -39,7 +40,8 @@ EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_roun
             "aspot_solve_batched", "pot_marginals_static", "pot_ws_param_count", "pot_ws_init",
             "pot_ws_features_workspace_size", "pot_ws_features", "pot_ws_targets", "pot_ws_workspace_size", "pot_ws_forward", "pot_ws_gradient",
             "pot_ws_train_step", "pot_ws_warm_workspace_size", "pot_ws_warm_start", "pot_rigid_workspace_size",
-            "pot_rigid_fit", "pot_rigid_apply", "pot_last_error"]
+            "pot_rigid_fit", "pot_rigid_apply", "pot_autotune_set", "pot_autotune_lookup", "pot_autotune_clear",
+            "pot_autotune_save", "pot_autotune_load", "pot_last_error"]
 
 
 class PotError(RuntimeError):
@@ -81,7 +83,8 @@ class _Result(ct.Structure):
                 ("rounding_branch", ct.c_int32), ("nonfinite", ct.c_int32),
                 ("pass_ms", ct.c_double), ("pass_launches", ct.c_int64), ("kernel_launches", ct.c_int64),
                 ("err_warm", ct.c_double), ("err_zero", ct.c_double), ("warm_used", ct.c_int32),
-                ("pad", ct.c_int32)]
+                ("tile_rows", ct.c_int32), ("tile_cols", ct.c_int32), ("pad", ct.c_int32),
+                ("tune_ms", ct.c_double)]
 
 
 _lib_handle = None
@@ -124,6 +127,11 @@ def lib() -> ct.CDLL:
         L.pot_rigid_workspace_size.argtypes = [i32, ct.POINTER(sz)]
         L.pot_rigid_fit.argtypes = [P, i32, PL, dbl, vp, vp, vp, sz, vp]
         L.pot_rigid_apply.argtypes = [P, i32, vp, vp, vp, sz, vp]
+        L.pot_autotune_set.argtypes = [P, i32, i32, i32]
+        L.pot_autotune_lookup.argtypes = [P, i32, ct.POINTER(i32), ct.POINTER(i32)]
+        L.pot_autotune_clear.argtypes = []
+        L.pot_autotune_save.argtypes = [ct.c_char_p]
+        L.pot_autotune_load.argtypes = [ct.c_char_p]
         L.pot_last_error.restype = ct.c_char_p
         for name in EXPORTED[:-1]:
             getattr(L, name).restype = ct.c_int
@@ -249,6 +257,9 @@ class SolveResult:
     err_warm: float = 0.0
     err_zero: float = 0.0
     warm_used: int = 0
+    tile_rows: int = 0
+    tile_cols: int = 0
+    tune_ms: float = 0.0
 
 
 _side_streams = {}
@@ -452,5 +463,34 @@ def aspot_solve_batched(probs, gamma: float, eps: float, max_iter: int = 10000, 
         r = rarr[k]
         out.append(SolveResult(r.status, r.iters, r.objective, r.err_final, r.eps_stop, r.gamma, r.cost_scale,
                                r.mass, r.ms, r.rounding_branch, r.nonfinite, plans[k], None, r.pass_ms,
-                               r.pass_launches, r.kernel_launches))
+                               r.pass_launches, r.kernel_launches, tile_rows=r.tile_rows, tile_cols=r.tile_cols,
+                               tune_ms=r.tune_ms))
     return out
+
+
+def _prob_array(probs):
+    return (_Problem * len(probs))(*[p.struct() for p in probs])
+
+
+def autotune_set(probs, tile_rows: int, tile_cols: int) -> None:
+    """Pin the batched pass's tile shape for the signature of this batch."""
+    _check(lib().pot_autotune_set(_prob_array(probs), len(probs), int(tile_rows), int(tile_cols)))
+
+
+def autotune_lookup(probs) -> tuple:
+    """Cached (tile_rows, tile_cols) for this batch's signature, (0, 0) if none."""
+    h, w = ct.c_int32(0), ct.c_int32(0)
+    _check(lib().pot_autotune_lookup(_prob_array(probs), len(probs), ct.byref(h), ct.byref(w)))
+    return int(h.value), int(w.value)
+
+
+def autotune_clear() -> None:
+    _check(lib().pot_autotune_clear())
+
+
+def autotune_save(path: str) -> None:
+    _check(lib().pot_autotune_save(os.fsencode(path)))
+
+
+def autotune_load(path: str) -> None:
+    _check(lib().pot_autotune_load(os.fsencode(path)))

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "../../include/aspot.h"
 #include "common.cuh"
@@ -30,8 +32,8 @@ using namespace pot;
 namespace {
 
 constexpr int kBT = 512;       // threads of a per-instance CTA
-constexpr int kH = 32;         // rows of a batched tile (8 warps x 4 rows)
-constexpr int kW = 256;        // columns of a batched tile
+constexpr int kH = 32;         // default rows of a batched tile (8 warps x 4 rows)
+constexpr int kW = 256;        // default columns of a batched tile
 
 template <int NV>
 __device__ void block_sums(double (&v)[NV]) {
@@ -431,8 +433,39 @@ __global__ void b_clear_kernel(float2* a, int64_t na, float2* b, int64_t nb) {
 
 // ----------------------------------------------------------------- host ---
 
+// Tile geometry of the batched pass: H rows x W columns per CTA, the work
+// list in instance order, and the partial strides the combines read.
+struct Geom {
+  int H = kH, W = kW;
+  int64_t T = 0, maxcb = 0, maxrb = 0;
+  std::vector<BTile> tiles;
+  std::vector<int64_t> tile0, ntile;
+};
+
+Geom b_geom(const pot_problem* P, int count, int H, int W) {
+  Geom G;
+  G.H = H; G.W = W;
+  G.tile0.resize(count); G.ntile.resize(count);
+  for (int k = 0; k < count; ++k) {
+    const int64_t nrb = (P[k].n + H - 1) / H, ncb = (P[k].m + W - 1) / W;
+    G.tile0[k] = G.T; G.ntile[k] = nrb * ncb;
+    G.T += nrb * ncb;
+    G.maxcb = std::max(G.maxcb, ncb); G.maxrb = std::max(G.maxrb, nrb);
+    for (int64_t rb = 0; rb < nrb; ++rb)
+      for (int64_t cb = 0; cb < ncb; ++cb) G.tiles.push_back(BTile{k, (int32_t)rb, (int32_t)cb, 0});
+  }
+  return G;
+}
+
+// Candidate tile shapes of the autotuner (rows a multiple of 32: eight warps
+// of four-row chunks; columns 128 or 256: one or two float4 groups per lane).
+// The smallest of each dimension bounds every workspace region.
+constexpr int kCandH[] = {32, 64, 128, 256};
+constexpr int kCandW[] = {128, 256};
+constexpr int kMinH = 32, kMinW = 128;
+
 struct BLayout {
-  int64_t N = 0, M = 0, T = 0, maxcb = 0, maxrb = 0;
+  int64_t N = 0, M = 0, T = 0, maxcb = 0, maxrb = 0;   // worst case over the candidate shapes
   size_t off_inst, off_tiles, off_cnt, off_xn, off_yn, off_rowp, off_colp, off_red, off_u[16], off_v[16], total;
   size_t off_rowA, off_colA, off_colB;
 };
@@ -440,15 +473,12 @@ struct BLayout {
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr int kBSlots = 10;   // rt lrt ut uc ub ug uh lrow + spare
 
-BLayout b_layout(const pot_problem* P, int count, std::vector<BTile>* tiles) {
+BLayout b_layout(const pot_problem* P, int count) {
   BLayout L;
   for (int k = 0; k < count; ++k) {
-    const int64_t nrb = (P[k].n + kH - 1) / kH, ncb = (P[k].m + kW - 1) / kW;
+    const int64_t nrb = (P[k].n + kMinH - 1) / kMinH, ncb = (P[k].m + kMinW - 1) / kMinW;
     L.N += P[k].n; L.M += P[k].m; L.T += nrb * ncb;
     L.maxcb = std::max(L.maxcb, ncb); L.maxrb = std::max(L.maxrb, nrb);
-    if (tiles)
-      for (int64_t rb = 0; rb < nrb; ++rb)
-        for (int64_t cb = 0; cb < ncb; ++cb) tiles->push_back(BTile{k, (int32_t)rb, (int32_t)cb, 0});
   }
   size_t o = 0;
   L.off_inst = o; o = al(o + sizeof(BInst) * count);
@@ -469,6 +499,34 @@ BLayout b_layout(const pot_problem* P, int count, std::vector<BTile>* tiles) {
 }
 
 pot_status bfail(pot_status s, const char* msg) { return set_last_error(s, msg); }
+
+// ---------------------------------------------------------- autotuner ---
+// Tile shapes chosen per batch signature (cost kind, largest d, number of
+// instances, total and largest n and m), kept for the process; save / load
+// write them as text lines "signature H W".
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;
+
+std::string batch_signature(const pot_problem* P, int count) {
+  int64_t N = 0, M = 0, nmax = 0, mmax = 0;
+  int dmax = 0;
+  for (int k = 0; k < count; ++k) {
+    N += P[k].n; M += P[k].m;
+    nmax = std::max<int64_t>(nmax, P[k].n); mmax = std::max<int64_t>(mmax, P[k].m);
+    dmax = std::max<int>(dmax, P[k].d);
+  }
+  char b[160];
+  snprintf(b, sizeof(b), "k%d_d%d_c%d_N%lld_M%lld_n%lld_m%lld", (int)P[0].kind, dmax, count, (long long)N,
+           (long long)M, (long long)nmax, (long long)mmax);
+  return b;
+}
+
+bool valid_shape(int H, int W) {
+  bool h = false, w = false;
+  for (int x : kCandH) h |= (x == H);
+  for (int x : kCandW) w |= (x == W);
+  return h && w;
+}
 
 pot_status check_batch(const pot_problem* probs, int32_t count) {
   if (!probs || count < 1) return bfail(POT_EINVAL, "batched: probs must be a host array of count >= 1 problems");
@@ -505,7 +563,63 @@ POT_API pot_status pot_workspace_size_batched(const pot_problem* probs, int32_t 
   pot_status s = check_batch(probs, count);
   if (s != POT_OK) return s;
   if (!bytes) return bfail(POT_EINVAL, "bytes is NULL");
-  *bytes = b_layout(probs, count, nullptr).total;
+  *bytes = b_layout(probs, count).total;
+  return POT_OK;
+}
+
+POT_API pot_status pot_autotune_set(const pot_problem* probs, int32_t count, int32_t tile_rows, int32_t tile_cols) {
+  pot_status s = check_batch(probs, count);
+  if (s != POT_OK) return s;
+  if (!valid_shape(tile_rows, tile_cols))
+    return bfail(POT_EINVAL, "autotune: tile_rows must be 32, 64, 128 or 256 and tile_cols 128 or 256");
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[batch_signature(probs, count)] = {tile_rows, tile_cols};
+  return POT_OK;
+}
+
+POT_API pot_status pot_autotune_lookup(const pot_problem* probs, int32_t count, int32_t* tile_rows,
+                                       int32_t* tile_cols) {
+  pot_status s = check_batch(probs, count);
+  if (s != POT_OK) return s;
+  if (!tile_rows || !tile_cols) return bfail(POT_EINVAL, "autotune: NULL output");
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find(batch_signature(probs, count));
+  if (it == g_tune.end()) { *tile_rows = 0; *tile_cols = 0; return POT_OK; }
+  *tile_rows = it->second.first; *tile_cols = it->second.second;
+  return POT_OK;
+}
+
+POT_API pot_status pot_autotune_clear(void) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune.clear();
+  return POT_OK;
+}
+
+POT_API pot_status pot_autotune_save(const char* path) {
+  if (!path) return bfail(POT_EINVAL, "autotune: path is NULL");
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  FILE* f = fopen(path, "w");
+  if (!f) return bfail(POT_EINVAL, "autotune: cannot open the file for writing");
+  for (const auto& e : g_tune) fprintf(f, "%s %d %d\n", e.first.c_str(), e.second.first, e.second.second);
+  const bool ok = fclose(f) == 0;
+  return ok ? POT_OK : bfail(POT_EINVAL, "autotune: write failed");
+}
+
+POT_API pot_status pot_autotune_load(const char* path) {
+  if (!path) return bfail(POT_EINVAL, "autotune: path is NULL");
+  FILE* f = fopen(path, "r");
+  if (!f) return bfail(POT_EINVAL, "autotune: cannot open the file");
+  std::map<std::string, std::pair<int, int>> got;
+  char key[160];
+  int H = 0, W = 0, r;
+  while ((r = fscanf(f, "%159s %d %d", key, &H, &W)) == 3) {
+    if (!valid_shape(H, W)) { fclose(f); return bfail(POT_EINVAL, "autotune: bad tile shape in the file"); }
+    got[key] = {H, W};
+  }
+  fclose(f);
+  if (r != EOF) return bfail(POT_EINVAL, "autotune: malformed line in the file");
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (const auto& e : got) g_tune[e.first] = e.second;
   return POT_OK;
 }
 
@@ -524,9 +638,9 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
       return bfail(POT_EINVAL, "batched: every plan pointer must be a device buffer");
   }
   if (!workspace || (uintptr_t)workspace % 256) return bfail(POT_EINVAL, "batched: workspace NULL or not 256-byte aligned");
-  std::vector<BTile> tiles;
-  const BLayout L = b_layout(probs, count, &tiles);
+  const BLayout L = b_layout(probs, count);
   if (ws_bytes < L.total) return bfail(POT_ENOMEM, "batched: workspace too small");
+  Geom G = b_geom(probs, count, kH, kW);
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   BInst* dinst = (BInst*)(ws + L.off_inst);
@@ -548,23 +662,22 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
 
   // instance table
   std::vector<BInst> hi(count);
-  int64_t r0 = 0, c0 = 0, t0 = 0;
+  int64_t r0 = 0, c0 = 0;
   for (int k = 0; k < count; ++k) {
     const pot_problem& p = probs[k];
     BInst& I = hi[k];
     memset(&I, 0, sizeof(I));
     I.n = p.n; I.m = p.m; I.row0 = r0; I.col0 = c0;
-    const int64_t nt = ((p.n + kH - 1) / kH) * ((p.m + kW - 1) / kW);
-    I.tile0 = t0; I.ntile = nt;
+    I.tile0 = G.tile0[k]; I.ntile = G.ntile[k];
     I.X = p.X; I.Y = p.Y; I.d = p.d; I.kind = p.kind; I.ldx = p.ldx; I.ldy = p.ldy;
     I.r = p.r; I.c = p.c; I.s = p.s; I.cost_scale = p.cost_scale;
     I.max_iter = params->max_iter;
     I.pu = plans[k].u; I.pv = plans[k].v; I.pw = plans[k].w; I.pf = plans[k].f; I.pg = plans[k].g;
     I.pp = plans[k].p; I.pq = plans[k].q; I.pkappa = plans[k].kappa;
-    r0 += p.n; c0 += p.m; t0 += nt;
+    r0 += p.n; c0 += p.m;
   }
   BCK(cudaMemcpyAsync(dinst, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, st));
-  BCK(cudaMemcpyAsync(dtiles, tiles.data(), sizeof(BTile) * L.T, cudaMemcpyHostToDevice, st));
+  BCK(cudaMemcpyAsync(dtiles, G.tiles.data(), sizeof(BTile) * G.T, cudaMemcpyHostToDevice, st));
   BCK(cudaMemsetAsync(ndone, 0, 64, st));
 
   BVecs V{};
@@ -577,7 +690,8 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   V.uo = U[8]; V.vo = Vv[8]; V.fc = U[9]; V.gc = Vv[9];
 
   BatchPass B{};
-  B.kind = probs[0].kind; B.H = kH; B.Ntot = L.N; B.Mtot = L.M; B.tiles = dtiles; B.ntiles = L.T; B.inst = dinst;
+  B.kind = probs[0].kind; B.H = G.H; B.W = G.W; B.Ntot = L.N; B.Mtot = L.M; B.tiles = dtiles; B.ntiles = G.T;
+  B.inst = dinst;
   B.xn = xn; B.yn = yn; B.row_part = rowp; B.col_part = colp; B.red_part = red; B.aoff0 = -1; B.aoff1 = -1;
   B.count = count;
   B.rowA = (float4*)(ws + L.off_rowA); B.colA = (float2*)(ws + L.off_colA); B.colB = (float2*)(ws + L.off_colB);
@@ -590,7 +704,7 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
     q.mode = mode; q.arow0 = a0; q.bcol0 = b0; q.aoff0 = w0; q.arow1 = a1; q.bcol1 = b1; q.aoff1 = w1;
     q.use_sel = use_sel;
     if (mode & (PASS_ROWS | PASS_COLS)) {
-      const int64_t na = (mode & PASS_ROWS) ? L.maxcb * L.N : 0, nb = (mode & PASS_COLS) ? L.maxrb * L.M : 0;
+      const int64_t na = (mode & PASS_ROWS) ? G.maxcb * L.N : 0, nb = (mode & PASS_COLS) ? G.maxrb * L.M : 0;
       b_clear_kernel<<<(unsigned)((na + nb + 255) / 256), 256, 0, st>>>(rowp, na, colp, nb);
       ++launches;
     }
@@ -601,7 +715,7 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
     launch_pass_simt_batched(q, st);
     ++launches;
     if (mode & (PASS_ROWS | PASS_COLS)) {
-      launch_combine(rowp, L.maxcb, L.N, (mode & PASS_ROWS) ? lrow : nullptr, colp, L.maxrb, L.M,
+      launch_combine(rowp, G.maxcb, L.N, (mode & PASS_ROWS) ? lrow : nullptr, colp, G.maxrb, L.M,
                      (mode & PASS_COLS) ? lcol : nullptr, nullptr, st);
       ++launches;
     }
@@ -644,6 +758,54 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
     I.log_s = log(I.s);
   }
   BCK(cudaMemcpyAsync(dinst, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, st));
+
+  // tile shape: a pinned or earlier choice for this batch signature, else
+  // (POT_FLAG_AUTOTUNE) the fastest candidate, timed with CUDA events on a
+  // two-sided pass at the zero dual point (a pass's cost does not depend on
+  // the potentials)
+  float tune_ms = 0.f;
+  if (params->flags & POT_FLAG_AUTOTUNE) {
+    const std::string sig = batch_signature(probs, count);
+    int th = 0, tw = 0;
+    {
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      auto it = g_tune.find(sig);
+      if (it != g_tune.end()) { th = it->second.first; tw = it->second.second; }
+    }
+    if (th == 0) {
+      cudaEvent_t a, b;
+      BCK(cudaEventCreate(&a));
+      BCK(cudaEventCreate(&b));
+      BCK(cudaMemsetAsync(V.ut, 0, sizeof(double) * L.N, st));
+      BCK(cudaMemsetAsync(V.vt, 0, sizeof(double) * L.M, st));
+      float best = 3.4e38f;
+      for (int cw : kCandW)
+        for (int ch : kCandH) {
+          G = b_geom(probs, count, ch, cw);
+          BCK(cudaMemcpyAsync(dtiles, G.tiles.data(), sizeof(BTile) * G.T, cudaMemcpyHostToDevice, st));
+          B.H = G.H; B.W = G.W; B.ntiles = G.T;
+          if ((s = pass(PASS_ROWS | PASS_COLS, V.ut, V.vt, -1, nullptr, nullptr, -1, 0)) != POT_OK) return s;
+          BCK(cudaEventRecord(a, st));
+          for (int rep = 0; rep < 3; ++rep)
+            if ((s = pass(PASS_ROWS | PASS_COLS, V.ut, V.vt, -1, nullptr, nullptr, -1, 0)) != POT_OK) return s;
+          BCK(cudaEventRecord(b, st));
+          BCK(cudaEventSynchronize(b));
+          float t = 0.f;
+          BCK(cudaEventElapsedTime(&t, a, b));
+          tune_ms += t;
+          if (t < best) { best = t; th = ch; tw = cw; }
+        }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tune[sig] = {th, tw};
+    }
+    G = b_geom(probs, count, th, tw);
+    for (int k = 0; k < count; ++k) { hi[k].tile0 = G.tile0[k]; hi[k].ntile = G.ntile[k]; }
+    BCK(cudaMemcpyAsync(dinst, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, st));
+    BCK(cudaMemcpyAsync(dtiles, G.tiles.data(), sizeof(BTile) * G.T, cudaMemcpyHostToDevice, st));
+    B.H = G.H; B.W = G.W; B.ntiles = G.T;
+  }
   b_init_kernel<<<count, kBT, 0, st>>>(V);
   ++launches;
 
@@ -749,6 +911,9 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
     R.rounding_branch = I.branch;
     R.nonfinite = I.nonfinite;
     R.kernel_launches = launches;
+    R.tile_rows = G.H;
+    R.tile_cols = G.W;
+    R.tune_ms = tune_ms;
     R.status = I.nonfinite ? POT_ENONFINITE
                            : ((I.E <= I.thr || (params->flags & POT_FLAG_NO_STOP)) ? POT_OK : POT_ENOCONV);
     if (R.status == POT_ENONFINITE) worst = POT_ENONFINITE;

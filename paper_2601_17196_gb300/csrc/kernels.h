@@ -119,7 +119,7 @@ struct BInst {
 };
 struct BTile { int32_t inst, rb, cb, pad; };
 struct BatchPass {
-  int mode, kind, H, vec;
+  int mode, kind, H, W;                                // W: tile columns, 128 or 256
   int64_t Ntot, Mtot;
   const BTile* tiles; int64_t ntiles;
   BInst* inst; int64_t count;

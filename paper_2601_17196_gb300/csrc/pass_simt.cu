@@ -570,9 +570,10 @@ void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
   }
 }
 
-// Batched pass: one CTA per tile of the work list; the tile's instance
-// supplies sizes, points, offsets and its scalar potentials.
-template <int KIND, bool VEC>
+// Batched pass: one CTA per tile of the work list (H rows x 128 V columns);
+// the tile's instance supplies sizes, points, offsets and its scalar
+// potentials.
+template <int KIND, int V>
 __global__ void __launch_bounds__(kThreads) pass_simt_batched_kernel(BatchPass B) {
   const BTile tl = B.tiles[blockIdx.x];
   BInst* I = B.inst + tl.inst;
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(kThreads) pass_simt_batched_kernel(BatchPass B
   P.rowA = B.rowA + I->row0;
   P.colA = B.colA + I->col0;
   P.colB = B.colB + I->col0;
-  simt_tile<KIND, 2, 4, VEC>(P, B.H, tl.cb, tl.rb, B.Ntot, B.Mtot, blockIdx.x);
+  simt_tile<KIND, V, 4, false>(P, B.H, tl.cb, tl.rb, B.Ntot, B.Mtot, blockIdx.x);
 }
 
 // Batched counterpart of prep_kernel: one CTA per instance.
@@ -634,13 +635,19 @@ void launch_prep_batched(const BatchPass& B, cudaStream_t st) {
   prep_batched_kernel<<<(unsigned)B.count, 512, 0, st>>>(B);
 }
 
-void launch_pass_simt_batched(const BatchPass& B, cudaStream_t st) {
+template <int V>
+void launch_batched_v(const BatchPass& B, cudaStream_t st) {
   const unsigned g = (unsigned)B.ntiles;
   switch (B.kind) {
-    case COST_SQEUCLID_BF16: pass_simt_batched_kernel<COST_SQEUCLID_BF16, false><<<g, kThreads, 0, st>>>(B); break;
-    case COST_SQEUCLID_F16: pass_simt_batched_kernel<COST_SQEUCLID_F16, false><<<g, kThreads, 0, st>>>(B); break;
-    default: pass_simt_batched_kernel<COST_SQEUCLID_F32, false><<<g, kThreads, 0, st>>>(B); break;
+    case COST_SQEUCLID_BF16: pass_simt_batched_kernel<COST_SQEUCLID_BF16, V><<<g, kThreads, 0, st>>>(B); break;
+    case COST_SQEUCLID_F16: pass_simt_batched_kernel<COST_SQEUCLID_F16, V><<<g, kThreads, 0, st>>>(B); break;
+    default: pass_simt_batched_kernel<COST_SQEUCLID_F32, V><<<g, kThreads, 0, st>>>(B); break;
   }
+}
+
+void launch_pass_simt_batched(const BatchPass& B, cudaStream_t st) {
+  if (B.W == 128) launch_batched_v<1>(B, st);
+  else launch_batched_v<2>(B, st);
 }
 
 SimtLayout simt_layout(int64_t n, int64_t m) {

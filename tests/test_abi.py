@@ -100,3 +100,51 @@ def test_warm_start_argument_checks(libpath):
     assert b"mode" in L.pot_last_error()
     assert L.pot_ws_gradient(ct.byref(s), idx.ctypes.data_as(ct.c_void_p), 2, 8, 0, 8, 8, 256, b.value, None) == 1
     assert b"target" in L.pot_last_error()
+
+
+def _fake_batch(B, sizes, kind=3, d=3):
+    """Host-side problem structs (placeholder device pointers: the autotune
+    cache calls only read sizes and validate arguments)."""
+    import ctypes as ct
+    arr = (B._Problem * len(sizes))()
+    for k, (n, m) in enumerate(sizes):
+        p = arr[k]
+        p.n, p.m, p.kind, p.d, p.ldx, p.ldy, p.s = n, m, kind, d, d, d, 0.5
+        p.X, p.Y, p.r, p.c = 16, 16, 16, 16
+    return arr
+
+
+def test_autotune_cache_calls(libpath, tmp_path):
+    """Pin / look up / save / clear / load of the batched pass's tile shapes
+    (host only), and the argument checks."""
+    import ctypes as ct
+    from paper_2601_17196_gb300 import binding as B
+    L = B.lib()
+    assert L.pot_autotune_clear() == 0
+    a = _fake_batch(B, [(100, 120), (64, 2048)])
+    b = _fake_batch(B, [(100, 121), (64, 2048)])
+    h, w = ct.c_int32(-1), ct.c_int32(-1)
+    assert L.pot_autotune_lookup(a, 2, ct.byref(h), ct.byref(w)) == 0 and (h.value, w.value) == (0, 0)
+    assert L.pot_autotune_set(a, 2, 64, 128) == 0
+    assert L.pot_autotune_set(b, 2, 256, 256) == 0
+    assert L.pot_autotune_lookup(a, 2, ct.byref(h), ct.byref(w)) == 0 and (h.value, w.value) == (64, 128)
+    assert L.pot_autotune_lookup(b, 2, ct.byref(h), ct.byref(w)) == 0 and (h.value, w.value) == (256, 256)
+    for bad in ((48, 128), (64, 64), (0, 256), (512, 256)):
+        assert L.pot_autotune_set(a, 2, *bad) == 1
+    assert L.pot_autotune_set(_fake_batch(B, [(100, 120)], d=5), 1, 32, 256) == 1      # d > 4: not batched
+    path = str(tmp_path / "tiles.txt")
+    assert L.pot_autotune_save(path.encode()) == 0
+    lines = open(path).read().split("\n")
+    assert len([ln for ln in lines if ln]) == 2
+    assert L.pot_autotune_clear() == 0
+    assert L.pot_autotune_lookup(a, 2, ct.byref(h), ct.byref(w)) == 0 and h.value == 0
+    assert L.pot_autotune_load(path.encode()) == 0
+    assert L.pot_autotune_lookup(b, 2, ct.byref(h), ct.byref(w)) == 0 and (h.value, w.value) == (256, 256)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("k3_d3_c1_N5_M5_n5_m5 48 256\n")
+    assert L.pot_autotune_load(str(bad).encode()) == 1
+    bad.write_text("k3_d3_c1_N5_M5_n5_m5 32\n")
+    assert L.pot_autotune_load(str(bad).encode()) == 1
+    assert L.pot_autotune_load(str(tmp_path / "missing.txt").encode()) == 1
+    assert L.pot_autotune_lookup(a, 2, ct.byref(h), ct.byref(w)) == 0 and (h.value, w.value) == (64, 128)
+    assert L.pot_autotune_clear() == 0

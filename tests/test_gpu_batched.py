@@ -54,3 +54,54 @@ def test_batched_fixed_iterations_and_invalid_mix():
     with pytest.raises(pkg.PotError) as e:
         pkg.aspot_solve_batched(bad, 0.05, 1e-3)
     assert e.value.status == 1
+
+
+def _batch_probs(seed, count, nmin, nmax):
+    insts = W.batch_3d(seed=seed, count=count, nmin=nmin, nmax=nmax)
+    return insts, [pkg.DeviceProblem.from_workload(pb, device="cuda") for pb in insts]
+
+
+def test_batched_every_tile_shape_matches_default():
+    """Each candidate tile shape of the autotuner (pinned through the cache)
+    follows the default 32 x 256 tiles' iterates: the shape only changes the
+    FP32 summation order of the partials.  60 fixed iterations agree to the
+    parity tolerance, and every shape solves every instance to its threshold
+    (where E_t is not monotone, so its first crossing may move by a few
+    iterations)."""
+    insts, probs = _batch_probs(8, 10, 64, 900)
+    K = 60
+    base = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=K, flags=pkg.FLAG_NO_STOP, check_every=6)
+    assert all(r.tile_rows == 32 and r.tile_cols == 256 for r in base)
+    ub = [r.plan.u.cpu().numpy() for r in base]
+    vb = [r.plan.v.cpu().numpy() for r in base]
+    for H in (32, 64, 128, 256):
+        for Wc in (128, 256):
+            pkg.autotune_clear()
+            pkg.autotune_set(probs, H, Wc)
+            res = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_AUTOTUNE,
+                                          check_every=6)
+            for k, r in enumerate(res):
+                assert (r.tile_rows, r.tile_cols) == (H, Wc) and r.tune_ms == 0.0 and r.iters == K
+                np.testing.assert_allclose(r.plan.u.cpu().numpy(), ub[k], rtol=0, atol=2e-5 * (1 + np.abs(ub[k]).max()))
+                np.testing.assert_allclose(r.plan.v.cpu().numpy(), vb[k], rtol=0, atol=2e-5 * (1 + np.abs(vb[k]).max()))
+            conv = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000, flags=pkg.FLAG_AUTOTUNE)
+            assert all(r.status == 0 and r.err_final <= r.eps_stop for r in conv)
+    pkg.autotune_clear()
+
+
+def test_batched_autotune_times_candidates_then_caches():
+    insts, probs = _batch_probs(9, 40, 64, 2048)
+    pkg.autotune_clear()
+    first = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000, flags=pkg.FLAG_AUTOTUNE)
+    shape = (first[0].tile_rows, first[0].tile_cols)
+    assert shape[0] in (32, 64, 128, 256) and shape[1] in (128, 256)
+    assert first[0].tune_ms > 0.0
+    assert pkg.autotune_lookup(probs) == shape
+    again = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000, flags=pkg.FLAG_AUTOTUNE)
+    assert (again[0].tile_rows, again[0].tile_cols) == shape and again[0].tune_ms == 0.0
+    for pb, r in zip(insts[:5], again[:5]):
+        C = O.sqeuclid_cost(pb.X, pb.Y, 0.0)
+        ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=r.iters, no_stop=True)
+        assert r.status == 0
+        assert abs(r.objective - ora.objective) <= 1e-5 * abs(ora.objective)
+    pkg.autotune_clear()
