@@ -622,18 +622,31 @@ def run_registration(args):
         X, Y0, Rt, tt = W.registration_3d(seed, n=1024, frac=0.5, max_angle=0.25, max_shift=0.08)
         pairs.append((X, Y0))
         truth.append((Rt, tt))
-    PR.register_batched(pairs[:2], alpha=0.6, max_reg=2)          # warm-up (build, caches)
+    PR.register_batched(pairs[:2], alpha=0.6, max_reg=2, autotune=False)          # warm-up (build, caches)
     torch.cuda.synchronize()
     t0 = time.time()
-    out = PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=40)
+    out = PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=40,
+                              autotune=False)
     torch.cuda.synchronize()
     wall = time.time() - t0
     err = np.array([max(np.abs(r.R - Rt).max(), np.abs(r.t - tt).max()) for r, (Rt, tt) in zip(out, truth)])
     regs = np.array([r.registrations for r in out])
     inner = np.array([r.inner_iterations for r in out])
+    # autotuned tiles: the first run times each new set of active pairs, the second hits the cache
+    import paper_2601_17196_gb300 as pkg
+    pkg.autotune_clear()
+    tune = {}
+    for leg in ("first_call_s", "wall_s"):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=40,
+                            autotune=True)
+        torch.cuda.synchronize()
+        tune[leg] = time.time() - t0
+    tune["vs_default_tile"] = tune["wall_s"] / wall
     print(json.dumps({"workload": "registration: 64 pairs, target n=1024 (3 ellipsoid surfaces), source = half, "
                                   "<=0.25 rad, <=0.08 shift, alpha=0.6, gamma 0.02*0.83^k >= 0.002, eps=1e-3",
-                      "wall_s": wall, "pairs": K, "registrations_mean": float(regs.mean()),
+                      "wall_s": wall, "autotuned": tune, "pairs": K, "registrations_mean": float(regs.mean()),
                       "registrations_max": int(regs.max()), "aspot_iters_per_registration": float(inner.sum() / regs.sum()),
                       "converged_pairs": int(sum(r.converged for r in out)),
                       "motion_error_median": float(np.median(err)), "motion_error_p90": float(np.quantile(err, 0.9)),

@@ -136,16 +136,18 @@ def targets_into(fs: FeatureSet, k: int, prob: B.DeviceProblem, gamma: float, u:
 
 
 def build_training_set(probs: Sequence[B.DeviceProblem], gamma: float, eps: float, batch: int = 512,
-                       max_iter: int = 20000) -> tuple:
+                       max_iter: int = 20000, autotune: bool = True) -> tuple:
     """Features of every problem and, as targets, the duals that batched GPU
-    ASPOT converges to (pot_ws_targets).  Returns (set, iterations array)."""
+    ASPOT converges to (pot_ws_targets).  Returns (set, iterations array).
+    ``autotune``: the batched solver's tile shape is timed on the first chunk
+    of each size signature and cached for the others."""
     fs = features(probs, gamma)
     iters = np.zeros(len(probs), dtype=np.int64)
     L = B.lib()
     ws = None
     for a in range(0, len(probs), batch):
         chunk = list(probs[a:a + batch])
-        res = B.aspot_solve_batched(chunk, gamma, eps, max_iter=max_iter)
+        res = B.aspot_solve_batched(chunk, gamma, eps, max_iter=max_iter, flags=B.FLAG_AUTOTUNE if autotune else 0)
         ws_w = torch.cat([r.plan.w for r in res]).cpu().numpy()
         for j, r in enumerate(res):
             iters[a + j] = r.iters
