@@ -552,6 +552,25 @@ def run_batched(args):
                         "first_call_ms": first_ms, "ms_all_to_eps": tms,
                         "instances_per_s": len(probs) / (tms / 1e3), "vs_default_tile": tms / ms,
                         "converged": sum(r.status == 0 for r in rt)}
+    if not args.no_greedy:
+        # greedy block rule with the autotuned tiles
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter, flags=pkg.FLAG_AUTOTUNE,
+                                        block_rule=pkg.BLOCK_GREEDY)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                rg = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter, flags=pkg.FLAG_AUTOTUNE,
+                                             block_rule=pkg.BLOCK_GREEDY)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1) / args.steps
+        gits = [r.iters for r in rg]
+        out["greedy_rule_autotuned"] = {"ms_all_to_eps": gms, "instances_per_s": len(probs) / (gms / 1e3),
+                                        "iters_max": max(gits), "iters_mean": sum(gits) / len(gits),
+                                        "converged": sum(r.status == 0 for r in rg), "vs_default": gms / ms}
     print(json.dumps(out), flush=True)
 
 

@@ -90,8 +90,8 @@ typedef struct {
   int32_t max_iter;    /* iteration cap (> 0) */
   int32_t block_rule;  /* ASPOT Greenkhorn block choice: 0 = cyclic t mod 3 (Algorithm 1); 1 = greedy,
                           the block whose step decreases phi the most (the choice of Theorem 3's proof),
-                          scored exactly from a two-sided pass (P2 then costs a full pass); ASPOT only,
-                          aspot_solve_batched takes 0 only */
+                          scored exactly from a two-sided pass (P2 then costs a full pass); ASPOT and
+                          aspot_solve_batched */
   int32_t flags;       /* POT_FLAG_* */
   int32_t check_every; /* iterations per captured CUDA graph between host polls of the stop flag (0 => 24) */
   const double* u0;    /* optional warm start of ASPOT (device FP64 [n]) or NULL */

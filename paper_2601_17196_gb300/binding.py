@@ -432,7 +432,7 @@ def pot_plan_dense(prob: DeviceProblem, plan: Plan, gamma: float) -> torch.Tenso
 
 def aspot_solve_batched(probs, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
                         check_every: int = 0, plans=None, ws: Optional[torch.Tensor] = None,
-                        allow_noconv: bool = True):
+                        allow_noconv: bool = True, block_rule: int = BLOCK_CYCLIC):
     """Solve many independent squared-Euclidean problems (d <= 4) in lockstep.
     Returns one SolveResult per problem."""
     L = lib()
@@ -453,7 +453,7 @@ def aspot_solve_batched(probs, gamma: float, eps: float, max_iter: int = 10000, 
     plans = plans or [Plan.empty(p.n, p.m, dev) for p in probs]
     plarr = (_Plan * count)(*[pl.struct() for pl in plans])
     rarr = (_Result * count)()
-    pa = _params(gamma, eps, max_iter, flags, check_every)
+    pa = _params(gamma, eps, max_iter, flags, check_every, block_rule=block_rule)
     side, cur = _stream()
     _check(L.aspot_solve_batched(parr, count, ct.byref(pa), ct.c_void_p(ws.data_ptr()), nbytes, plarr, rarr,
                                  ct.c_void_p(side.cuda_stream)), allow=(0, 4) if allow_noconv else (0,))

@@ -340,6 +340,164 @@ __global__ void b_after_final_kernel(BVecs V, int k) {
   }
 }
 
+// ------------------------------------------------- greedy block rule ---
+// Per instance (one CTA): the exact decreases of phi of the three block steps,
+//   D_u = sum_i rho(r~_i, r_i(B) + e^{u_i}), D_v likewise, D_w = rho(s, |B|_1),
+// rho(a, b) = b - a + a log(a / b), from the two-sided pass at the point; the
+// block with the largest is stepped (ties to the lower index), as in the
+// single-instance solver.
+
+__device__ __forceinline__ double b_rho_log(double a, double la, double lb) {
+  return sexp(lb) - a + (a > 0.0 ? a * (la - lb) : 0.0);
+}
+__device__ __forceinline__ int b_pick(double du, double dv, double dw) {
+  int k = 0;
+  double best = du;
+  if (dv > best) { k = 1; best = dv; }
+  if (dw > best) k = 2;
+  return k;
+}
+__device__ __forceinline__ void lse_add(double x, double& acc, double& s) {
+  if (x > acc) { s = s * exp(acc - x) + 1.0; acc = x; } else s += exp(x - acc);
+}
+
+// After the two-sided pass at z_grave: choose k, Greenkhorn step, closed-form
+// phi(z^), argmin against phi(z_check).  z^ is written whole to (uh, vh).
+__global__ void b_greedy_greenkhorn_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  if (I.done) return;
+  double d[2] = {0, 0};
+  double acc = -INFINITY, ss = 0.0;
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double R = V.lrow[g];
+    d[0] += b_rho_log(V.rt[g], V.lrt[g], logaddexp(R, V.ug[g]));
+    lse_add(R, acc, ss);
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    d[1] += b_rho_log(V.ct[g], V.lct[g], logaddexp(V.lcol[g], V.vg[g]));
+  }
+  block_sums<2>(d);
+  const double lt = block_lse(acc > -INFINITY ? acc + log(ss) : POT_NEG_BIG, acc > -INFINITY);
+  const int k = b_pick(d[0], d[1], b_rho_log(I.s, I.log_s, lt));
+  double v[2] = {0, 0};
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double ug = V.ug[g];
+    if (k == 0) {
+      const double uh = V.lrt[g] - softplus(V.lrow[g] - ug);
+      V.uh[g] = uh;
+      v[0] += -uh * V.rt[g];
+    } else {
+      V.uh[g] = ug;
+      v[0] += sexp(ug) - ug * V.rt[g];
+    }
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    const double vg = V.vg[g];
+    if (k == 1) {
+      const double vh = V.lct[g] - softplus(V.lcol[g] - vg);
+      V.vh[g] = vh;
+      v[1] += -vh * V.ct[g];
+    } else {
+      V.vh[g] = vg;
+      v[1] += sexp(vg) - vg * V.ct[g];
+    }
+  }
+  block_sums<2>(v);
+  if (threadIdx.x == 0) {
+    double wh = I.w_grave, base;
+    if (k == 0) base = I.sum_rt;
+    else if (k == 1) base = I.sum_ct;
+    else { wh = I.w_grave + I.log_s - lt; base = I.s; }
+    I.kg = k;
+    I.w_hat = wh;
+    const double ph = base + v[0] + v[1] - wh * I.s;
+    I.phi_hat = ph;
+    const int take = ph < I.phi_check;
+    I.take_hat = take;
+    I.phi_z = take ? ph : I.phi_check;
+    I.w_z = take ? wh : I.w_check;
+  }
+}
+
+// After the two-sided pass at z^t: E_t, the block k2 with the largest
+// decrease at z^t, z_check^{t+1} = Greenkhorn_{k2}(z^t) and its closed-form
+// phi, theta update and the stop test.
+__global__ void b_greedy_final_kernel(BVecs V) {
+  BInst& I = V.inst[blockIdx.x];
+  if (I.done) return;
+  const int take = I.take_hat;
+  // E parts, |B|_1, D_u, D_v, phi parts: rows stepped / kept, columns stepped / kept, nonfinite
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double acc = -INFINITY, ss = 0.0;
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double uz = take ? V.uh[g] : V.uc[g];
+    const double R = V.lrow[g], a = V.rt[g];
+    const double rB = sexp(R), eu = sexp(uz);
+    v[0] += fabs(rB + eu - a);
+    v[1] += rB;
+    v[2] += b_rho_log(a, V.lrt[g], logaddexp(R, uz));
+    v[4] += -(V.lrt[g] - softplus(R - uz)) * a;
+    v[5] += eu - uz * a;
+    I.pu[i] = uz;
+    V.uo[g] = uz;
+    if (!isfinite(R) && R != POT_NEG_BIG) v[8] = 1.0;
+    lse_add(R, acc, ss);
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    const double vz = take ? V.vh[g] : V.vc[g];
+    const double Cc = V.lcol[g], c = V.ct[g];
+    const double cB = sexp(Cc), ev = sexp(vz);
+    v[0] += fabs(cB + ev - c);
+    v[3] += b_rho_log(c, V.lct[g], logaddexp(Cc, vz));
+    v[6] += -(V.lct[g] - softplus(Cc - vz)) * c;
+    v[7] += ev - vz * c;
+    I.pv[j] = vz;
+    V.vo[g] = vz;
+    if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[8] = 1.0;
+  }
+  block_sums<9>(v);
+  const double lt = block_lse(acc > -INFINITY ? acc + log(ss) : POT_NEG_BIG, acc > -INFINITY);
+  const double s = I.s;
+  const int k2 = b_pick(v[2], v[3], b_rho_log(s, I.log_s, lt));
+  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    const int64_t g = I.row0 + i;
+    const double uz = V.uo[g];
+    V.uc[g] = (k2 == 0) ? V.lrt[g] - softplus(V.lrow[g] - uz) : uz;
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+    const int64_t g = I.col0 + j;
+    const double vz = V.vo[g];
+    V.vc[g] = (k2 == 1) ? V.lct[g] - softplus(V.lcol[g] - vz) : vz;
+  }
+  if (threadIdx.x == 0) {
+    const double E = fabs(v[1] - s) + v[0];
+    const double wz = I.w_z;
+    I.w_out = wz;
+    double wc = wz, ph;
+    if (k2 == 0) ph = I.sum_rt + v[4] + v[7] - wz * s;
+    else if (k2 == 1) ph = I.sum_ct + v[5] + v[6] - wz * s;
+    else { wc = wz + I.log_s - lt; ph = s + v[5] + v[7] - wc * s; }
+    I.w_check = wc;
+    I.phi_check = ph;
+    I.E = E;
+    I.tot = v[1];
+    const double th = I.theta;
+    I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
+    I.t = I.t + 1;
+    if (v[8] != 0.0 || !isfinite(E)) I.nonfinite = 1;
+    if (E <= I.thr || I.t >= I.max_iter || I.nonfinite) {
+      I.done = 1;
+      atomicAdd(V.ndone, 1);
+    }
+  }
+}
+
 // rounding reading R1-R4, per instance (original r, c, s)
 __global__ void b_round1_kernel(BVecs V) {
   BInst& I = V.inst[blockIdx.x];
@@ -630,7 +788,9 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   if (s != POT_OK) return s;
   if (!params || !(params->eps > 0.0) || params->max_iter < 1 || !isfinite(params->gamma))
     return bfail(POT_EINVAL, "batched: bad params");
-  if (params->block_rule != 0) return bfail(POT_EINVAL, "batched: only the cyclic block rule (0)");
+  if (params->block_rule != 0 && params->block_rule != 1)
+    return bfail(POT_EINVAL, "batched: block_rule must be 0 (cyclic) or 1 (greedy)");
+  const bool greedy = params->block_rule == 1;
   if (!plans || !res) return bfail(POT_EINVAL, "batched: plans and results must be host arrays of count entries");
   for (int k = 0; k < count; ++k) {
     const pot_plan& pl = plans[k];
@@ -819,14 +979,25 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
     if ((q = pass(PASS_ROWS | PASS_COLS, V.ub, V.vb, offw_bar, nullptr, nullptr, -1, 0)) != POT_OK) return q;
     b_after_grad_kernel<<<count, kBT, 0, st>>>(V);
     ++launches;
-    if ((q = pass(k == 1 ? PASS_COLS : PASS_ROWS, V.ug, V.vg, offw_grave, nullptr, nullptr, -1, 0)) != POT_OK) return q;
-    b_after_greenkhorn_kernel<<<count, kBT, 0, st>>>(V, k);
-    ++launches;
-    if ((q = pass(PASS_ROWS | PASS_COLS, V.uc, V.vc, offw_check, (k == 0) ? V.uh : V.ug, (k == 1) ? V.vh : V.vg,
-                  offw_hat, 1)) != POT_OK)
-      return q;
-    b_after_final_kernel<<<count, kBT, 0, st>>>(V, k);
-    ++launches;
+    if (greedy) {
+      // greedy rule: both sides at z_grave to score the blocks; z^ written whole
+      if ((q = pass(PASS_ROWS | PASS_COLS, V.ug, V.vg, offw_grave, nullptr, nullptr, -1, 0)) != POT_OK) return q;
+      b_greedy_greenkhorn_kernel<<<count, kBT, 0, st>>>(V);
+      ++launches;
+      if ((q = pass(PASS_ROWS | PASS_COLS, V.uc, V.vc, offw_check, V.uh, V.vh, offw_hat, 1)) != POT_OK) return q;
+      b_greedy_final_kernel<<<count, kBT, 0, st>>>(V);
+      ++launches;
+    } else {
+      if ((q = pass(k == 1 ? PASS_COLS : PASS_ROWS, V.ug, V.vg, offw_grave, nullptr, nullptr, -1, 0)) != POT_OK)
+        return q;
+      b_after_greenkhorn_kernel<<<count, kBT, 0, st>>>(V, k);
+      ++launches;
+      if ((q = pass(PASS_ROWS | PASS_COLS, V.uc, V.vc, offw_check, (k == 0) ? V.uh : V.ug, (k == 1) ? V.vh : V.vg,
+                    offw_hat, 1)) != POT_OK)
+        return q;
+      b_after_final_kernel<<<count, kBT, 0, st>>>(V, k);
+      ++launches;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(POT_ECUDA, cudaGetErrorString(e));
     return POT_OK;
