@@ -49,6 +49,9 @@ def _args():
     ap.add_argument("--n", type=int, default=N_FULL, help="problem size (default: the 32k workload)")
     ap.add_argument("--max-iter", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--block-rule", default="cyclic", choices=["cyclic", "greedy"],
+                    help="headline: Greenkhorn block rule of the timed solves (cyclic: t mod 3 as Algorithm 1 "
+                         "prints it; greedy: the block with the largest decrease of phi)")
     ap.add_argument("--no-greedy", action="store_true",
                     help="headline: skip the greedy-block-rule solves measured beside the cyclic ones")
     ap.add_argument("--mode", default="solve", choices=["solve", "pass"],
@@ -140,7 +143,7 @@ class Clocks:
 _ORACLE_SAMPLE = {}
 
 
-def _oracle_iters_per_s(n_sample, iters, seed=0):
+def _oracle_iters_per_s(n_sample, iters, seed=0, rule="cyclic"):
     """ASPOT iterations of the FP64 oracle, as it stands, at n = m = n_sample
     (the cost matrix is built once, outside the timed region)."""
     import pot_workloads as W
@@ -151,7 +154,8 @@ def _oracle_iters_per_s(n_sample, iters, seed=0):
         _ORACLE_SAMPLE[key] = (pb, O.sqeuclid_cost(pb.X, pb.Y, 0.0))
     pb, C = _ORACLE_SAMPLE[key]
     t0 = time.perf_counter()
-    O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=iters, no_stop=True, cmax=float(C.max()))
+    O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=iters, no_stop=True, cmax=float(C.max()),
+            block_rule=rule)
     dt = time.perf_counter() - t0
     return iters / dt, dt
 
@@ -161,10 +165,10 @@ def run_reference(args, rank, world):
         return
     scale = (CPU_SAMPLE_N / args.n) ** 2
     for _ in range(args.warmup):
-        _oracle_iters_per_s(CPU_SAMPLE_N, 1)
+        _oracle_iters_per_s(CPU_SAMPLE_N, 1, rule=args.block_rule)
     rates, secs = [], 0.0
     for _ in range(args.steps):
-        r, dt = _oracle_iters_per_s(CPU_SAMPLE_N, 2)
+        r, dt = _oracle_iters_per_s(CPU_SAMPLE_N, 2, rule=args.block_rule)
         rates.append(r * scale)
         secs += dt
     value = statistics.mean(rates)
@@ -175,7 +179,7 @@ def run_reference(args, rank, world):
             "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": _workload_desc(args.n),
-                       "parallelism": "single (rank 0 of the launch runs the oracle)"},
+                       "parallelism": "single (rank 0 of the launch runs the oracle)", "block_rule": args.block_rule},
             "cpu_baseline": {"value": value, "unit": "it/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -217,8 +221,11 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)     # > 129 MB L2
     flags = pkg.FLAG_PROFILE
 
+    rule = pkg.BLOCK_GREEDY if args.block_rule == "greedy" else pkg.BLOCK_CYCLIC
+
     def solve(prob):
-        return pkg.aspot_solve(prob, pb.gamma, pb.eps, max_iter=args.max_iter, flags=flags, check_every=24)
+        return pkg.aspot_solve(prob, pb.gamma, pb.eps, max_iter=args.max_iter, flags=flags, check_every=24,
+                               block_rule=rule)
 
     with torch.cuda.stream(stream):
         first_ms = None
@@ -290,7 +297,7 @@ def run_ours(args, rank, world, local_rank):
 
         # ---------------- the greedy block rule, same workload and timing ---
         greedy = None
-        if world == 1 and not args.no_greedy:
+        if world == 1 and not args.no_greedy and args.block_rule == "cyclic":
             def solve_greedy(prob):
                 return pkg.aspot_solve(prob, pb.gamma, pb.eps, max_iter=args.max_iter, flags=flags, check_every=24,
                                        block_rule=pkg.BLOCK_GREEDY)
@@ -341,7 +348,8 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "bf16", "data": "synthetic",
         "config": {"workload": _workload_desc(n), "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs (16 MiB) fit in L2; a 256 MiB buffer is written before every step",
-                   "stop": "E_t <= eps/(8 max C) = 1.25e-3", "max_iter": args.max_iter},
+                   "stop": "E_t <= eps/(8 max C) = 1.25e-3", "max_iter": args.max_iter,
+                   "block_rule": args.block_rule},
         "time_to_eps_ms": ms / args.steps,
         "first_call_ms": first_ms,
         "iters_per_solve": iters / (args.steps * world),
@@ -369,7 +377,7 @@ def run_ours(args, rank, world, local_rank):
         line["warm_vs_cold"]["note"] = ("small study run inside the headline bench; --workload warmstart runs "
                                         "the 20000-instance / 1000-seed configuration")
     if world == 1 and not args.no_cpu_baseline:
-        rate, dt = _oracle_iters_per_s(CPU_SAMPLE_N, CPU_SAMPLE_ITERS)
+        rate, dt = _oracle_iters_per_s(CPU_SAMPLE_N, CPU_SAMPLE_ITERS, rule=args.block_rule)
         line["cpu_baseline"] = {"value": rate * (CPU_SAMPLE_N / n) ** 2, "unit": "it/s", "cores": 1,
                                 "kind": "oracle",
                                 "sample": f"{CPU_SAMPLE_ITERS} FP64 oracle ASPOT iterations at n=m={CPU_SAMPLE_N} "
