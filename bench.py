@@ -723,7 +723,7 @@ def run_ws_train(args):
 
 
 def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batch: int = 32, lr: float = 3e-3,
-                     device="cuda") -> dict:
+                     device="cuda", greedy: bool = False) -> dict:
     """Learned warm start on the 2-D mixture workload (n = m = 1024, 2-6
     Gaussians per cloud, masses U[1,1.5], s ~ U[0.6,0.95] x min mass,
     gamma = 0.02, eps = 1e-3): a training set of n_train instances (seeds
@@ -731,7 +731,9 @@ def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batc
     the GPU, then n_eval held-out seeds (0 .. n_eval-1) solved from zero and
     from the network's start (with the E(z_warm) > E(0) fallback).  Times are
     CUDA events on the solve stream; the warm time includes the warm start
-    itself (features, network, shift step) and the fallback check."""
+    itself (features, network, shift step) and the fallback check.  With
+    ``greedy`` the held-out seeds are also solved with the greedy block rule,
+    from zero and from the same warm start."""
     import numpy as np
     import torch
     import paper_2601_17196_gb300 as pkg
@@ -756,7 +758,7 @@ def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batc
         train_ms = e0.elapsed_time(e1)
         steps = net.step
         del fs
-        cold_it, warm_it, cold_ms, warm_ms, used, gap = [], [], [], [], [], []
+        cold_it, warm_it, cold_ms, warm_ms, used, gap, g_rows = [], [], [], [], [], [], []
         for k in range(n_eval):
             dp = pkg.DeviceProblem.from_workload(W.mix_2d(k), device=device, kind=pkg.COST_SQEUCLID_F32)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -771,9 +773,29 @@ def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batc
             cold_it.append(c.iters); warm_it.append(w.iters)
             cold_ms.append(a0.elapsed_time(a1)); warm_ms.append(b0.elapsed_time(b1))
             used.append(w.warm_used); gap.append(abs(w.objective - c.objective))
+            if greedy:
+                g0, g1, h0, h1 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+                g0.record(stream)
+                gc = pkg.aspot_solve(dp, gamma, eps, max_iter=20000, block_rule=pkg.BLOCK_GREEDY)
+                g1.record(stream)
+                h0.record(stream)
+                gw = net.solve(dp, gamma, eps, block_rule=pkg.BLOCK_GREEDY)
+                h1.record(stream)
+                torch.cuda.synchronize()
+                g_rows.append((gc.iters, gw.iters, g0.elapsed_time(g1), h0.elapsed_time(h1), gw.warm_used))
     ci, wi = np.array(cold_it, dtype=float), np.array(warm_it, dtype=float)
     cm, wm = np.array(cold_ms), np.array(warm_ms)
+    greedy_out = None
+    if g_rows:
+        G = np.array(g_rows, dtype=float)
+        greedy_out = {"cold_iters_mean": float(G[:, 0].mean()), "warm_iters_mean": float(G[:, 1].mean()),
+                      "cold_ms_mean": float(G[:, 2].mean()), "warm_ms_mean": float(G[:, 3].mean()),
+                      "iters_ratio_warm_over_cold": float(G[:, 1].mean() / G[:, 0].mean()),
+                      "time_ratio_warm_over_cold": float(G[:, 3].mean() / G[:, 2].mean()),
+                      "fallback_fraction": float(1.0 - G[:, 4].mean()),
+                      "cold_greedy_over_cold_cyclic_time": float(G[:, 2].mean() / cm.mean())}
     return {"workload": "mix_2d n=m=1024 gamma=0.02 eps=1e-3", "train_instances": n_train, "eval_seeds": n_eval,
+            "greedy_rule": greedy_out,
             "mode": "bf16 tcgen05" if mode == 1 else "fp32", "data_gen_s": t1 - t0,
             "train_iters_mean": float(iters.mean()), "train_steps": steps, "train_ms": train_ms,
             "train_ms_per_step": train_ms / max(steps, 1), "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
@@ -786,7 +808,7 @@ def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batc
 
 
 def run_warmstart(args):
-    r = warm_start_study(args.ws_train, args.ws_eval, args.ws_epochs)
+    r = warm_start_study(args.ws_train, args.ws_eval, args.ws_epochs, greedy=not args.no_greedy)
     r.update({"metric": "time-to-epsilon (ms) of warm-started ASPOT, learned warm start vs cold start",
               "value": r["warm_ms_mean"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
               "dtype": "bf16 network, fp32 passes, fp64 duals", "data": "synthetic"})

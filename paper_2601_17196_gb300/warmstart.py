@@ -278,11 +278,12 @@ class WarmStartNet:
         B._finish(side, cur)
         return u0, v0, float(w0.value)
 
-    def solve(self, prob: B.DeviceProblem, gamma: float, eps: float, max_iter: int = 20000, flags: int = 0):
+    def solve(self, prob: B.DeviceProblem, gamma: float, eps: float, max_iter: int = 20000, flags: int = 0,
+              block_rule: int = B.BLOCK_CYCLIC):
         """Warm-started ASPOT with the zero-start fallback (POT_FLAG_WARM_CHECK)."""
         u0, v0, w0 = self.warm_start(prob, gamma)
         return B.aspot_solve(prob, gamma, eps, max_iter=max_iter, flags=flags | B.FLAG_WARM_CHECK,
-                             u0=u0, v0=v0, w0=w0)
+                             u0=u0, v0=v0, w0=w0, block_rule=block_rule)
 
     def state(self) -> dict:
         return {"d": self.d, "params": self.params.detach().cpu().numpy().copy(), "step": self.step}
