@@ -43,6 +43,31 @@ __device__ __forceinline__ float load_pt(const void* base, int64_t idx) {
   }
 }
 
+// v[0..3] (one value per row) reduced over the 32 lanes; lane 8r ends with
+// row r's total in v[0].  IS_MAX selects max, else sum.
+template <bool IS_MAX>
+__device__ __forceinline__ void rows4_reduce(float (&v)[4], int lane) {
+  const bool up16 = lane & 16, up8 = lane & 8;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = up16 ? v[k] : v[k + 2];
+    const float keep = up16 ? v[k + 2] : v[k];
+    const float got = __shfl_xor_sync(0xffffffffu, send, 16);
+    v[k] = IS_MAX ? fmaxf(keep, got) : keep + got;
+  }
+  {
+    const float send = up8 ? v[0] : v[1];
+    const float keep = up8 ? v[1] : v[0];
+    const float got = __shfl_xor_sync(0xffffffffu, send, 8);
+    v[0] = IS_MAX ? fmaxf(keep, got) : keep + got;
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const float got = __shfl_xor_sync(0xffffffffu, v[0], o);
+    v[0] = IS_MAX ? fmaxf(v[0], got) : v[0] + got;
+  }
+}
+
 // Per-pass row / column terms of the logit, formed once per pass in FP64 and
 // handed to the pass kernels as FP32 (hi, lo) pairs in log2 units:
 //   rowA[i] = (hi, lo of (a_i + aoff - gC |x_i|^2) log2 e, |x_i|^2, p_i)
@@ -95,16 +120,21 @@ __global__ void prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad) {
 // One H x 128V tile (column block cb, row block rb) of the pass.  Partials
 // go to row_part[cb * rstride + i] and col_part[rb * cstride + j]; objective /
 // max-cost partials to red_part[red_idx].
-template <int KIND, int V, int DMAX, bool VEC>
+// MT: 0 = the pass mode is read at run time (any mode, including the
+// objective and max-cost passes); 1 / 2 / 3 = rows + columns / rows /
+// columns fixed at compile time, which drops the other modes' registers.
+template <int KIND, int V, int DMAX, bool VEC, int MT = 0>
 __device__ __forceinline__ void simt_tile(const PassDesc& P, int H, int64_t cb, int64_t rb, int64_t rstride,
                                           int64_t cstride, int64_t red_idx) {
   constexpr int NC = 4 * V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t col0 = cb * (128 * V);
   const int64_t row0 = rb * H;
-const bool want_rows = P.mode & PASS_ROWS, want_cols = P.mode & PASS_COLS;
-  const bool want_obj = P.mode & PASS_OBJ, want_max = P.mode & PASS_MAXCOST;
-  const bool need_pot = P.mode & (PASS_ROWS | PASS_COLS | PASS_OBJ);
+const bool want_rows = MT == 0 ? (P.mode & PASS_ROWS) != 0 : (MT == 1 || MT == 2);
+  const bool want_cols = MT == 0 ? (P.mode & PASS_COLS) != 0 : (MT == 1 || MT == 3);
+  const bool want_obj = MT == 0 ? (P.mode & PASS_OBJ) != 0 : false;
+  const bool want_max = MT == 0 ? (P.mode & PASS_MAXCOST) != 0 : false;
+  const bool need_pot = MT == 0 ? (P.mode & (PASS_ROWS | PASS_COLS | PASS_OBJ)) != 0 : true;
   const float g2 = (float)(P.gC * kL2E);
   const bool sq = KIND != COST_DENSE_F32;
 
@@ -230,18 +260,28 @@ const bool want_rows = P.mode & PASS_ROWS, want_cols = P.mode & PASS_COLS;
     }
 
     if (want_rows) {
+      // the chunk's four rows reduced together by the transposing butterfly
+      float mx[R], sm[R], rm[R];
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) {
-        const int64_t i = ib + (int64_t)kWarps * rr;
-        float mx = POT_NEG_BIGF;
+        mx[rr] = POT_NEG_BIGF;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) mx = fmaxf(mx, lg[rr][q]);
-        const float m_i = warp_max(mx);
+        for (int q = 0; q < NC; ++q) mx[rr] = fmaxf(mx[rr], lg[rr][q]);
+      }
+      rows4_reduce<true>(mx, lane);                 // lane 8r: row r's max in mx[0]
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) rm[rr] = __shfl_sync(0xffffffffu, mx[0], 8 * rr);
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
         float ssum = 0.f;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) ssum += (lg[rr][q] > -1.0e29f) ? ex2(lg[rr][q] - m_i) : 0.f;
-        ssum = warp_sum(ssum);
-        if (lane == 0 && i < rend) P.row_part[cb * rstride + i] = make_float2(m_i, ssum);
+        for (int q = 0; q < NC; ++q) ssum += (lg[rr][q] > -1.0e29f) ? ex2(lg[rr][q] - rm[rr]) : 0.f;
+        sm[rr] = ssum;
+      }
+      rows4_reduce<false>(sm, lane);                // lane 8r: row r's sum in sm[0]
+      if ((lane & 7) == 0) {
+        const int64_t i = ib + (int64_t)kWarps * (lane >> 3);
+        if (i < rend) P.row_part[cb * rstride + i] = make_float2(mx[0], sm[0]);
       }
     }
     if (want_cols) {
@@ -313,31 +353,6 @@ const bool want_rows = P.mode & PASS_ROWS, want_cols = P.mode & PASS_COLS;
 // Requires m % 4 == 0, ldc % 4 == 0 and a 16-byte aligned C.
 
 using tcx::pk2; using tcx::upk2; using tcx::add2; using tcx::fma2; using tcx::max3f;
-
-// v[0..3] (one value per row) reduced over the 32 lanes; lane 8r ends with
-// row r's total in v[0].  IS_MAX selects max, else sum.
-template <bool IS_MAX>
-__device__ __forceinline__ void rows4_reduce(float (&v)[4], int lane) {
-  const bool up16 = lane & 16, up8 = lane & 8;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float send = up16 ? v[k] : v[k + 2];
-    const float keep = up16 ? v[k + 2] : v[k];
-    const float got = __shfl_xor_sync(0xffffffffu, send, 16);
-    v[k] = IS_MAX ? fmaxf(keep, got) : keep + got;
-  }
-  {
-    const float send = up8 ? v[0] : v[1];
-    const float keep = up8 ? v[1] : v[0];
-    const float got = __shfl_xor_sync(0xffffffffu, send, 8);
-    v[0] = IS_MAX ? fmaxf(keep, got) : keep + got;
-  }
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1) {
-    const float got = __shfl_xor_sync(0xffffffffu, v[0], o);
-    v[0] = IS_MAX ? fmaxf(v[0], got) : v[0] + got;
-  }
-}
 
 __global__ void clear_parts_kernel(float2* a, int64_t cnt, const int* done, const int* skip, int skip_if) {
   if ((done && *done) || (skip && *skip == skip_if)) return;
@@ -573,8 +588,8 @@ void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
 // Batched pass: one CTA per tile of the work list (H rows x 128 V columns);
 // the tile's instance supplies sizes, points, offsets and its scalar
 // potentials.
-template <int KIND, int V>
-__global__ void __launch_bounds__(kThreads) pass_simt_batched_kernel(BatchPass B) {
+template <int KIND, int V, int MT>
+__global__ void __launch_bounds__(kThreads, MT == 0 ? 1 : (V == 1 ? 3 : 2)) pass_simt_batched_kernel(BatchPass B) {
   const BTile tl = B.tiles[blockIdx.x];
   BInst* I = B.inst + tl.inst;
   if (B.check_done && I->done) return;
@@ -601,7 +616,7 @@ __global__ void __launch_bounds__(kThreads) pass_simt_batched_kernel(BatchPass B
   P.rowA = B.rowA + I->row0;
   P.colA = B.colA + I->col0;
   P.colB = B.colB + I->col0;
-  simt_tile<KIND, V, 4, false>(P, B.H, tl.cb, tl.rb, B.Ntot, B.Mtot, blockIdx.x);
+  simt_tile<KIND, V, 4, false, MT>(P, B.H, tl.cb, tl.rb, B.Ntot, B.Mtot, blockIdx.x);
 }
 
 // Batched counterpart of prep_kernel: one CTA per instance.
@@ -635,14 +650,22 @@ void launch_prep_batched(const BatchPass& B, cudaStream_t st) {
   prep_batched_kernel<<<(unsigned)B.count, 512, 0, st>>>(B);
 }
 
-template <int V>
-void launch_batched_v(const BatchPass& B, cudaStream_t st) {
+template <int V, int MT>
+void launch_batched_vm(const BatchPass& B, cudaStream_t st) {
   const unsigned g = (unsigned)B.ntiles;
   switch (B.kind) {
-    case COST_SQEUCLID_BF16: pass_simt_batched_kernel<COST_SQEUCLID_BF16, V><<<g, kThreads, 0, st>>>(B); break;
-    case COST_SQEUCLID_F16: pass_simt_batched_kernel<COST_SQEUCLID_F16, V><<<g, kThreads, 0, st>>>(B); break;
-    default: pass_simt_batched_kernel<COST_SQEUCLID_F32, V><<<g, kThreads, 0, st>>>(B); break;
+    case COST_SQEUCLID_BF16: pass_simt_batched_kernel<COST_SQEUCLID_BF16, V, MT><<<g, kThreads, 0, st>>>(B); break;
+    case COST_SQEUCLID_F16: pass_simt_batched_kernel<COST_SQEUCLID_F16, V, MT><<<g, kThreads, 0, st>>>(B); break;
+    default: pass_simt_batched_kernel<COST_SQEUCLID_F32, V, MT><<<g, kThreads, 0, st>>>(B); break;
   }
+}
+
+template <int V>
+void launch_batched_v(const BatchPass& B, cudaStream_t st) {
+  if (B.mode == (PASS_ROWS | PASS_COLS)) launch_batched_vm<V, 1>(B, st);
+  else if (B.mode == PASS_ROWS) launch_batched_vm<V, 2>(B, st);
+  else if (B.mode == PASS_COLS) launch_batched_vm<V, 3>(B, st);
+  else launch_batched_vm<V, 0>(B, st);
 }
 
 void launch_pass_simt_batched(const BatchPass& B, cudaStream_t st) {
