@@ -188,7 +188,7 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
 
 /* Autotuner of the batched pass.  A tile is tile_rows x tile_cols entries of
  * one instance, handled by one CTA; the candidates are 32, 64, 128, 256 rows
- * x 128, 256 columns (default 32 x 256).  With POT_FLAG_AUTOTUNE,
+ * x 128, 256 columns (default 256 x 256).  With POT_FLAG_AUTOTUNE,
  * aspot_solve_batched takes the shape cached for the batch's signature (cost
  * kind, largest d, count, total and largest n and m) or, on a miss, times
  * every candidate on one two-sided pass of this batch (CUDA events, three

@@ -32,7 +32,7 @@ using namespace pot;
 namespace {
 
 constexpr int kBT = 512;       // threads of a per-instance CTA
-constexpr int kH = 32;         // default rows of a batched tile (8 warps x 4 rows)
+constexpr int kH = 256;        // default rows of a batched tile (8 warps x 8 chunks of 4 rows)
 constexpr int kW = 256;        // default columns of a batched tile
 
 template <int NV>

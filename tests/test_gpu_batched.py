@@ -18,7 +18,9 @@ def test_batched_matches_oracle_and_single_solves():
         C = O.sqeuclid_cost(pb.X, pb.Y, 0.0)
         conv = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=5000)
         assert r.status == 0 and r.err_final <= r.eps_stop
-        assert abs(r.iters - conv.iters) <= 2      # the stop test may flip on a near-tie of E_t
+        # E_t is not monotone near the threshold: the summation order (tile shape)
+        # can move its first crossing by a few iterations
+        assert abs(r.iters - conv.iters) <= 4
         # same number of iterations in the oracle: the iterates (and objectives) agree
         ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=r.iters, no_stop=True)
         assert abs(r.objective - ora.objective) <= 1e-5 * abs(ora.objective)
@@ -63,7 +65,7 @@ def _batch_probs(seed, count, nmin, nmax):
 
 def test_batched_every_tile_shape_matches_default():
     """Each candidate tile shape of the autotuner (pinned through the cache)
-    follows the default 32 x 256 tiles' iterates: the shape only changes the
+    follows the default 256 x 256 tiles' iterates: the shape only changes the
     FP32 summation order of the partials.  60 fixed iterations agree to the
     parity tolerance, and every shape solves every instance to its threshold
     (where E_t is not monotone, so its first crossing may move by a few
@@ -71,7 +73,7 @@ def test_batched_every_tile_shape_matches_default():
     insts, probs = _batch_probs(8, 10, 64, 900)
     K = 60
     base = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=K, flags=pkg.FLAG_NO_STOP, check_every=6)
-    assert all(r.tile_rows == 32 and r.tile_cols == 256 for r in base)
+    assert all(r.tile_rows == 256 and r.tile_cols == 256 for r in base)
     ub = [r.plan.u.cpu().numpy() for r in base]
     vb = [r.plan.v.cpu().numpy() for r in base]
     for H in (32, 64, 128, 256):
