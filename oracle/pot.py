@@ -18,7 +18,7 @@ dual point z = (u, v, w) with u in R^n, v in R^m, w in R, and
 The paper states everything with m = n; every function here allows m != n
 (the point-cloud appendix already uses two sizes).
 
-Readings of passages that are silent or ambiguous (listed in the design doc):
+Readings of passages that are silent or ambiguous:
   * N2  the zero start "0_{n+1}" of Algorithm 2 is the zero dual point
         (u, v, w) = 0 in R^{n+m+1}.
   * N3  inside the loop every marginal is the smoothed one (r~, c~): in the
