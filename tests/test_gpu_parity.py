@@ -268,14 +268,16 @@ def test_max_iter_reports_noconv_with_feasible_plan():
     _check_feasible(_plan_fp64(C, res.plan, res.gamma, res.cost_scale), pb.r, pb.c, pb.s)
 
 
+@pytest.mark.parametrize("rule", [0, 1])
 @pytest.mark.parametrize("gamma", [0.1, 0.03, 0.01])
-def test_dense_4096_full_size_properties(gamma):
-    """n = m = 4096, 64-D, FP32 cost: the GPU solve is checked in FP64 at its
-    own duals (E_t below the threshold, objective and feasibility of the
-    rounded plan); the oracle's full solve at this size is too slow for a test."""
+def test_dense_4096_full_size_properties(gamma, rule):
+    """n = m = 4096, 64-D, FP32 cost, both block rules: the GPU solve is
+    checked in FP64 at its own duals (E_t below the threshold, objective and
+    feasibility of the rounded plan); the oracle's full solve at this size is
+    too slow for a test."""
     pb = W.dense_4096(0, gamma=gamma)
     C = pb.C.astype(np.float64)
-    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=20000)
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=20000, block_rule=rule)
     assert res.status == 0
     st = O.approx_setup(pb.r, pb.c, pb.s, pb.eps, 1.0, pb.gamma)
     z = O.Dual(_np(res.plan.u), _np(res.plan.v), float(res.plan.w.item()))
