@@ -1,7 +1,9 @@
 // O(n + m) kernels around the passes: combining log-sum-exp partials, the
 // dual updates of ASPOT (Algorithm 2) and of the feasible Sinkhorn baseline
 // (Algorithm 3 on the extended kernel), the rounding reading R1-R4 and the
-// scalar bookkeeping.  Everything here is FP64.
+// scalar bookkeeping.  Potentials, updates and scalar sums are FP64; the
+// combine of the passes' FP32 partials sums in FP32 (compensated) and takes
+// its logarithm on an exact mantissa / exponent split.
 //
 // Scalar reductions are deterministic: every block writes its partial, the
 // last block to finish (atomic ticket) sums the partials in block order and
@@ -15,29 +17,15 @@ namespace {
 
 constexpr double kLn2 = 0.6931471805599453;
 
-// Natural log of the sum over blocks of partials (max, sum) in log2 units:
-// the largest shift first, then a compensated (Kahan) FP32 sum of
-// sum_b * 2^(max_b - M) (each term <= 128, ex2.approx relative error 2^-22),
-// one FP64 log at the end.  FP64 exp per partial would dominate the O(n+m)
-// kernels on this GPU (FP64 runs at a small fraction of the FP32 rate).
-__device__ __forceinline__ double combine_parts(const float2* part, int64_t nblk, int64_t stride, int64_t idx) {
-  float M = -INFINITY;
-  for (int64_t b = 0; b < nblk; ++b) {
-    const float2 p = part[b * stride + idx];
-    if (p.y > 0.f) M = fmaxf(M, p.x);
-  }
-  if (!(M > -INFINITY)) return POT_NEG_BIG;
-  float S = 0.f, comp = 0.f;
-  for (int64_t b = 0; b < nblk; ++b) {
-    const float2 p = part[b * stride + idx];
-    if (p.y > 0.f) {
-      const float y = p.y * ex2(p.x - M) - comp;
-      const float t = S + y;
-      comp = (t - S) - y;
-      S = t;
-    }
-  }
-  return ((double)M + log2((double)S)) * kLn2;
+// Natural log of 2^M * S (M in log2 units, S > 0 an FP32 sum): the exponent
+// of S is split off exactly (frexpf), so the FP32 log2 acts on a mantissa in
+// [0.5, 1) and its absolute error stays near 1e-7; M, the exponent and that
+// logarithm are added in FP64.  FP64 logarithms would dominate the combine on
+// this GPU (FP64 runs at a small fraction of the FP32 rate).
+__device__ __forceinline__ double log_shifted_sum(float M, float S) {
+  int ex;
+  const float mant = frexpf(S, &ex);
+  return ((double)M + (double)ex + (double)log2f(mant)) * kLn2;
 }
 
 // Partials -> FP64 log-sums for rows and / or columns.  Block = 32 entries x
@@ -75,13 +63,19 @@ __global__ void combine_kernel(const float2* row_part, int64_t ncolblk, int64_t 
     float Mt = -INFINITY;
 #pragma unroll
     for (int k = 0; k < 8; ++k) Mt = fmaxf(Mt, sM[k][jj]);
-    double St = 0.0;
+    // compensated (Kahan) FP32 sum of the eight slices' sum * 2^(max - Mt)
+    float St = 0.f, comp = 0.f;
     if (Mt > -INFINITY) {
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        if (sS[k][jj] > 0.f) St += (double)sS[k][jj] * (double)ex2(sM[k][jj] - Mt);
+        if (sS[k][jj] > 0.f) {
+          const float y = sS[k][jj] * ex2(sM[k][jj] - Mt) - comp;
+          const float t = St + y;
+          comp = (t - St) - y;
+          St = t;
+        }
     }
-    out[j] = St > 0.0 ? ((double)Mt + log2(St)) * kLn2 : POT_NEG_BIG;
+    out[j] = St > 0.f ? log_shifted_sum(Mt, St) : POT_NEG_BIG;
   }
 }
 
