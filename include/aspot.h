@@ -180,7 +180,9 @@ POT_API pot_status pot_marginals(const pot_problem* prob, double gamma, const do
  * all instances still running; an instance stops at its own threshold.
  * `plans` and `res` are host arrays of `count` entries (plan buffers on the
  * device); the return value is the worst instance status.  Workspace size
- * from pot_workspace_size_batched. */
+ * from pot_workspace_size_batched.  The call synchronises `stream` (setup,
+ * autotuning, stop polling), so a stream under graph capture is rejected with
+ * POT_EINVAL, as for the single-instance solvers. */
 POT_API pot_status pot_workspace_size_batched(const pot_problem* probs, int32_t count, size_t* bytes /* host */);
 POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, const pot_params* params,
                                        void* workspace, size_t ws_bytes, pot_plan* plans, pot_result* res,

@@ -798,6 +798,12 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
       return bfail(POT_EINVAL, "batched: every plan pointer must be a device buffer");
   }
   if (!workspace || (uintptr_t)workspace % 256) return bfail(POT_EINVAL, "batched: workspace NULL or not 256-byte aligned");
+  {
+    // the solve synchronises its stream (setup, tuning, stop polling): no caller capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      return bfail(POT_EINVAL, "batched: the stream is being captured");
+  }
   const BLayout L = b_layout(probs, count);
   if (ws_bytes < L.total) return bfail(POT_ENOMEM, "batched: workspace too small");
   Geom G = b_geom(probs, count, kH, kW);
