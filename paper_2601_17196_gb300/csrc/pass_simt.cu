@@ -8,8 +8,10 @@
 // Tile = H rows x W = 128*V columns.  Lane l of every warp owns columns
 // col0 + 128k + 4l + e (k < V, e < 4), so one warp reads a row segment with
 // coalesced 128-bit loads; warp w takes rows row0 + w, row0 + w + 8, ...
-//   * row side: exact per-row max over the W columns (warp shuffle), then
-//     sum_j 2^(logit - max); one (max, sum) partial per row and column block.
+//   * row side: exact per-row max over the W columns, then
+//     sum_j 2^(logit - max), the four rows of a chunk reduced over the warp
+//     together by a transposing butterfly; one (max, sum) partial per row and
+//     column block.
 //   * column side: every lane keeps an exact running (max, sum) for each of
 //     its 4V columns; rows come in chunks of four, so a column costs one
 //     rescale per chunk plus one ex2 per entry.  The eight warps' columns
