@@ -350,3 +350,26 @@ def test_feasibility_error_is_l1_norm_of_gradient():
         z = O.Dual(rng.normal(size=5) - 2, rng.normal(size=6) - 2, rng.normal())
         E = O.feas_error(C, 0.07, p.r, p.c, p.s, z)
         assert E == pytest.approx(np.abs(O.grad_phi(C, 0.07, p.r, p.c, p.s, z).flat()).sum(), rel=1e-13)
+
+
+def test_greedy_trace_and_replay():
+    """The greedy rule's recorded blocks are the argmax of the recorded exact
+    decreases (ties to the lower index); replaying a run's own decisions
+    reproduces it exactly, and forcing other blocks is obeyed.  (The GPU
+    parity tests replay the GPU's decisions through this option.)"""
+    p = W.small_dense(6, n=40, m=52)
+    C = p.C.astype(np.float64)
+    free = O.aspot(C, p.r, p.c, p.s, 0.05, None, max_iter=30, no_stop=True, block_rule="greedy", record=True)
+    for t in range(30):
+        d_grave, d_z = (np.asarray(x) for x in free.trace.dec[t])
+        assert free.trace.k[t] == int(np.argmax(d_grave))
+        assert free.trace.k2[t] == int(np.argmax(d_z))
+    rep = O.aspot(C, p.r, p.c, p.s, 0.05, None, max_iter=30, no_stop=True, block_rule="greedy", record=True,
+                  forced_hat=free.trace.took_hat, forced_blocks=list(zip(free.trace.k, free.trace.k2)))
+    np.testing.assert_array_equal(rep.z.u, free.z.u)
+    np.testing.assert_array_equal(rep.z.v, free.z.v)
+    forced = [(0, 1)] * 30
+    other = O.aspot(C, p.r, p.c, p.s, 0.05, None, max_iter=30, no_stop=True, block_rule="greedy", record=True,
+                    forced_blocks=forced)
+    assert other.trace.k == [0] * 30 and other.trace.k2 == [1] * 30
+    assert np.abs(other.z.u - free.z.u).max() > 1e-6
