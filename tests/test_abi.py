@@ -148,3 +148,58 @@ def test_autotune_cache_calls(libpath, tmp_path):
     assert L.pot_autotune_load(str(tmp_path / "missing.txt").encode()) == 1
     assert L.pot_autotune_lookup(a, 2, ct.byref(h), ct.byref(w)) == 0 and (h.value, w.value) == (64, 128)
     assert L.pot_autotune_clear() == 0
+
+
+def test_headers_are_plain_c99():
+    """Every public header compiles on its own as C99 (the boundary has no C++
+    or CUDA types)."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    for h in HEADERS:
+        r = subprocess.run([cc, "-fsyntax-only", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-x", "c",
+                            "-I", os.path.join(ROOT, "include"), h], capture_output=True, text=True)
+        assert r.returncode == 0 and not r.stderr.strip(), (h, r.stderr)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "aspot.h"
+#include "registration.h"
+#include "warmstart.h"
+int main(void) {
+  pot_problem p;
+  size_t bytes = 0;
+  int64_t np = 0;
+  memset(&p, 0, sizeof(p));
+  p.n = 0; p.m = 5;                                   /* invalid: rejected on the host */
+  if (pot_workspace_size(&p, NULL, &bytes) != POT_EINVAL) return 1;
+  if (strlen(pot_last_error()) == 0) return 2;
+  if (pot_autotune_clear() != POT_OK) return 3;
+  if (pot_ws_param_count(2, &np) != POT_OK || np <= 0) return 4;
+  if (pot_rigid_workspace_size(4, &bytes) != POT_OK || bytes == 0) return 5;
+  printf("ok %lld\n", (long long)np);
+  return 0;
+}
+"""
+
+
+def test_c_program_links_and_calls_the_library(libpath, tmp_path):
+    """A plain C program includes the headers, links the shared library and
+    calls host-side entry points (argument checks, the autotune cache, sizes)."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "probe.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "probe"
+    libdir = os.path.dirname(libpath)
+    name = os.path.basename(libpath)
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        os.path.join(libdir, name), "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), (r.returncode, r.stdout, r.stderr)
