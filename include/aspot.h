@@ -188,6 +188,16 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
                                        void* workspace, size_t ws_bytes, pot_plan* plans, pot_result* res,
                                        void* stream);
 
+/* Decisions of the last aspot_solve_batched that used this workspace: for
+ * each of the `count` instances (the same probs as the solve), the first
+ * `iters` iterations (0 <= iters <= 1024) as one byte each, took + 2 k + 8 k2:
+ * took = 1 when the argmin kept z^, k the block of the Greenkhorn step at
+ * z_grave, k2 that of the step at z^t (k2 = k for the cyclic rule).  Bytes of
+ * iterations an instance did not run are undefined.  out: host [count][iters].
+ * Synchronises the stream. */
+POT_API pot_status pot_trace_batched(void* workspace, const pot_problem* probs, int32_t count, int32_t iters,
+                                     uint8_t* out /* host */, void* stream);
+
 /* Autotuner of the batched pass.  A tile is tile_rows x tile_cols entries of
  * one instance, handled by one CTA; the candidates are 32, 64, 128, 256 rows
  * x 128, 256 columns (default 256 x 256).  With POT_FLAG_AUTOTUNE,

@@ -40,7 +40,8 @@ EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_roun
             "aspot_solve_batched", "pot_marginals_static", "pot_ws_param_count", "pot_ws_init",
             "pot_ws_features_workspace_size", "pot_ws_features", "pot_ws_targets", "pot_ws_workspace_size", "pot_ws_forward", "pot_ws_gradient",
             "pot_ws_train_step", "pot_ws_warm_workspace_size", "pot_ws_warm_start", "pot_rigid_workspace_size",
-            "pot_rigid_fit", "pot_rigid_apply", "pot_autotune_set", "pot_autotune_lookup", "pot_autotune_clear",
+            "pot_rigid_fit", "pot_rigid_apply", "pot_trace_batched", "pot_autotune_set", "pot_autotune_lookup",
+            "pot_autotune_clear",
             "pot_autotune_save", "pot_autotune_load", "pot_last_error"]
 
 
@@ -127,6 +128,7 @@ def lib() -> ct.CDLL:
         L.pot_rigid_workspace_size.argtypes = [i32, ct.POINTER(sz)]
         L.pot_rigid_fit.argtypes = [P, i32, PL, dbl, vp, vp, vp, sz, vp]
         L.pot_rigid_apply.argtypes = [P, i32, vp, vp, vp, sz, vp]
+        L.pot_trace_batched.argtypes = [vp, P, i32, i32, vp, vp]
         L.pot_autotune_set.argtypes = [P, i32, i32, i32]
         L.pot_autotune_lookup.argtypes = [P, i32, ct.POINTER(i32), ct.POINTER(i32)]
         L.pot_autotune_clear.argtypes = []
@@ -260,6 +262,7 @@ class SolveResult:
     tile_rows: int = 0
     tile_cols: int = 0
     tune_ms: float = 0.0
+    decisions: Optional[np.ndarray] = None    # batched: per iteration took + 2 k + 8 k2 (first 1024)
 
 
 _side_streams = {}
@@ -432,9 +435,10 @@ def pot_plan_dense(prob: DeviceProblem, plan: Plan, gamma: float) -> torch.Tenso
 
 def aspot_solve_batched(probs, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
                         check_every: int = 0, plans=None, ws: Optional[torch.Tensor] = None,
-                        allow_noconv: bool = True, block_rule: int = BLOCK_CYCLIC):
+                        allow_noconv: bool = True, block_rule: int = BLOCK_CYCLIC, decisions: bool = False):
     """Solve many independent squared-Euclidean problems (d <= 4) in lockstep.
-    Returns one SolveResult per problem."""
+    Returns one SolveResult per problem; with ``decisions`` each carries the
+    per-iteration argmin and block decisions of its first 1024 iterations."""
     L = lib()
     count = len(probs)
     parr = (_Problem * count)(*[p.struct() for p in probs])
@@ -457,6 +461,12 @@ def aspot_solve_batched(probs, gamma: float, eps: float, max_iter: int = 10000, 
     side, cur = _stream()
     _check(L.aspot_solve_batched(parr, count, ct.byref(pa), ct.c_void_p(ws.data_ptr()), nbytes, plarr, rarr,
                                  ct.c_void_p(side.cuda_stream)), allow=(0, 4) if allow_noconv else (0,))
+    codes = None
+    if decisions:
+        it = min(max(int(rarr[k].iters) for k in range(count)), 1024)
+        codes = np.zeros((count, max(it, 1)), dtype=np.uint8)
+        _check(L.pot_trace_batched(ct.c_void_p(ws.data_ptr()), parr, count, it, codes.ctypes.data_as(ct.c_void_p),
+                                   ct.c_void_p(side.cuda_stream)))
     _finish(side, cur)
     out = []
     for k in range(count):
@@ -464,7 +474,8 @@ def aspot_solve_batched(probs, gamma: float, eps: float, max_iter: int = 10000, 
         out.append(SolveResult(r.status, r.iters, r.objective, r.err_final, r.eps_stop, r.gamma, r.cost_scale,
                                r.mass, r.ms, r.rounding_branch, r.nonfinite, plans[k], None, r.pass_ms,
                                r.pass_launches, r.kernel_launches, tile_rows=r.tile_rows, tile_cols=r.tile_cols,
-                               tune_ms=r.tune_ms))
+                               tune_ms=r.tune_ms,
+                               decisions=None if codes is None else codes[k, :min(int(r.iters), 1024)].copy()))
     return out
 
 

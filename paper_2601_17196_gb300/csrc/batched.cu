@@ -87,12 +87,15 @@ __device__ double block_lse(double x, bool act) {
 __device__ __forceinline__ double sexp(double x) { return x > -700.0 ? exp(x) : 0.0; }
 __device__ __forceinline__ double clampl(double x) { return x > POT_NEG_BIG ? x : POT_NEG_BIG; }
 
+constexpr int kBTrace = 1024;  // iterations of each instance whose decisions are recorded
+
 struct BVecs {
   BInst* inst;
   double *rt, *ct, *lrt, *lct, *ut, *vt, *uc, *vc, *ub, *vb, *ug, *vg, *uh, *vh;
   double *uo, *vo, *fc, *gc;          // concatenated final duals and plan potentials
   const double *lrow, *lcol;
   int* ndone;
+  unsigned char* trace;               // [count][kBTrace]: took + 2 k + 8 k2 per iteration
 };
 
 // masses, minima and finiteness of r and c per instance
@@ -329,6 +332,7 @@ __global__ void b_after_final_kernel(BVecs V, int k) {
     I.phi_check = base + v[2] - wc * s;
     I.E = E;
     I.tot = v[1];
+    if (I.t < kBTrace) V.trace[(int64_t)blockIdx.x * kBTrace + I.t] = (unsigned char)(take + 10 * k);
     const double th = I.theta;
     I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
     I.t = I.t + 1;
@@ -487,6 +491,7 @@ __global__ void b_greedy_final_kernel(BVecs V) {
     I.phi_check = ph;
     I.E = E;
     I.tot = v[1];
+    if (I.t < kBTrace) V.trace[(int64_t)blockIdx.x * kBTrace + I.t] = (unsigned char)(take + 2 * I.kg + 8 * k2);
     const double th = I.theta;
     I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
     I.t = I.t + 1;
@@ -625,6 +630,7 @@ constexpr int kMinH = 32, kMinW = 128;
 struct BLayout {
   int64_t N = 0, M = 0, T = 0, maxcb = 0, maxrb = 0;   // worst case over the candidate shapes
   size_t off_inst, off_tiles, off_cnt, off_xn, off_yn, off_rowp, off_colp, off_red, off_u[16], off_v[16], total;
+  size_t off_trace;
   size_t off_rowA, off_colA, off_colB;
 };
 
@@ -652,6 +658,7 @@ BLayout b_layout(const pot_problem* P, int count) {
   L.off_colB = o; o = al(o + sizeof(float2) * L.M);
   for (int s = 0; s < kBSlots; ++s) { L.off_u[s] = o; o = al(o + sizeof(double) * L.N); }
   for (int s = 0; s < kBSlots; ++s) { L.off_v[s] = o; o = al(o + sizeof(double) * L.M); }
+  L.off_trace = o; o = al(o + (size_t)kBTrace * count);
   L.total = o;
   return L;
 }
@@ -722,6 +729,21 @@ POT_API pot_status pot_workspace_size_batched(const pot_problem* probs, int32_t 
   if (s != POT_OK) return s;
   if (!bytes) return bfail(POT_EINVAL, "bytes is NULL");
   *bytes = b_layout(probs, count).total;
+  return POT_OK;
+}
+
+POT_API pot_status pot_trace_batched(void* workspace, const pot_problem* probs, int32_t count, int32_t iters,
+                                     uint8_t* out, void* stream) {
+  pot_status s = check_batch(probs, count);
+  if (s != POT_OK) return s;
+  if (!workspace || !out) return bfail(POT_EINVAL, "trace: workspace and out must not be NULL");
+  if (iters < 0 || iters > kBTrace) return bfail(POT_EINVAL, "trace: iters must be in 0 .. 1024");
+  if (iters == 0) return POT_OK;
+  const BLayout L = b_layout(probs, count);
+  const unsigned char* src = (const unsigned char*)workspace + L.off_trace;
+  BCK(cudaMemcpy2DAsync(out, (size_t)iters, src, (size_t)kBTrace, (size_t)iters, (size_t)count,
+                        cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  BCK(cudaStreamSynchronize((cudaStream_t)stream));
   return POT_OK;
 }
 
@@ -854,6 +876,7 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   double* lcol = Vv[7];
   V.lrow = lrow; V.lcol = lcol; V.ndone = ndone;
   V.uo = U[8]; V.vo = Vv[8]; V.fc = U[9]; V.gc = Vv[9];
+  V.trace = (unsigned char*)(ws + L.off_trace);
 
   BatchPass B{};
   B.kind = probs[0].kind; B.H = G.H; B.W = G.W; B.Ntot = L.N; B.Mtot = L.M; B.tiles = dtiles; B.ntiles = G.T;

@@ -109,35 +109,55 @@ def test_batched_autotune_times_candidates_then_caches():
     pkg.autotune_clear()
 
 
+def _replay(codes):
+    codes = np.asarray(codes, dtype=np.int64)
+    return list((codes & 1) > 0), list(zip((codes >> 1) & 3, (codes >> 3) & 3))
+
+
 def test_batched_greedy_rule_matches_oracle():
-    """Greedy block rule in the batched solver: 30 fixed iterations against
-    the oracle's greedy run (the parity check proper), then converged solves.
-    Near the threshold the block decreases carry the FP32 passes' error
-    amplified by rho's cancellation (delta sqrt(2 D sum a), of the size of D
-    itself), so block choices there are near-ties that FP32 and FP64 may take
-    differently; with no trace to replay, a converged solve is compared with
-    the oracle's own greedy solve at the level by which two eps-accurate
-    stopping points differ (1e-3 relative), and must reach its threshold in
-    fewer iterations than the cyclic rule."""
+    """Greedy block rule in the batched solver, with the oracle replaying each
+    instance's recorded argmin and block decisions (pot_trace_batched): 30
+    fixed iterations match in the potentials, converged solves in the
+    objective at the GPU's iteration count, and every instance reaches its
+    threshold in fewer iterations than the cyclic rule."""
     insts, probs = _batch_probs(11, 5, 64, 400)
     K = 30
     res = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=K, flags=pkg.FLAG_NO_STOP, check_every=6,
-                                  block_rule=pkg.BLOCK_GREEDY)
+                                  block_rule=pkg.BLOCK_GREEDY, decisions=True)
     for pb, r in zip(insts, res):
         C = O.sqeuclid_cost(pb.X, pb.Y, 0.0)
-        ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, block_rule="greedy")
-        assert r.iters == K
+        assert r.iters == K and len(r.decisions) == K
+        took, blocks = _replay(r.decisions)
+        ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, block_rule="greedy",
+                      forced_hat=took, forced_blocks=blocks)
         np.testing.assert_allclose(r.plan.u.cpu().numpy(), ora.z.u, rtol=0, atol=2e-5 * (1 + np.abs(ora.z.u).max()))
         np.testing.assert_allclose(r.plan.v.cpu().numpy(), ora.z.v, rtol=0, atol=2e-5 * (1 + np.abs(ora.z.v).max()))
-    conv = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000, block_rule=pkg.BLOCK_GREEDY)
+    conv = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000, block_rule=pkg.BLOCK_GREEDY, decisions=True)
     cyc = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000)
     for pb, r, c in zip(insts, conv, cyc):
         assert r.status == 0 and r.err_final <= r.eps_stop
         assert r.iters < c.iters                      # the greedy rule needs fewer iterations here
         C = O.sqeuclid_cost(pb.X, pb.Y, 0.0)
-        ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=5000, block_rule="greedy")
-        assert abs(r.objective - ora.objective) <= 1e-3 * abs(ora.objective)
+        took, blocks = _replay(r.decisions)
+        ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=r.iters, no_stop=True,
+                            block_rule="greedy", forced_hat=took, forced_blocks=blocks)
+        assert abs(r.objective - ora.objective) <= 1e-5 * abs(ora.objective)
         f, g, p, q = (t.cpu().numpy() for t in (r.plan.f, r.plan.g, r.plan.p, r.plan.q))
         X = np.exp(f[:, None] + g[None, :] - C / r.gamma) + float(r.plan.kappa.item()) * np.outer(p, q)
         assert (X.sum(1) <= pb.r * (1 + 1e-6)).all() and (X.sum(0) <= pb.c * (1 + 1e-6)).all()
         assert X.sum() == pytest.approx(pb.s, rel=1e-6)
+
+
+def test_batched_records_cyclic_decisions():
+    """The cyclic rule's recorded blocks are t mod 3 (k2 = k), and replaying
+    the recorded argmin decisions reproduces the oracle's iterates."""
+    insts, probs = _batch_probs(12, 4, 64, 300)
+    K = 24
+    res = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=K, flags=pkg.FLAG_NO_STOP, check_every=6,
+                                  decisions=True)
+    for pb, r in zip(insts, res):
+        took, blocks = _replay(r.decisions)
+        assert blocks == [(t % 3, t % 3) for t in range(K)]
+        C = O.sqeuclid_cost(pb.X, pb.Y, 0.0)
+        ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, forced_hat=took)
+        np.testing.assert_allclose(r.plan.u.cpu().numpy(), ora.z.u, rtol=0, atol=2e-5 * (1 + np.abs(ora.z.u).max()))
