@@ -68,16 +68,28 @@ def test_marginals_dense(n, m):
 
 
 @pytest.mark.parametrize("kind,d", [(pkg.COST_SQEUCLID_F32, 3), (pkg.COST_SQEUCLID_F32, 2),
-                                    (pkg.COST_SQEUCLID_BF16, 128), (pkg.COST_SQEUCLID_BF16, 64)])
+                                    (pkg.COST_SQEUCLID_BF16, 128), (pkg.COST_SQEUCLID_BF16, 64),
+                                    # CUDA-core paths: small d in registers, and the generic loop over d
+                                    (pkg.COST_SQEUCLID_F32, 7), (pkg.COST_SQEUCLID_F16, 3),
+                                    (pkg.COST_SQEUCLID_F16, 33), (pkg.COST_SQEUCLID_BF16, 3),
+                                    (pkg.COST_SQEUCLID_BF16, 20)])
 def test_marginals_sqeuclid(kind, d):
     n, m = 385, 521
-    if kind == pkg.COST_SQEUCLID_BF16:
+    if kind == pkg.COST_SQEUCLID_BF16 and d % 64 == 0:
         pb = W.cloud_32k(2, n=n, m=m, d=d)
     else:
         rng = np.random.default_rng(d)
-        pb = W.Problem("pts", np.full(n, 1.0 / n), np.full(m, 1.3 / m), 0.8, 0.05, 1e-3,
-                       X=rng.uniform(0, 1, (n, d)).astype(np.float32).astype(np.float64),
-                       Y=rng.uniform(0, 1, (m, d)).astype(np.float32).astype(np.float64))
+        X, Y = rng.uniform(0, 1, (n, d)), rng.uniform(0, 1, (m, d))
+        if kind == pkg.COST_SQEUCLID_F16:                  # the values the kernel sees
+            X, Y = X.astype(np.float16).astype(np.float64), Y.astype(np.float16).astype(np.float64)
+        elif kind == pkg.COST_SQEUCLID_BF16:
+            Xb, Yb = W.to_bf16_bits(X), W.to_bf16_bits(Y)
+            X, Y = W.from_bf16_bits(Xb), W.from_bf16_bits(Yb)
+        else:
+            X, Y = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+        pb = W.Problem("pts", np.full(n, 1.0 / n), np.full(m, 1.3 / m), 0.8, 0.05, 1e-3, X=X, Y=Y)
+        if kind == pkg.COST_SQEUCLID_BF16:
+            pb.X_bf16, pb.Y_bf16 = Xb, Yb
     Dm = O.sqeuclid_cost(pb.X, pb.Y, 1.0)
     scale = 1.0 / Dm.max()
     pb.cost_scale = scale
@@ -88,9 +100,18 @@ def test_marginals_sqeuclid(kind, d):
     u, v, w = rng.uniform(-30, 5, n), rng.uniform(-30, 5, m), 3.0
     lr, lc, tot = pkg.pot_marginals(dp, gam, _t(u), _t(v), w)
     L = O.log_gibbs(C, gam, u, v, w)
-    np.testing.assert_allclose(_np(lr), O.logsumexp(L, axis=1), rtol=0, atol=2e-5)
-    np.testing.assert_allclose(_np(lc), O.logsumexp(L, axis=0), rtol=0, atol=2e-5)
-    assert pkg.pot_cost_max(dp) == pytest.approx(Dm.max(), rel=2e-6)
+    # The generic loop over d (d > 4, not a tensor-core size) forms the cost from
+    # FP32 dot products and squared norms.  A d-term FP32 sum errs by at most
+    # about d 2^-24 times the sum of magnitudes, so a cost entry by
+    # 2 (d + 2) 2^-24 (|x|^2 + |y|^2), and a logit by that x scale / gamma.
+    # The register path (d <= 4) and the tensor-core paths keep 2e-5.
+    tol = 2e-5
+    if d > 4 and not (kind == pkg.COST_SQEUCLID_BF16 and d % 64 == 0):
+        mag = (pb.X ** 2).sum(1).max() + (pb.Y ** 2).sum(1).max()
+        tol += 2 * (d + 2) * 2.0 ** -24 * mag * scale / gam
+    np.testing.assert_allclose(_np(lr), O.logsumexp(L, axis=1), rtol=0, atol=tol)
+    np.testing.assert_allclose(_np(lc), O.logsumexp(L, axis=0), rtol=0, atol=tol)
+    assert pkg.pot_cost_max(dp) == pytest.approx(Dm.max(), rel=2e-6 * max(1, (d + 2) / 6))
 
 
 # ----------------------------------------------------------- solvers ---
