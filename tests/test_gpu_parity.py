@@ -325,3 +325,35 @@ def test_tuned_gamma_sinkhorn_matches_oracle(p_tune):
     assert res.status == 0 and abs(res.iters - ora.iters) <= 1
     assert abs(res.objective - ora.objective) <= 1e-5 * abs(ora.objective)
     _check_feasible(_plan_fp64(C, res.plan, res.gamma, res.cost_scale), pb.r, pb.c, pb.s)
+
+
+@pytest.mark.parametrize("kind,d", [(pkg.COST_SQEUCLID_F32, 3), (pkg.COST_SQEUCLID_F16, 3),
+                                    (pkg.COST_SQEUCLID_F32, 7), (pkg.COST_SQEUCLID_BF16, 20)])
+def test_aspot_solve_on_point_clouds(kind, d):
+    """ASPOT to its threshold on point clouds of each storage kind through the
+    CUDA-core paths (registers for d <= 4, the generic loop otherwise), the
+    oracle replaying the GPU's argmin decisions at the GPU's iteration count:
+    objectives to 1e-5 relative, feasible rounded plan."""
+    n, m = 210, 170
+    rng = np.random.default_rng(100 + d)
+    X, Y = rng.uniform(0, 1, (n, d)), rng.uniform(0, 1, (m, d)) * 0.8 + 0.1
+    Xb = Yb = None
+    if kind == pkg.COST_SQEUCLID_F16:
+        X, Y = X.astype(np.float16).astype(np.float64), Y.astype(np.float16).astype(np.float64)
+    elif kind == pkg.COST_SQEUCLID_BF16:
+        Xb, Yb = W.to_bf16_bits(X), W.to_bf16_bits(Y)
+        X, Y = W.from_bf16_bits(Xb), W.from_bf16_bits(Yb)
+    else:
+        X, Y = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+    r, c = np.full(n, 1.0 / n), np.full(m, 1.25 / m)
+    pb = W.Problem("pts", r, c, 0.8, 0.05, 1e-3, X=X, Y=Y, X_bf16=Xb, Y_bf16=Yb)
+    Dm = O.sqeuclid_cost(X, Y, 1.0)
+    pb.cost_scale = 1.0 / Dm.max()
+    C = Dm * pb.cost_scale
+    res = pkg.aspot_solve(_dev(pb, kind=kind), pb.gamma, pb.eps, max_iter=5000, flags=pkg.FLAG_TRACE)
+    assert res.status == 0 and res.err_final <= res.eps_stop
+    took = res.trace[:, 3] > 0.5
+    ora = O.solve_aspot(C, r, c, pb.s, pb.eps, pb.gamma, max_iter=res.iters, no_stop=True, forced_hat=list(took),
+                        cmax=1.0)
+    assert abs(res.objective - ora.objective) <= 1e-5 * abs(ora.objective)
+    _check_feasible(_plan_fp64(C, res.plan, res.gamma, 1.0), r, c, pb.s)
