@@ -191,3 +191,35 @@ def test_cloud_32k_full_size_greedy_solve():
         c = csr * ((Y[j][None, :] - X) ** 2).sum(axis=1)
         xj = np.exp(f + gg[j] - c / res.gamma).sum() + kap * p.sum() * q[j]
         assert xj <= pb.c[j] * (1 + 1e-5) + 1e-15
+
+
+@pytest.mark.parametrize("d", [128, 3])
+def test_sinkhorn_on_point_clouds_matches_oracle(d):
+    """The feasible Sinkhorn baseline on point clouds: BF16 d = 128 through the
+    tcgen05 pass, FP32 d = 3 through the CUDA-core pass.  Iterations within one
+    of the oracle's, objective to 1e-5 relative (the tcgen05 pass's log-sum
+    error is a few 1e-6), feasible rounded plan."""
+    if d == 128:
+        pb, Dm = _cloud(13, 300, 420)
+    else:
+        rng = np.random.default_rng(14)
+        X = rng.uniform(0, 1, (300, 3)).astype(np.float32).astype(np.float64)
+        Y = rng.uniform(0, 1, (420, 3)).astype(np.float32).astype(np.float64)
+        pb = W.Problem("pts", np.full(300, 1.0 / 300), np.full(420, 1.25 / 420), 0.9, 0.05, 1e-3, X=X, Y=Y)
+        Dm = O.sqeuclid_cost(X, Y, 1.0)
+        pb.cost_scale = 1.0 / Dm.max()
+    C = Dm * pb.cost_scale
+    kind = pkg.COST_SQEUCLID_BF16 if d == 128 else pkg.COST_SQEUCLID_F32
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda", kind=kind)
+    res = pkg.sinkhorn_pot_solve(dp, pb.gamma, pb.eps, max_iter=20000)
+    ora = O.solve_sinkhorn(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=20000)
+    assert res.status == 0 and abs(res.iters - ora.iters) <= 1
+    assert abs(res.objective - ora.objective) <= 1e-5 * abs(ora.objective)
+    f, g, p, q = (_np(t) for t in (res.plan.f, res.plan.g, res.plan.p, res.plan.q))
+    X = np.exp(f[:, None] + g[None, :] - C / res.gamma) + float(res.plan.kappa.item()) * np.outer(p, q)
+    # rows the rounding makes tight meet r exactly in the GPU's own arithmetic; the
+    # plan re-evaluated in FP64 differs by the pass's log-sum error (a few 1e-6 on
+    # the tcgen05 pass, whose products accumulate in FP32), so 1e-5 there
+    tol = 1e-5 if d == 128 else 1e-6
+    assert (X.sum(1) <= pb.r * (1 + tol)).all() and (X.sum(0) <= pb.c * (1 + tol)).all()
+    assert X.sum() == pytest.approx(pb.s, rel=tol)
