@@ -10,12 +10,14 @@ setup, the accelerated loop to the stop threshold eps / (8 max C), rounding
 to a feasible plan of mass s and the objective <C, X>.
 
 Metric: ASPOT iterations per second at n = 32k (whole solve included), with
-the time to epsilon per solve reported alongside.  Multi-GPU runs are
-independent replicas (one instance per rank, seed = rank): weak scaling.
+the time to epsilon per solve reported alongside; the block rule of
+Algorithm 1 as printed (t mod 3) unless ``--block-rule greedy``, and the
+greedy rule's solves measured beside the headline at N = 1.  Multi-GPU runs
+are independent replicas (one instance per rank, seed = rank): weak scaling.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm):
 each step is a bounded sample, ASPOT iterations of the oracle on the same
-generator at n = m = 2048, scaled to n = 32768 by the number of cost entries.
+generator at n = m = 4096, scaled to n = 32768 by the number of cost entries.
 """
 import argparse
 import json
