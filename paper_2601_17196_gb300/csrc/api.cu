@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/aspot.h"
 #include "kernels.h"
@@ -477,6 +478,15 @@ struct Timer {
   ~Timer() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
 };
 
+// NVTX range for the whole scope (solver phases show up by name in profilers;
+// without an attached tool the calls do nothing).
+struct Nvtx {
+  explicit Nvtx(const char* name) { nvtxRangePushA(name); }
+  ~Nvtx() { nvtxRangePop(); }
+  Nvtx(const Nvtx&) = delete;
+  Nvtx& operator=(const Nvtx&) = delete;
+};
+
 }  // namespace
 
 namespace pot {
@@ -512,8 +522,12 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   Ctx X;
   if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
   X.prof = (params->flags & POT_FLAG_PROFILE) != 0;
+  Nvtx range_all("aspot_solve");
   Timer tm(X.st);
-  if ((s = prologue(X, true)) != POT_OK) return s;
+  {
+    Nvtx range("aspot: setup");
+    if ((s = prologue(X, true)) != POT_OK) return s;
+  }
   const SetupOut so = approx_setup(X, params);
   const int64_t n = prob->n, m = prob->m;
   DevState h{};
@@ -628,8 +642,11 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   const int per = params->check_every > 0 ? params->check_every : 24;
   auto aspot_passes = [](int k) { return k == 2 ? 2 : 3; };      // P1, P2 (, P3a); P3b is not timed
   auto greedy_passes = [](int) { return 2; };                     // P1, P2; the passes at z^t are not timed
-  if (params->block_rule == 1) s = drive(X, per, params->max_iter, greedy_passes, body_greedy);
-  else s = drive(X, per, params->max_iter, aspot_passes, body);
+  {
+    Nvtx range("aspot: iterations");
+    if (params->block_rule == 1) s = drive(X, per, params->max_iter, greedy_passes, body_greedy);
+    else s = drive(X, per, params->max_iter, aspot_passes, body);
+  }
   if (s != POT_OK) return s;
   if ((s = read_state(X, h)) != POT_OK) return s;
   CK(cudaMemcpyAsync(plan->w, &X.S->w_out, sizeof(double), cudaMemcpyDeviceToDevice, X.st));
@@ -640,9 +657,12 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   res->cost_scale = X.cost_scale;
   res->nonfinite = h.nonfinite;
   int branch = 0;
-  if ((s = do_round(X, gamma, plan->u, plan->v, plan, &branch)) != POT_OK) return s;
-  res->rounding_branch = branch;
-  if ((s = do_objective(X, gamma, plan, &res->objective)) != POT_OK) return s;
+  {
+    Nvtx range("aspot: round + objective");
+    if ((s = do_round(X, gamma, plan->u, plan->v, plan, &branch)) != POT_OK) return s;
+    res->rounding_branch = branch;
+    if ((s = do_objective(X, gamma, plan, &res->objective)) != POT_OK) return s;
+  }
   res->mass = prob->s;
   res->ms = tm.stop();
   res->pass_ms = X.pass_ms;
@@ -674,6 +694,7 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
   Ctx X;
   if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
   X.prof = (params->flags & POT_FLAG_PROFILE) != 0;
+  Nvtx range_all("sinkhorn_pot_solve");
   Timer tm(X.st);
   if ((s = prologue(X, true)) != POT_OK) return s;
   SetupOut so = approx_setup(X, params);
@@ -726,7 +747,10 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
     return POT_OK;
   };
   const int per = params->check_every > 0 ? params->check_every : 24;
-  if ((s = drive(X, per, params->max_iter, [](int) { return 2; }, body)) != POT_OK) return s;
+  {
+    Nvtx range("sinkhorn: iterations");
+    if ((s = drive(X, per, params->max_iter, [](int) { return 2; }, body)) != POT_OK) return s;
+  }
   if ((s = read_state(X, h)) != POT_OK) return s;
   // final duals: the first n / m extended potentials, w = 0
   CK(cudaMemcpyAsync(plan->u, V.u, sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));

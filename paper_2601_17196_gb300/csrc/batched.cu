@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/aspot.h"
 #include "common.cuh"
@@ -810,6 +811,11 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   if (s != POT_OK) return s;
   if (!params || !(params->eps > 0.0) || params->max_iter < 1 || !isfinite(params->gamma))
     return bfail(POT_EINVAL, "batched: bad params");
+  // NVTX range over the whole call (no effect without an attached profiler)
+  struct Range {
+    Range() { nvtxRangePushA("aspot_solve_batched"); }
+    ~Range() { nvtxRangePop(); }
+  } range_all;
   if (params->block_rule != 0 && params->block_rule != 1)
     return bfail(POT_EINVAL, "batched: block_rule must be 0 (cyclic) or 1 (greedy)");
   const bool greedy = params->block_rule == 1;
