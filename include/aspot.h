@@ -83,6 +83,21 @@ typedef struct {
   double s;                     /* 0 < s <= min(|r|_1, |c|_1) */
 } pot_problem;
 
+/* Complete state of an ASPOT solve between two iterations (Algorithm 2): the
+ * gradient sequence z~ = (u~, v~, w~), the Greenkhorn sequence z_check with
+ * phi(z_check), theta_t and the iteration count t.  Filled by
+ * aspot_state_export; passed back through pot_params.resume, the solve goes
+ * on from iteration t exactly as if it had not stopped.  Vectors are device
+ * FP64 buffers owned by the caller. */
+typedef struct {
+  double* u_tilde;     /* [n] */
+  double* v_tilde;     /* [m] */
+  double* u_check;     /* [n] */
+  double* v_check;     /* [m] */
+  double w_tilde, w_check, phi_check, theta;
+  int32_t t, pad;
+} pot_aspot_state;
+
 typedef struct {
   double gamma;        /* entropic parameter; <= 0 => eps / (4 log max(n, m)) (Algorithm 2 setup) */
   double eps;          /* accuracy; stop threshold eps~ = eps / (8 max C) (Algorithm 2 setup) */
@@ -97,6 +112,9 @@ typedef struct {
   const double* u0;    /* optional warm start of ASPOT (device FP64 [n]) or NULL */
   const double* v0;    /* optional warm start (device FP64 [m]) or NULL */
   double w0;
+  const pot_aspot_state* resume;  /* ASPOT only: continue from an exported state (NULL => start from z~ = z_check
+                                     = the warm start or zero); excludes u0 / v0 / w0; max_iter counts from 0,
+                                     so it must exceed the state's t */
 } pot_params;
 
 /* Rounded plan, kept implicit (O(n + m) storage):
@@ -238,6 +256,12 @@ POT_API pot_status pot_cost_max(const pot_problem* prob, void* workspace, size_t
 /* Materialise an implicit plan into X (device FP32, row-major, ldx >= m). */
 POT_API pot_status pot_plan_dense(const pot_problem* prob, const pot_plan* plan, double gamma, float* X, int64_t ldx,
                           void* stream);
+
+/* State of the last aspot_solve that used `workspace`, with the same prob and
+ * params->flags: z~ and z_check are copied into state's device vectors and
+ * the scalars are filled, for a later resume.  Synchronises the stream. */
+POT_API pot_status aspot_state_export(const pot_problem* prob, const pot_params* params, void* workspace,
+                                      size_t ws_bytes, pot_aspot_state* state, void* stream);
 
 /* Per-iteration record of the last solve that set POT_FLAG_TRACE, copied
  * into host `out` as [iters][4] doubles (E_t, phi(z^t), phi(z_check^{t+1}),

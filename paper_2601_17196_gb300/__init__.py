@@ -14,6 +14,8 @@ from .binding import (  # noqa: F401
     SolveResult,
     aspot_solve,
     aspot_solve_batched,
+    aspot_state_export,
+    AspotState,
     sinkhorn_pot_solve,
     pot_round,
     pot_objective,

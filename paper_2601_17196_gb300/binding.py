@@ -36,7 +36,8 @@ STATUS = {0: "POT_OK", 1: "POT_EINVAL", 2: "POT_ENOMEM", 3: "POT_ECUDA", 4: "POT
           5: "POT_ENONFINITE", 6: "POT_ETIMEOUT"}
 
 EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_round", "pot_objective",
-            "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "pot_workspace_size_batched",
+            "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "aspot_state_export",
+            "pot_workspace_size_batched",
             "aspot_solve_batched", "pot_marginals_static", "pot_ws_param_count", "pot_ws_init",
             "pot_ws_features_workspace_size", "pot_ws_features", "pot_ws_targets", "pot_ws_workspace_size", "pot_ws_forward", "pot_ws_gradient",
             "pot_ws_train_step", "pot_ws_warm_workspace_size", "pot_ws_warm_start", "pot_rigid_workspace_size",
@@ -61,7 +62,14 @@ class _Problem(ct.Structure):
 class _Params(ct.Structure):
     _fields_ = [("gamma", ct.c_double), ("eps", ct.c_double), ("p_tune", ct.c_double),
                 ("max_iter", ct.c_int32), ("block_rule", ct.c_int32), ("flags", ct.c_int32),
-                ("check_every", ct.c_int32), ("u0", ct.c_void_p), ("v0", ct.c_void_p), ("w0", ct.c_double)]
+                ("check_every", ct.c_int32), ("u0", ct.c_void_p), ("v0", ct.c_void_p), ("w0", ct.c_double),
+                ("resume", ct.c_void_p)]
+
+
+class _State(ct.Structure):
+    _fields_ = [("u_tilde", ct.c_void_p), ("v_tilde", ct.c_void_p), ("u_check", ct.c_void_p),
+                ("v_check", ct.c_void_p), ("w_tilde", ct.c_double), ("w_check", ct.c_double),
+                ("phi_check", ct.c_double), ("theta", ct.c_double), ("t", ct.c_int32), ("pad", ct.c_int32)]
 
 
 class _WsSet(ct.Structure):
@@ -110,6 +118,7 @@ def lib() -> ct.CDLL:
         L.pot_cost_max.argtypes = [P, vp, ct.c_size_t, ct.POINTER(dbl), vp]
         L.pot_plan_dense.argtypes = [P, PL, dbl, vp, i64, vp]
         L.pot_trace.argtypes = [vp, i32, vp, vp]
+        L.aspot_state_export.argtypes = [P, Q, vp, ct.c_size_t, ct.POINTER(_State), vp]
         L.pot_workspace_size_batched.argtypes = [P, i32, ct.POINTER(ct.c_size_t)]
         L.aspot_solve_batched.argtypes = [P, i32, Q, vp, ct.c_size_t, PL, R, vp]
         L.pot_marginals_static.argtypes = [P, dbl, vp, vp, dbl, vp, vp, vp, vp]
@@ -324,20 +333,66 @@ def _workspace(prob: DeviceProblem, flags: int, ws: Optional[torch.Tensor]):
 
 
 def _params(gamma, eps, max_iter, flags, check_every, p_tune=0.0, u0=None, v0=None, w0=0.0,
-            block_rule=0) -> _Params:
+            block_rule=0, resume=None) -> _Params:
     pa = _Params()
     pa.gamma, pa.eps, pa.p_tune = float(gamma), float(eps), float(p_tune)
     pa.max_iter, pa.block_rule, pa.flags, pa.check_every = int(max_iter), int(block_rule), int(flags), int(check_every)
     pa.u0, pa.v0, pa.w0 = _ptr(u0), _ptr(v0), float(w0)
+    pa._resume_ref = resume                      # keeps the state struct alive while pa is used
+    pa.resume = ct.cast(ct.pointer(resume), ct.c_void_p) if resume is not None else None
     return pa
 
 
+@dataclasses.dataclass
+class AspotState:
+    """Complete ASPOT state between iterations (z~, z_check, phi(z_check),
+    theta, t): aspot_state_export fills it, aspot_solve(resume=...) goes on
+    from it."""
+    u_tilde: torch.Tensor
+    v_tilde: torch.Tensor
+    u_check: torch.Tensor
+    v_check: torch.Tensor
+    w_tilde: float = 0.0
+    w_check: float = 0.0
+    phi_check: float = 0.0
+    theta: float = 1.0
+    t: int = 0
+
+    def struct(self) -> _State:
+        st = _State()
+        st.u_tilde, st.v_tilde = self.u_tilde.data_ptr(), self.v_tilde.data_ptr()
+        st.u_check, st.v_check = self.u_check.data_ptr(), self.v_check.data_ptr()
+        st.w_tilde, st.w_check, st.phi_check, st.theta = self.w_tilde, self.w_check, self.phi_check, self.theta
+        st.t = int(self.t)
+        return st
+
+
+def aspot_state_export(prob: "DeviceProblem", ws: torch.Tensor, flags: int = 0) -> AspotState:
+    """State of the last aspot_solve that ran on ``ws`` with this problem and
+    these flags (pass the same ws to that solve)."""
+    dev = prob.r.device
+    st = AspotState(torch.empty(prob.n, dtype=torch.float64, device=dev),
+                    torch.empty(prob.m, dtype=torch.float64, device=dev),
+                    torch.empty(prob.n, dtype=torch.float64, device=dev),
+                    torch.empty(prob.m, dtype=torch.float64, device=dev))
+    raw = st.struct()
+    pa = _params(1.0, 1.0, 1, flags, 0)
+    base, nbytes = _workspace(prob, flags, ws)           # the same aligned start the solve used
+    side, cur = _stream()
+    _check(lib().aspot_state_export(ct.byref(prob.struct()), ct.byref(pa), ct.c_void_p(base.data_ptr()), nbytes,
+                                    ct.byref(raw), ct.c_void_p(side.cuda_stream)))
+    _finish(side, cur)
+    st.w_tilde, st.w_check, st.phi_check, st.theta, st.t = raw.w_tilde, raw.w_check, raw.phi_check, raw.theta, raw.t
+    return st
+
+
 def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, plan, ws,
-           allow_noconv, block_rule=0) -> SolveResult:
+           allow_noconv, block_rule=0, resume=None) -> SolveResult:
     L = lib()
     plan = plan or Plan.empty(prob.n, prob.m, prob.r.device)
     ws, need = _workspace(prob, flags, ws)
-    pa = _params(gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, block_rule)
+    pa = _params(gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, block_rule,
+                 resume.struct() if resume is not None else None)
     res = _Result()
     side, cur = _stream()
     st = _check(getattr(L, fn)(ct.byref(prob.struct()), ct.byref(pa), ct.c_void_p(ws.data_ptr()), need,
@@ -360,11 +415,12 @@ def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w
 def aspot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
                 check_every: int = 0, u0=None, v0=None, w0: float = 0.0, plan: Optional[Plan] = None,
                 ws: Optional[torch.Tensor] = None, allow_noconv: bool = True,
-                block_rule: int = BLOCK_CYCLIC) -> SolveResult:
+                block_rule: int = BLOCK_CYCLIC, resume: Optional["AspotState"] = None) -> SolveResult:
     """ASPOT (Algorithm 2).  block_rule: BLOCK_CYCLIC (t mod 3, Algorithm 1) or
-    BLOCK_GREEDY (the block with the largest decrease of phi)."""
+    BLOCK_GREEDY (the block with the largest decrease of phi).  resume: go on
+    from a state exported by aspot_state_export (max_iter counts from 0)."""
     return _solve("aspot_solve", prob, gamma, eps, max_iter, flags, check_every, 0.0, u0, v0, w0, plan, ws,
-                  allow_noconv, block_rule)
+                  allow_noconv, block_rule, resume)
 
 
 def sinkhorn_pot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 100000, flags: int = 0,

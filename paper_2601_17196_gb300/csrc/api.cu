@@ -182,6 +182,16 @@ pot_status check_params(const pot_params* Q) {
   if (Q->block_rule != 0 && Q->block_rule != 1) return fail(POT_EINVAL, "block_rule must be 0 (cyclic) or 1 (greedy)");
   if (Q->check_every < 0) return fail(POT_EINVAL, "check_every must be >= 0");
   if (!isfinite(Q->w0)) return fail(POT_EINVAL, "w0 must be finite");
+  if (Q->resume) {
+    const pot_aspot_state* R = Q->resume;
+    if (Q->u0 || Q->v0 || Q->w0 != 0.0) return fail(POT_EINVAL, "resume excludes a warm start (u0, v0, w0)");
+    if (!R->u_tilde || !R->v_tilde || !R->u_check || !R->v_check)
+      return fail(POT_EINVAL, "resume: every state vector must be a device buffer");
+    if (!(R->theta > 0.0) || R->theta > 1.0 || R->t < 0) return fail(POT_EINVAL, "resume: bad theta or t");
+    if (!isfinite(R->w_tilde) || !isfinite(R->w_check) || !isfinite(R->phi_check))
+      return fail(POT_EINVAL, "resume: non-finite scalars");
+    if (R->t >= Q->max_iter) return fail(POT_EINVAL, "resume: max_iter must exceed the state's t");
+  }
   return POT_OK;
 }
 
@@ -334,12 +344,12 @@ pot_status read_state(Ctx& X, DevState& h) {
   return POT_OK;
 }
 
-// Run `body` (one iteration per call, k = iteration index mod 3) until the
-// device stop flag is set.  With a capturable stream the iterations are
+// Run `body` (one iteration per call, k = iteration index mod 3, the index
+// starting at k0) until the device stop flag is set.  With a capturable stream the iterations are
 // captured into a CUDA graph of `per` iterations.
 // passes_per_iter(k): timed passes of an iteration with block k
 template <class Body, class PassesPerIter>
-pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, Body body) {
+pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, Body body, int k0 = 0) {
   cudaStreamCaptureStatus cs;
   CK(cudaStreamIsCapturing(X.st, &cs));
   if (cs != cudaStreamCaptureStatusNone) return fail(POT_EINVAL, "the stream is being captured");
@@ -355,7 +365,7 @@ pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, B
     X.pass_ord = 0;
     CK(cudaStreamBeginCapture(X.st, cudaStreamCaptureModeThreadLocal));
     pot_status s = POT_OK;
-    for (int it = 0; it < per && s == POT_OK; ++it) s = body(it % 3);
+    for (int it = 0; it < per && s == POT_OK; ++it) s = body((it + k0) % 3);
     per_graph_launches = X.launches - l0;
     X.launches = l0;
     cudaGraph_t g2 = nullptr;
@@ -376,7 +386,7 @@ pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, B
       X.launches += per_graph_launches;
     } else {
       X.pass_ord = 0;
-      for (int it = 0; it < per && st == POT_OK; ++it) st = body(it % 3);
+      for (int it = 0; it < per && st == POT_OK; ++it) st = body((it + k0) % 3);
       if (st != POT_OK) break;
     }
     launched += per;
@@ -387,7 +397,7 @@ pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, B
       // passes of the iterations that ran in this launch (later ones returned at once)
       const int ran = std::min(flags3[0] - t_prev, per);
       int npass = 0;
-      for (int it = 0; it < ran; ++it) npass += passes_per_iter(it % 3);
+      for (int it = 0; it < ran; ++it) npass += passes_per_iter((it + k0) % 3);
       npass = std::min<int>(npass, (int)X.ev.size() / 2);
       for (int k = 0; k < npass; ++k) {
         float ms = 0.f;
@@ -546,6 +556,22 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
   launch_aspot_init(V, prob->r, prob->c, so.eps_s, params->u0, params->v0, params->w0, X.st); X.launches += 1;
   CKL();
+  const pot_aspot_state* RS = params->resume;
+  if (RS) {
+    // continue a solve: z~, z_check (and z^t = z_check until the first iteration), theta, t, phi(z_check)
+    CK(cudaMemcpyAsync(V.ut, RS->u_tilde, sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));
+    CK(cudaMemcpyAsync(V.vt, RS->v_tilde, sizeof(double) * m, cudaMemcpyDeviceToDevice, X.st));
+    CK(cudaMemcpyAsync(V.uc, RS->u_check, sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));
+    CK(cudaMemcpyAsync(V.vc, RS->v_check, sizeof(double) * m, cudaMemcpyDeviceToDevice, X.st));
+    CK(cudaMemcpyAsync(V.uo, RS->u_check, sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));
+    CK(cudaMemcpyAsync(V.vo, RS->v_check, sizeof(double) * m, cudaMemcpyDeviceToDevice, X.st));
+    DevState h2;
+    if ((s = read_state(X, h2)) != POT_OK) return s;
+    h2.theta = RS->theta; h2.t = RS->t;
+    h2.w_tilde = RS->w_tilde; h2.w_check = RS->w_check; h2.w_out = RS->w_check; h2.w_z = RS->w_check;
+    h2.phi_check = RS->phi_check;
+    if ((s = upload_state(X, h2)) != POT_OK) return s;
+  }
 
   const double gamma = so.gamma;
   PassDesc d = base_desc(X, gamma);
@@ -644,8 +670,9 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   auto greedy_passes = [](int) { return 2; };                     // P1, P2; the passes at z^t are not timed
   {
     Nvtx range("aspot: iterations");
+    const int k0 = RS ? RS->t % 3 : 0;      // the cyclic rule goes on with block t mod 3
     if (params->block_rule == 1) s = drive(X, per, params->max_iter, greedy_passes, body_greedy);
-    else s = drive(X, per, params->max_iter, aspot_passes, body);
+    else s = drive(X, per, params->max_iter, aspot_passes, body, k0);
   }
   if (s != POT_OK) return s;
   if ((s = read_state(X, h)) != POT_OK) return s;
@@ -682,12 +709,40 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   return (pot_status)res->status;
 }
 
+pot_status aspot_state_export(const pot_problem* prob, const pot_params* params, void* workspace, size_t ws_bytes,
+                              pot_aspot_state* state, void* stream) {
+  g_err.clear();
+  pot_status s;
+  if ((s = check_problem(prob)) != POT_OK) return s;
+  if (!params) return fail(POT_EINVAL, "params is NULL");
+  if (!state || !state->u_tilde || !state->v_tilde || !state->u_check || !state->v_check)
+    return fail(POT_EINVAL, "state: every vector must be a device buffer");
+  Ctx X;
+  if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
+  const int64_t n = prob->n, m = prob->m;
+  // the solve's slots: z~ in U[2] / V[2], z_check in U[3] / V[3]
+  CK(cudaMemcpyAsync(state->u_tilde, X.U[2], sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));
+  CK(cudaMemcpyAsync(state->v_tilde, X.V[2], sizeof(double) * m, cudaMemcpyDeviceToDevice, X.st));
+  CK(cudaMemcpyAsync(state->u_check, X.U[3], sizeof(double) * n, cudaMemcpyDeviceToDevice, X.st));
+  CK(cudaMemcpyAsync(state->v_check, X.V[3], sizeof(double) * m, cudaMemcpyDeviceToDevice, X.st));
+  DevState h;
+  if ((s = read_state(X, h)) != POT_OK) return s;
+  state->w_tilde = h.w_tilde;
+  state->w_check = h.w_check;
+  state->phi_check = h.phi_check;
+  state->theta = h.theta;
+  state->t = h.t;
+  state->pad = 0;
+  return POT_OK;
+}
+
 pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params, void* workspace,
                               size_t ws_bytes, pot_plan* plan, pot_result* res, void* stream) {
   g_err.clear();
   pot_status s;
   if ((s = check_problem(prob)) != POT_OK) return s;
   if ((s = check_params(params)) != POT_OK) return s;
+  if (params->resume) return fail(POT_EINVAL, "resume applies to ASPOT only");
   if ((s = check_plan(plan)) != POT_OK) return s;
   if (!res) return fail(POT_EINVAL, "result is NULL");
   memset(res, 0, sizeof(*res));

@@ -818,6 +818,7 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   } range_all;
   if (params->block_rule != 0 && params->block_rule != 1)
     return bfail(POT_EINVAL, "batched: block_rule must be 0 (cyclic) or 1 (greedy)");
+  if (params->resume) return bfail(POT_EINVAL, "batched: resume applies to single ASPOT solves only");
   const bool greedy = params->block_rule == 1;
   if (!plans || !res) return bfail(POT_EINVAL, "batched: plans and results must be host arrays of count entries");
   for (int k = 0; k < count; ++k) {

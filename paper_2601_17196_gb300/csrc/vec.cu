@@ -613,10 +613,11 @@ __global__ void aspot_greedy_final_kernel(AspotVecs V) {
 }
 
 // z_check^{t+1} = Greenkhorn_{k2}(z^t) (greedy rule); w_check was set by the
-// final kernel.  Skipped once the solve has stopped (z_check is not used then).
+// final kernel.  It also runs in the iteration that set the stop flag (so an
+// exported state holds z_check^{t+1}) and after it, where it rewrites the same
+// values: it reads only z^t, the pass sums and scalars that no longer change.
 __global__ void aspot_greedy_apply_kernel(AspotVecs V) {
   DevState* S = V.S;
-  if (S->done) return;
   const int k = S->kg, take = S->take_hat, k2 = S->k2;
   const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -357,3 +357,29 @@ def test_aspot_solve_on_point_clouds(kind, d):
                         cmax=1.0)
     assert abs(res.objective - ora.objective) <= 1e-5 * abs(ora.objective)
     _check_feasible(_plan_fp64(C, res.plan, res.gamma, 1.0), r, c, pb.s)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_aspot_resume_continues_exactly(rule):
+    """Checkpoint / resume: a solve stopped after 61 iterations (not a multiple
+    of 3, so the cyclic rule must go on with block 61 mod 3), exported with
+    aspot_state_export and resumed to 122 iterations, ends bit for bit where an
+    uninterrupted 122-iteration solve ends."""
+    pb = W.small_dense(3, n=200, m=233)
+    dp = _dev(pb)
+    flags = pkg.FLAG_NO_STOP
+    ws = torch.empty(pkg.binding.workspace_bytes(dp, flags) + 256, dtype=torch.uint8, device="cuda")
+    a = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=61, flags=flags, ws=ws, block_rule=rule)
+    assert a.iters == 61
+    st = pkg.aspot_state_export(dp, ws, flags)
+    assert st.t == 61 and 0.0 < st.theta < 1.0
+    b = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=122, flags=flags, block_rule=rule, resume=st)
+    c = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=122, flags=flags, block_rule=rule)
+    assert b.iters == c.iters == 122
+    np.testing.assert_array_equal(_np(b.plan.u), _np(c.plan.u))
+    np.testing.assert_array_equal(_np(b.plan.v), _np(c.plan.v))
+    assert float(b.plan.w.item()) == float(c.plan.w.item())
+    assert b.objective == c.objective
+    with pytest.raises(pkg.PotError) as e:      # a resume excludes a warm start
+        pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=122, resume=st, u0=b.plan.u)
+    assert e.value.status == 1
