@@ -50,7 +50,8 @@ typedef enum {
   POT_ECUDA = 3,       /* a CUDA call failed (message in pot_last_error) */
   POT_ENOCONV = 4,     /* max_iter reached before the stop test; the plan is still rounded and feasible */
   POT_ENONFINITE = 5,  /* NaN/Inf in a potential or a sum */
-  POT_ETIMEOUT = 6
+  POT_ETIMEOUT = 6     /* the stop flag was never set, or a tcgen05 pass's bounded pipeline wait ran out
+                          (its sums are then invalid; see pot_params.wait_limit_ns) */
 } pot_status;
 
 typedef enum {
@@ -115,6 +116,11 @@ typedef struct {
   const pot_aspot_state* resume;  /* ASPOT only: continue from an exported state (NULL => start from z~ = z_check
                                      = the warm start or zero); excludes u0 / v0 / w0; max_iter counts from 0,
                                      so it must exceed the state's t */
+  int64_t wait_limit_ns;  /* bound, in ns, of every pipeline wait inside the tcgen05 passes (0 => 2 s).  A pass
+                             whose wait runs out stops, drains its own copies and MMAs, frees its tensor memory
+                             and raises a flag: the solve then returns POT_ETIMEOUT.  A negative value is a
+                             test hook: the solve's hot-loop tcgen05 passes also withhold their first
+                             accumulator hand-off, so their waits run out after |wait_limit_ns| ns */
 } pot_params;
 
 /* Rounded plan, kept implicit (O(n + m) storage):
@@ -185,10 +191,22 @@ POT_API pot_status pot_objective(const pot_problem* prob, const pot_plan* plan, 
 
 /* Log row and column sums of B(u, v, w): lrow[i] = log sum_j B_ij,
  * lcol[j] = log sum_i B_ij (device FP64, either may be NULL), and
- * *tot = |B|_1 (device FP64 scalar, may be NULL).  Enqueued only. */
+ * *tot = |B|_1 (device FP64 scalar, may be NULL).  Enqueued only; w is
+ * passed by value to a kernel, so the call may be captured into a CUDA graph.
+ * If the tcgen05 pass gave up waiting on its pipeline, every output is NaN
+ * and pot_pass_status reports POT_ETIMEOUT. */
 POT_API pot_status pot_marginals(const pot_problem* prob, double gamma, const double* u, const double* v, double w,
                          void* workspace, size_t ws_bytes, double* lrow, double* lcol, double* tot,
                          void* stream);
+
+/* Bytes of workspace pot_marginals needs (one pass: less than
+ * pot_workspace_size, which covers the solvers' iteration state). */
+POT_API pot_status pot_marginals_workspace_size(const pot_problem* prob, size_t* bytes /* host */);
+
+/* Status of the last pot_marginals that used `workspace`: synchronises
+ * `stream`, then returns POT_ETIMEOUT if its tcgen05 pass gave up waiting on
+ * its pipeline (the outputs are then NaN), else POT_OK. */
+POT_API pot_status pot_pass_status(void* workspace, void* stream);
 
 /* Batched ASPOT: `count` independent problems (host array `probs`, each with
  * its own device buffers, sizes and s; squared-Euclidean point clouds of one
@@ -242,8 +260,9 @@ POT_API pot_status pot_autotune_load(const char* path);
  * device memory (for example while a framework's caching allocator owns the
  * device, or in a loop that forbids allocation after start-up).  The paper
  * has no counterpart: this is a deployment convenience.  Scratch comes from a
- * 16 MiB array inside the library (held on every GPU that loads it); larger
- * problems are rejected with POT_ENOMEM.  All calls share that array, so
+ * 16 MiB array inside the library (held on every GPU that loads it);
+ * problems whose pot_marginals_workspace_size exceeds it are rejected with
+ * POT_ENOMEM.  All calls share that array, so
  * calls that overlap on the GPU race.  The first call on a device looks up
  * the array's address and should come before any stream capture.
  * Arguments and results as pot_marginals.  Enqueued only. */

@@ -22,6 +22,8 @@ from .binding import (  # noqa: F401
     pot_marginals,
     pot_cost_max,
     pot_plan_dense,
+    workspace_bytes,
+    marginals_workspace_bytes,
     lib,
     exported_symbols,
     FLAG_STOP_RAW_EPS,

@@ -36,7 +36,7 @@ STATUS = {0: "POT_OK", 1: "POT_EINVAL", 2: "POT_ENOMEM", 3: "POT_ECUDA", 4: "POT
           5: "POT_ENONFINITE", 6: "POT_ETIMEOUT"}
 
 EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_round", "pot_objective",
-            "pot_marginals", "pot_cost_max", "pot_plan_dense", "pot_trace", "aspot_state_export",
+            "pot_marginals", "pot_marginals_workspace_size", "pot_pass_status", "pot_cost_max", "pot_plan_dense", "pot_trace", "aspot_state_export",
             "pot_workspace_size_batched",
             "aspot_solve_batched", "pot_marginals_static", "pot_ws_param_count", "pot_ws_init",
             "pot_ws_features_workspace_size", "pot_ws_features", "pot_ws_targets", "pot_ws_workspace_size", "pot_ws_forward", "pot_ws_gradient",
@@ -63,7 +63,7 @@ class _Params(ct.Structure):
     _fields_ = [("gamma", ct.c_double), ("eps", ct.c_double), ("p_tune", ct.c_double),
                 ("max_iter", ct.c_int32), ("block_rule", ct.c_int32), ("flags", ct.c_int32),
                 ("check_every", ct.c_int32), ("u0", ct.c_void_p), ("v0", ct.c_void_p), ("w0", ct.c_double),
-                ("resume", ct.c_void_p)]
+                ("resume", ct.c_void_p), ("wait_limit_ns", ct.c_int64)]
 
 
 class _State(ct.Structure):
@@ -115,6 +115,8 @@ def lib() -> ct.CDLL:
         L.pot_round.argtypes = [P, dbl, vp, vp, dbl, vp, ct.c_size_t, PL, ct.POINTER(i32), vp]
         L.pot_objective.argtypes = [P, PL, dbl, vp, ct.c_size_t, ct.POINTER(dbl), vp]
         L.pot_marginals.argtypes = [P, dbl, vp, vp, dbl, vp, ct.c_size_t, vp, vp, vp, vp]
+        L.pot_pass_status.argtypes = [vp, vp]
+        L.pot_marginals_workspace_size.argtypes = [P, ct.POINTER(ct.c_size_t)]
         L.pot_cost_max.argtypes = [P, vp, ct.c_size_t, ct.POINTER(dbl), vp]
         L.pot_plan_dense.argtypes = [P, PL, dbl, vp, i64, vp]
         L.pot_trace.argtypes = [vp, i32, vp, vp]
@@ -305,6 +307,13 @@ def workspace_bytes(prob: DeviceProblem, flags: int = 0) -> int:
     return int(b.value)
 
 
+def marginals_workspace_bytes(prob: DeviceProblem) -> int:
+    """Workspace bytes of one pot_marginals pass."""
+    b = ct.c_size_t(0)
+    _check(lib().pot_marginals_workspace_size(ct.byref(prob.struct()), ct.byref(b)))
+    return int(b.value)
+
+
 _ws_cache = {}
 
 
@@ -333,8 +342,9 @@ def _workspace(prob: DeviceProblem, flags: int, ws: Optional[torch.Tensor]):
 
 
 def _params(gamma, eps, max_iter, flags, check_every, p_tune=0.0, u0=None, v0=None, w0=0.0,
-            block_rule=0, resume=None) -> _Params:
+            block_rule=0, resume=None, wait_limit_ns=0) -> _Params:
     pa = _Params()
+    pa.wait_limit_ns = int(wait_limit_ns)
     pa.gamma, pa.eps, pa.p_tune = float(gamma), float(eps), float(p_tune)
     pa.max_iter, pa.block_rule, pa.flags, pa.check_every = int(max_iter), int(block_rule), int(flags), int(check_every)
     pa.u0, pa.v0, pa.w0 = _ptr(u0), _ptr(v0), float(w0)
@@ -387,12 +397,12 @@ def aspot_state_export(prob: "DeviceProblem", ws: torch.Tensor, flags: int = 0) 
 
 
 def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, plan, ws,
-           allow_noconv, block_rule=0, resume=None) -> SolveResult:
+           allow_noconv, block_rule=0, resume=None, wait_limit_ns=0) -> SolveResult:
     L = lib()
     plan = plan or Plan.empty(prob.n, prob.m, prob.r.device)
     ws, need = _workspace(prob, flags, ws)
     pa = _params(gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w0, block_rule,
-                 resume.struct() if resume is not None else None)
+                 resume.struct() if resume is not None else None, wait_limit_ns)
     res = _Result()
     side, cur = _stream()
     st = _check(getattr(L, fn)(ct.byref(prob.struct()), ct.byref(pa), ct.c_void_p(ws.data_ptr()), need,
@@ -415,12 +425,15 @@ def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w
 def aspot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
                 check_every: int = 0, u0=None, v0=None, w0: float = 0.0, plan: Optional[Plan] = None,
                 ws: Optional[torch.Tensor] = None, allow_noconv: bool = True,
-                block_rule: int = BLOCK_CYCLIC, resume: Optional["AspotState"] = None) -> SolveResult:
+                block_rule: int = BLOCK_CYCLIC, resume: Optional["AspotState"] = None,
+                wait_limit_ns: int = 0) -> SolveResult:
     """ASPOT (Algorithm 2).  block_rule: BLOCK_CYCLIC (t mod 3, Algorithm 1) or
     BLOCK_GREEDY (the block with the largest decrease of phi).  resume: go on
-    from a state exported by aspot_state_export (max_iter counts from 0)."""
+    from a state exported by aspot_state_export (max_iter counts from 0).
+    wait_limit_ns: bound of the tcgen05 passes' pipeline waits (0: 2 s;
+    negative: the stall test hook of pot_params)."""
     return _solve("aspot_solve", prob, gamma, eps, max_iter, flags, check_every, 0.0, u0, v0, w0, plan, ws,
-                  allow_noconv, block_rule, resume)
+                  allow_noconv, block_rule, resume, wait_limit_ns)
 
 
 def sinkhorn_pot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 100000, flags: int = 0,
@@ -464,7 +477,7 @@ def pot_marginals(prob: DeviceProblem, gamma: float, u: torch.Tensor, v: torch.T
     _check(lib().pot_marginals(ct.byref(prob.struct()), gamma, u.data_ptr(), v.data_ptr(), float(w),
                                ct.c_void_p(ws.data_ptr()), need, lrow.data_ptr(), lcol.data_ptr(), tot.data_ptr(),
                                ct.c_void_p(side.cuda_stream)))
-    side.synchronize()
+    _check(lib().pot_pass_status(ct.c_void_p(ws.data_ptr()), ct.c_void_p(side.cuda_stream)))
     _finish(side, cur)
     return lrow, lcol, float(tot.item())
 

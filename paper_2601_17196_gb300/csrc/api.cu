@@ -72,7 +72,9 @@ bool wants_tc(const pot_problem* P, int flags) {
   return tc_supported(d);
 }
 
-Layout make_layout(const pot_problem* P, int flags) {
+// nslots: FP64 potential slots per side (the solvers use kSlots; a lone pass
+// needs one, for its combined log-sums)
+Layout make_layout(const pot_problem* P, int flags, int nslots = kSlots) {
   Layout L;
   const int64_t n = P->n, m = P->m;
   L.sl = simt_layout(n, m);
@@ -106,8 +108,8 @@ Layout make_layout(const pot_problem* P, int flags) {
   L.off_yn = o; o = align_up(o + sizeof(float) * (m + 1));
   L.off_rowp = o; o = align_up(o + sizeof(float2) * L.ncolblk * n);
   L.off_colp = o; o = align_up(o + sizeof(float2) * L.nrowblk * m);
-  for (int k = 0; k < kSlots; ++k) { L.off_u[k] = o; o = align_up(o + sizeof(double) * (n + 2)); }
-  for (int k = 0; k < kSlots; ++k) { L.off_v[k] = o; o = align_up(o + sizeof(double) * (m + 2)); }
+  for (int k = kSlots - nslots; k < kSlots; ++k) { L.off_u[k] = o; o = align_up(o + sizeof(double) * (n + 2)); }
+  for (int k = kSlots - nslots; k < kSlots; ++k) { L.off_v[k] = o; o = align_up(o + sizeof(double) * (m + 2)); }
   {
     const int64_t np = L.use_tc ? std::max<int64_t>(L.tl.n_pad, n) : n;
     const int64_t mp = L.use_tc ? std::max<int64_t>(L.tl.m_pad, m) : m;
@@ -137,6 +139,8 @@ struct Ctx {
   double* V[kSlots];
   double cost_scale = 1.0;
   double max_raw = 0.0;
+  uint64_t wait_ns = 0;         // bound of the tcgen05 passes' pipeline waits (0: their 2 s default)
+  int stall = 0;                // test hook: hot-loop tcgen05 passes withhold their first hand-off
   double sum_r = 0, sum_c = 0, min_r = 0, min_c = 0;
   // kernel launch count and optional CUDA-event timing of the main-loop passes
   int64_t launches = 0;
@@ -195,10 +199,11 @@ pot_status check_params(const pot_params* Q) {
   return POT_OK;
 }
 
-pot_status bind(Ctx& X, const pot_problem* P, int flags, void* ws, size_t ws_bytes, void* stream) {
+pot_status bind(Ctx& X, const pot_problem* P, int flags, void* ws, size_t ws_bytes, void* stream,
+                int nslots = kSlots) {
   X.P = P;
   X.st = (cudaStream_t)stream;
-  X.L = make_layout(P, flags);
+  X.L = make_layout(P, flags, nslots);
   if (!ws) return fail(POT_EINVAL, "workspace is NULL");
   if ((uintptr_t)ws % 256 != 0) return fail(POT_EINVAL, "workspace must be 256-byte aligned");
   if (ws_bytes < X.L.total) return fail(POT_ENOMEM, "workspace too small: %zu < %zu bytes", ws_bytes, X.L.total);
@@ -230,7 +235,29 @@ PassDesc base_desc(const Ctx& X, double gamma) {
   d.gC = gamma > 0.0 ? X.cost_scale / gamma : 0.0;
   d.row_part = X.rowp; d.col_part = X.colp; d.red_part = X.red;
   d.rowA = X.rowA; d.colA = X.colA; d.colB = X.colB; d.err = &X.S->tc_err;
+  d.wait_ns = X.wait_ns > 0 ? X.wait_ns : kDefaultWaitNs;
+  d.stall = X.stall;
   return d;
+}
+
+// A tcgen05 pass whose bounded pipeline wait ran out raises S->tc_err (its
+// sums are then invalid).  clear_tc resets the flag at the start of a call;
+// check_tc synchronises the stream and turns a raised flag into POT_ETIMEOUT.
+pot_status clear_tc(Ctx& X) {
+  CK(cudaMemsetAsync(&X.S->tc_err, 0, sizeof(int), X.st));
+  return POT_OK;
+}
+
+pot_status tc_timeout() {
+  return fail(POT_ETIMEOUT, "a tcgen05 pass gave up waiting on its pipeline (bounded mbarrier wait ran out); "
+                            "its sums are invalid");
+}
+
+pot_status check_tc(Ctx& X) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, &X.S->tc_err, sizeof(int), cudaMemcpyDeviceToHost, X.st));
+  CK(cudaStreamSynchronize(X.st));
+  return e ? tc_timeout() : POT_OK;
 }
 
 pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true) {
@@ -277,6 +304,8 @@ int64_t pass_ctas(const Ctx& X) {  // one partial per CTA of a max / objective p
 pot_status prologue(Ctx& X, bool need_max) {
   const pot_problem* P = X.P;
   CK(cudaMemsetAsync(X.cnt, 0, sizeof(unsigned int) * 8, X.st));
+  pot_status s0 = clear_tc(X);
+  if (s0 != POT_OK) return s0;
   launch_marg_stats(P->r, P->c, P->n, P->m, X.red, X.cnt, X.stats, X.st); X.launches += 1;
   CKL();
   if (P->kind != POT_COST_DENSE_F32) {
@@ -294,8 +323,11 @@ pot_status prologue(Ctx& X, bool need_max) {
     CKL();
   }
   double h[8];
+  int tce = 0;
   CK(cudaMemcpyAsync(h, X.stats, sizeof(h), cudaMemcpyDeviceToHost, X.st));
+  CK(cudaMemcpyAsync(&tce, &X.S->tc_err, sizeof(int), cudaMemcpyDeviceToHost, X.st));
   CK(cudaStreamSynchronize(X.st));
+  if (tce) return tc_timeout();
   X.sum_r = h[0]; X.sum_c = h[1]; X.min_r = h[2]; X.min_c = h[3];
   if (h[4] != 0.0) return fail(POT_EINVAL, "r and c must be finite and non-negative");
   if (!(X.sum_r > 0.0) || !(X.sum_c > 0.0)) return fail(POT_EINVAL, "r and c must have positive mass");
@@ -377,7 +409,7 @@ pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, B
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return fail(POT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
   }
   pot_status st = POT_OK;
-  int flags3[3] = {0, 0, 0};         // DevState t, take_hat, done (adjacent ints)
+  int flags3[6] = {0, 0, 0, 0, 0, 0};   // DevState t, take_hat, done, max_iter, nonfinite, tc_err (adjacent ints)
   int t_prev = 0;
   while (launched < max_iter + per) {
     if (graphs) {
@@ -406,6 +438,7 @@ pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, B
     }
     t_prev = flags3[0];
     done = flags3[2];
+    if (flags3[5]) { st = tc_timeout(); break; }
     if (done) break;
   }
   X.in_loop = false;
@@ -438,6 +471,7 @@ pot_status do_round(Ctx& X, double gamma, const double* u, const double* v, pot_
   CKL();
   DevState h;
   if ((s = read_state(X, h)) != POT_OK) return s;
+  if (h.tc_err) return tc_timeout();
   if (h.m2 >= P->s) {
     launch_round_r3(R, X.st); X.launches += 1;
     CKL();
@@ -461,10 +495,21 @@ pot_status do_objective(Ctx& X, double gamma, const pot_plan* plan, double* out)
   launch_reduce_parts(X.red, pass_ctas(X), 0, X.stats + 7, X.st); X.launches += 1;
   CKL();
   double h;
+  int tce = 0;
   CK(cudaMemcpyAsync(&h, X.stats + 7, sizeof(double), cudaMemcpyDeviceToHost, X.st));
+  CK(cudaMemcpyAsync(&tce, &X.S->tc_err, sizeof(int), cudaMemcpyDeviceToHost, X.st));
   CK(cudaStreamSynchronize(X.st));
+  if (tce) return tc_timeout();
   *out = h * X.cost_scale;
   return POT_OK;
+}
+
+// pot_params.wait_limit_ns: > 0 bounds the tcgen05 passes' pipeline waits;
+// < 0 also injects a stall into the hot-loop passes (a test hook); 0 keeps 2 s.
+void set_wait(Ctx& X, const pot_params* Q) {
+  const int64_t w = Q->wait_limit_ns;
+  X.wait_ns = w == 0 ? 0 : (uint64_t)(w < 0 ? -w : w);
+  X.stall = w < 0 ? 1 : 0;
 }
 
 pot_status check_plan(const pot_plan* plan) {
@@ -505,6 +550,8 @@ pot_status set_last_error(pot_status s, const char* msg) {
   g_err = msg;
   return s;
 }
+// Scratch bytes pot_marginals needs for this problem (its one-pass layout).
+size_t marginals_scratch_bytes(const pot_problem* prob) { return make_layout(prob, 0, 1).total; }
 }  // namespace pot
 
 extern "C" {
@@ -520,6 +567,15 @@ pot_status pot_workspace_size(const pot_problem* prob, const pot_params* params,
   return POT_OK;
 }
 
+pot_status pot_marginals_workspace_size(const pot_problem* prob, size_t* bytes) {
+  g_err.clear();
+  pot_status s = check_problem(prob);
+  if (s != POT_OK) return s;
+  if (!bytes) return fail(POT_EINVAL, "bytes is NULL");
+  *bytes = make_layout(prob, 0, 1).total;
+  return POT_OK;
+}
+
 pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* workspace, size_t ws_bytes,
                        pot_plan* plan, pot_result* res, void* stream) {
   g_err.clear();
@@ -532,6 +588,7 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   Ctx X;
   if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
   X.prof = (params->flags & POT_FLAG_PROFILE) != 0;
+  set_wait(X, params);
   Nvtx range_all("aspot_solve");
   Timer tm(X.st);
   {
@@ -749,6 +806,7 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
   Ctx X;
   if ((s = bind(X, prob, params->flags, workspace, ws_bytes, stream)) != POT_OK) return s;
   X.prof = (params->flags & POT_FLAG_PROFILE) != 0;
+  set_wait(X, params);
   Nvtx range_all("sinkhorn_pot_solve");
   Timer tm(X.st);
   if ((s = prologue(X, true)) != POT_OK) return s;
@@ -851,8 +909,7 @@ pot_status pot_round(const pot_problem* prob, double gamma, const double* u, con
   int b = 0;
   if ((s = do_round(X, gamma, u, v, plan, &b)) != POT_OK) return s;
   if (branch) *branch = b;
-  CK(cudaStreamSynchronize(X.st));
-  return POT_OK;
+  return check_tc(X);
 }
 
 pot_status pot_objective(const pot_problem* prob, const pot_plan* plan, double gamma, void* workspace,
@@ -878,20 +935,21 @@ pot_status pot_marginals(const pot_problem* prob, double gamma, const double* u,
   if (!u || !v || !isfinite(w)) return fail(POT_EINVAL, "u, v must be device pointers and w finite");
   if (prob->cost_scale == 0.0) return fail(POT_EINVAL, "pot_marginals needs an explicit cost_scale > 0");
   Ctx X;
-  if ((s = bind(X, prob, 0, workspace, ws_bytes, stream)) != POT_OK) return s;
+  if ((s = bind(X, prob, 0, workspace, ws_bytes, stream, 1)) != POT_OK) return s;   // one pass: one slot per side
   X.cost_scale = prob->cost_scale;
   if (prob->kind != POT_COST_DENSE_F32) {
     launch_sqnorm(prob->kind, prob->X, prob->n, prob->d, prob->ldx, X.xn, X.st);
     launch_sqnorm(prob->kind, prob->Y, prob->m, prob->d, prob->ldy, X.yn, X.st);
     CKL();
   }
-  CK(cudaMemcpyAsync(&X.S->w_out, &w, sizeof(double), cudaMemcpyHostToDevice, X.st));
-  CK(cudaMemsetAsync(X.cnt, 0, sizeof(unsigned int) * 8, X.st));
+  // w (by value in a kernel argument), the reduction counters and the stall flag
+  launch_marginals_setup(X.S, w, X.cnt, X.st);
   PassDesc d = base_desc(X, gamma);
   d.mode = PASS_ROWS | (lcol ? PASS_COLS : 0);
   d.arow0 = u; d.bcol0 = v; d.aoff0 = &X.S->w_out;
   if ((s = run_pass(X, d)) != POT_OK) return s;
-  launch_marginals_out(prob->n, prob->m, X.lrow, lcol ? X.lcol : nullptr, lrow, lcol, X.red, X.cnt, tot, X.st);
+  launch_marginals_out(prob->n, prob->m, X.lrow, lcol ? X.lcol : nullptr, lrow, lcol, X.red, X.cnt, tot,
+                       &X.S->tc_err, X.st);
   CKL();
   return POT_OK;
 }
@@ -924,6 +982,16 @@ pot_status pot_plan_dense(const pot_problem* prob, const pot_plan* plan, double 
   launch_dense_plan(d, plan->f, plan->g, plan->p, plan->q, plan->kappa, Xout, ldx, (cudaStream_t)stream);
   CKL();
   return POT_OK;
+}
+
+pot_status pot_pass_status(void* workspace, void* stream) {
+  g_err.clear();
+  if (!workspace) return fail(POT_EINVAL, "workspace is NULL");
+  const DevState* S = (const DevState*)((char*)workspace);   // the state sits at offset 0
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, &S->tc_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return e ? tc_timeout() : POT_OK;
 }
 
 pot_status pot_trace(void* workspace, int32_t iters, double* out, void* stream) {

@@ -36,6 +36,11 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
+// Maxima that keep a NaN (fmaxf / fmax drop it): a NaN anywhere in the cost
+// must reach the prologue's finiteness check through the max-cost pass.
+__device__ __forceinline__ float nanmaxf(float a, float b) { return (a > b || a != a) ? a : b; }
+__device__ __forceinline__ double nanmax(double a, double b) { return (a > b || a != a) ? a : b; }
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));

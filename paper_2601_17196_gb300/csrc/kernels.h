@@ -166,8 +166,11 @@ void launch_round_r2(const RoundVecs& V, cudaStream_t st);
 void launch_round_r3(const RoundVecs& V, cudaStream_t st);
 void launch_round_r4(const RoundVecs& V, cudaStream_t st);
 
+void launch_marginals_setup(DevState* S, double w, unsigned int* counter, cudaStream_t st);
+// err: a raised pass error flag turns every output into NaN
 void launch_marginals_out(int64_t n, int64_t m, const double* lrow_in, const double* lcol_in, double* lrow,
-                          double* lcol, double* red, unsigned int* counter, double* tot_out, cudaStream_t st);
+                          double* lcol, double* red, unsigned int* counter, double* tot_out, const int* err,
+                          cudaStream_t st);
 void launch_combine(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow, const float2* col_part,
                     int64_t nrowblk, int64_t m, double* lcol, const int* done, cudaStream_t st,
                     const int* skip = nullptr, int skip_if = 0);

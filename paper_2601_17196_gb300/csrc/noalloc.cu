@@ -12,8 +12,10 @@
 //
 // Limits and sharing rules:
 //  * the array holds kStaticScratchBytes (16 MiB) on every GPU that loads the
-//    library, until the process exits; problems whose scratch would exceed it
-//    are rejected with POT_ENOMEM before anything is launched;
+//    library, until the process exits; problems whose one-pass scratch (the
+//    layout pot_marginals binds: state, pass partials, one slot of log-sums
+//    per side, per-pass terms) would exceed it are rejected with POT_ENOMEM
+//    before anything is launched;
 //  * every call uses the same array, which keeps the previous call's contents;
 //    the counters that must start at zero are cleared by the pass itself, and
 //    two calls whose work overlaps on the GPU (different streams, or
@@ -28,6 +30,7 @@
 
 namespace pot {
 pot_status set_last_error(pot_status s, const char* msg);
+size_t marginals_scratch_bytes(const pot_problem* prob);
 }
 
 namespace {
@@ -63,8 +66,9 @@ extern "C" POT_API pot_status pot_marginals_static(const pot_problem* prob, doub
                                                    const double* v, double w, double* lrow, double* lcol,
                                                    double* tot, void* stream) {
   size_t need = 0;
-  pot_status s = pot_workspace_size(prob, nullptr, &need);
+  pot_status s = pot_workspace_size(prob, nullptr, &need);     // argument checks
   if (s != POT_OK) return s;
+  need = pot::marginals_scratch_bytes(prob);                   // what the pass itself binds
   if (need > kStaticScratchBytes)
     return pot::set_last_error(POT_ENOMEM, "pot_marginals_static: the problem needs more scratch than the "
                                            "16 MiB static array; use pot_marginals with a workspace");

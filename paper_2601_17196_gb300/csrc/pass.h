@@ -17,6 +17,8 @@ namespace pot {
 
 enum PassMode { PASS_ROWS = 1, PASS_COLS = 2, PASS_OBJ = 4, PASS_MAXCOST = 8 };
 
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;   // default bound of a pass's pipeline waits (2 s)
+
 enum CostKind { COST_DENSE_F32 = 0, COST_SQEUCLID_BF16 = 1, COST_SQEUCLID_F16 = 2, COST_SQEUCLID_F32 = 3 };
 
 struct PassDesc {
@@ -40,7 +42,9 @@ struct PassDesc {
   int skip_if;
   // tensor-core path only: per-pass row / column terms (padded) and an error flag
   float4* rowA; float2* colA; float2* colB;
-  int* err;
+  int* err;              // set to 1 when a bounded pipeline wait of the pass ran out
+  uint64_t wait_ns;      // bound of each pipeline wait (ns)
+  int stall;             // test hook: the hot-loop tcgen05 pass withholds its first accumulator hand-off
 };
 
 // True when the pass must not run (the solve has stopped, or its skip

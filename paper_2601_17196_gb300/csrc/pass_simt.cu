@@ -249,8 +249,8 @@ const bool want_rows = MT == 0 ? (P.mode & PASS_ROWS) != 0 : (MT == 1 || MT == 2
         for (int q = 0; q < NC; ++q) {
           const int64_t j = col0 + 128 * (q >> 2) + 4 * lane + (q & 3);
           if (j < P.m) {
-            const float cst = sq ? fmaxf(xn + P.yn[j] - 2.f * cost[rr][q], 0.f) : cost[rr][q];
-            maxc = fmaxf(maxc, cst);
+            const float cst = sq ? nanmaxf(xn + P.yn[j] - 2.f * cost[rr][q], 0.f) : cost[rr][q];
+            maxc = nanmaxf(maxc, cst);
             if (want_obj) {
               const float x = (lg[rr][q] > -1.0e29f ? ex2(lg[rr][q]) : 0.f) + kpi * qv[q];
               rowacc = fmaf(cst, x, rowacc);
@@ -331,13 +331,13 @@ const bool want_rows = MT == 0 ? (P.mode & PASS_ROWS) != 0 : (MT == 1 || MT == 2
     if (want_obj) v = warp_sum_d(v);
     else {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+      for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     }
     if (lane == 0) sRed[warp] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
       double acc = want_obj ? 0.0 : sRed[0];
-      for (int w = 0; w < kWarps; ++w) acc = want_obj ? acc + sRed[w] : fmax(acc, sRed[w]);
+      for (int w = 0; w < kWarps; ++w) acc = want_obj ? acc + sRed[w] : nanmax(acc, sRed[w]);
       P.red_part[red_idx] = acc;
     }
   }

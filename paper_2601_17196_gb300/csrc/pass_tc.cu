@@ -122,7 +122,7 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
       int issued = 0;
       for (int li = 0; li < nt; ++li) {
         const int s = li % NSTAGE;
-        if (li >= NSTAGE && !mbar_wait(emptyB + s, ((li / NSTAGE) - 1) & 1, s_abort)) break;
+        if (li >= NSTAGE && !mbar_wait(emptyB + s, ((li / NSTAGE) - 1) & 1, s_abort, P.wait_ns)) break;
         unsigned char* sB = smem + SL.b_off + s * SL.b_stage;
         mbar_expect_tx(fullB + s, SL.b_stage);
         const int col = (int)((t_begin + li) * BN);
@@ -130,15 +130,8 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
         issued = li + 1;
       }
       // wait for our own loads still in flight before the CTA may exit
-      for (int li = (issued > NSTAGE ? issued - NSTAGE : 0); li < issued; ++li) {
-        const int s = li % NSTAGE;
-        const uint64_t t0 = gtime();
-        while (!mbar_try(fullB + s, (li / NSTAGE) & 1) && gtime() - t0 < kTimeoutNs) {}
-      }
-      {
-        const uint64_t t0 = gtime();
-        while (!mbar_try(fullA, 0) && gtime() - t0 < kTimeoutNs) {}
-      }
+      for (int li = (issued > NSTAGE ? issued - NSTAGE : 0); li < issued; ++li) mbar_drain(fullB + li % NSTAGE, (li / NSTAGE) & 1);
+      mbar_drain(fullA, 0);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA
@@ -146,11 +139,11 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
       const uint32_t idesc = idesc_bf16(BM, BN);
       const uint32_t a_base = smem_u32(smem + SL.a_off);
       int last = -1;
-      if (mbar_wait(fullA, 0, s_abort)) {
+      if (mbar_wait(fullA, 0, s_abort, P.wait_ns)) {
         for (int li = 0; li < nt; ++li) {
           const int b = li & 1, s = li % NSTAGE;
-          if (li >= 2 && !mbar_wait(tempty + b, ((li >> 1) - 1) & 1, s_abort)) break;
-          if (!mbar_wait(fullB + s, (li / NSTAGE) & 1, s_abort)) break;
+          if (li >= 2 && !mbar_wait(tempty + b, ((li >> 1) - 1) & 1, s_abort, P.wait_ns)) break;
+          if (!mbar_wait(fullB + s, (li / NSTAGE) & 1, s_abort, P.wait_ns)) break;
           tc_fence_after();
           const uint32_t b_base = smem_u32(smem + SL.b_off + s * SL.b_stage);
           for (int kb = 0; kb < kblocks; ++kb) {
@@ -167,10 +160,7 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
         }
       }
       // the accumulator of the last issued tile must be complete before TMEM is freed
-      if (last >= 0) {
-        const uint64_t t0 = gtime();
-        while (!mbar_try(tfull + (last & 1), (last >> 1) & 1) && gtime() - t0 < kTimeoutNs) {}
-      }
+      if (last >= 0) mbar_drain(tfull + (last & 1), (last >> 1) & 1);
     }
   } else {
     // ----------------------------------------------------------- epilogue
@@ -193,7 +183,7 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
       const int b = li & 1;
       const int64_t j0 = (t_begin + li) * BN + h * 64;
       float t[64];
-      const bool ok = mbar_wait(tfull + b, (li >> 1) & 1, s_abort);
+      const bool ok = mbar_wait(tfull + b, (li >> 1) & 1, s_abort, P.wait_ns);
       if (ok) {
         tc_fence_after();
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + h * 64);
@@ -236,13 +226,14 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
         t[2 * c] = fmaf(k2, t[2 * c], ahi + bb.x) + bb.y;
         t[2 * c + 1] = fmaf(k2, t[2 * c + 1], ahi + bb.z) + bb.w;
       }
+      if (MODE == M_MAX) {          // NaN-keeping max: a NaN coordinate must reach the finiteness check
+#pragma unroll
+        for (int k = 0; k < 64; ++k) maxc = nanmaxf(maxc, t[k]);
+        continue;
+      }
       float mx = t[0];
 #pragma unroll
       for (int k = 1; k < 64; ++k) mx = fmaxf(mx, t[k]);
-      if (MODE == M_MAX) {
-        maxc = fmaxf(maxc, mx);
-        continue;
-      }
       const bool rowok = mx > -1.0e29f;
       float ssum = 0.f;
 #pragma unroll
@@ -313,13 +304,13 @@ tc_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX,
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const double y = __shfl_xor_sync(0xffffffffu, v, o);
-        v = (MODE == M_MAX) ? fmax(v, y) : v + y;
+        v = (MODE == M_MAX) ? nanmax(v, y) : v + y;
       }
       if (lane == 0) red[warp - 2] = v;
       named_bar(3, 256);
       if (threadIdx.x == 64) {
         double mm = red[0];
-        for (int w = 1; w < 8; ++w) mm = (MODE == M_MAX) ? fmax(mm, red[w]) : mm + red[w];
+        for (int w = 1; w < 8; ++w) mm = (MODE == M_MAX) ? nanmax(mm, red[w]) : mm + red[w];
         P.red_part[unit] = mm;
       }
     }

@@ -83,6 +83,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
   uint64_t* tempty = bars + 12;                // [2]
   uint64_t* cfull = bars + 14;                 // [NCA]
   uint64_t* cempty = bars + 14 + NCA;          // [NCA]
+  uint64_t* spare = bars + 14 + 2 * NCA;       // stall test hook: receives the withheld hand-off
   uint32_t* s_tmem = (uint32_t*)(smem + SL.misc_off);
   volatile int* s_abort = (volatile int*)(smem + SL.misc_off + 4);
   float4* sCA = (float4*)(smem + SL.ca_off);
@@ -101,6 +102,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
     for (int s = 0; s < nst; ++s) { mbar_init(fullB + s, 1); mbar_init(emptyB + s, 1); }
     for (int b = 0; b < 2; ++b) { mbar_init(tfull + b, 1); mbar_init(tempty + b, NEPI); }
     for (int k = 0; k < NCA; ++k) { mbar_init(cfull + k, 32); mbar_init(cempty + k, NEPI); }
+    mbar_init(spare, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -122,7 +124,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
     for (int li = 0; li < nt; ++li) {
       const int64_t tau = t_start + li, rb = tau / ntiles, ct = tau % ntiles;
       if (rb != cur_rb) {
-        if (a_idx > 0 && !mbar_wait(aempty, (a_idx - 1) & 1, s_abort)) break;
+        if (a_idx > 0 && !mbar_wait(aempty, (a_idx - 1) & 1, s_abort, P.wait_ns)) break;
         if (lane == 0) {
           mbar_expect_tx(fullA, (uint32_t)(kblocks * 2 * 128 * 128));
           for (int kb = 0; kb < kblocks; ++kb)
@@ -133,7 +135,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
         cur_rb = rb;
       }
       const int s = li % nst;
-      if (li >= nst && !mbar_wait(emptyB + s, ((li / nst) - 1) & 1, s_abort)) break;
+      if (li >= nst && !mbar_wait(emptyB + s, ((li / nst) - 1) & 1, s_abort, P.wait_ns)) break;
       if (lane == 0) {
         unsigned char* sB = smem + SL.b_off + s * SL.b_stage;
         mbar_expect_tx(fullB + s, SL.b_stage);
@@ -141,7 +143,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
       }
       issued = li + 1;
       const int cs = li % NCA;
-      if (li >= NCA && !mbar_wait(cempty + cs, ((li / NCA) - 1) & 1, s_abort)) break;
+      if (li >= NCA && !mbar_wait(cempty + cs, ((li / NCA) - 1) & 1, s_abort, P.wait_ns)) break;
       {
         // lane l < BN2/4 stages columns 4l .. 4l+3 as pairs (bhi_j, bhi_j+1, blo_j, blo_j+1)
         if (lane < BN2 / 4) {
@@ -156,14 +158,8 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
     __syncwarp();
     if (lane == 0) {
       // our own loads still in flight must land before the CTA may exit
-      for (int li = (issued > nst ? issued - nst : 0); li < issued; ++li) {
-        const uint64_t t0 = gtime();
-        while (!mbar_try(fullB + li % nst, (li / nst) & 1) && gtime() - t0 < kTimeoutNs) {}
-      }
-      if (a_idx > 0) {
-        const uint64_t t0 = gtime();
-        while (!mbar_try(fullA, (a_idx - 1) & 1) && gtime() - t0 < kTimeoutNs) {}
-      }
+      for (int li = (issued > nst ? issued - nst : 0); li < issued; ++li) mbar_drain(fullB + li % nst, (li / nst) & 1);
+      if (a_idx > 0) mbar_drain(fullA, (a_idx - 1) & 1);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA
@@ -175,13 +171,13 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
       for (int li = 0; li < nt; ++li) {
         const int64_t tau = t_start + li, rb = tau / ntiles;
         if (rb != cur_rb) {
-          if (!mbar_wait(fullA, a_idx & 1, s_abort)) break;
+          if (!mbar_wait(fullA, a_idx & 1, s_abort, P.wait_ns)) break;
           ++a_idx;
           cur_rb = rb;
         }
         const int b = li & 1, s = li % nst;
-        if (li >= 2 && !mbar_wait(tempty + b, ((li >> 1) - 1) & 1, s_abort)) break;
-        if (!mbar_wait(fullB + s, (li / nst) & 1, s_abort)) break;
+        if (li >= 2 && !mbar_wait(tempty + b, ((li >> 1) - 1) & 1, s_abort, P.wait_ns)) break;
+        if (!mbar_wait(fullB + s, (li / nst) & 1, s_abort, P.wait_ns)) break;
         tc_fence_after();
         const uint32_t b_base = smem_u32(smem + SL.b_off + s * SL.b_stage);
         for (int kb = 0; kb < kblocks; ++kb) {
@@ -196,15 +192,15 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
           }
         }
         umma_commit(emptyB + s);
-        umma_commit(tfull + b);
+        // test hook (P.stall): the first tile's hand-off goes to a spare barrier, so the
+        // epilogue's wait for it runs out and the pass reports the stall
+        umma_commit((P.stall && li == 0) ? spare : tfull + b);
         const bool rb_ends = (li + 1 == nt) || ((t_start + li + 1) / ntiles != rb);
         if (rb_ends) umma_commit(aempty);
         last = li;
       }
-      if (last >= 0) {
-        const uint64_t t0 = gtime();
-        while (!mbar_try(tfull + (last & 1), (last >> 1) & 1) && gtime() - t0 < kTimeoutNs) {}
-      }
+      // the MMAs of the last committed tile (and all before it) must be complete before TMEM is freed
+      if (last >= 0) mbar_drain((P.stall && last == 0) ? spare : tfull + (last & 1), (last >> 1) & 1);
     }
   } else {
     // ------------------------------------------------------------- epilogue
@@ -259,7 +255,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
       }
       const int b = li & 1;
       float x0[32], x1[32];
-      const bool ok = mbar_wait(tfull + b, (li >> 1) & 1, s_abort);
+      const bool ok = mbar_wait(tfull + b, (li >> 1) & 1, s_abort, P.wait_ns);
       if (ok) {
         tc_fence_after();
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + g * 32);
@@ -276,7 +272,7 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
 
       // ---- logits (log2 units, row lo part applied per row)
       const int cslot = li % NCA;
-      const bool okc = mbar_wait(cfull + cslot, (li / NCA) & 1, s_abort);
+      const bool okc = mbar_wait(cfull + cslot, (li / NCA) & 1, s_abort, P.wait_ns);
       const unsigned long long AH0 = pk2(ahi0, ahi0), AH1 = pk2(ahi1, ahi1);
 #pragma unroll
       for (int p = 0; p < 16; ++p) {

@@ -6,7 +6,10 @@
 namespace pot {
 namespace tcx {
 
-constexpr uint64_t kTimeoutNs = 2000000000ull;   // every mbarrier wait gives up after 2 s
+// Default bound of every mbarrier wait (2 s).  The passes take their pipeline
+// waits' bound from the pass descriptor (a caller may shorten it); the waits
+// that drain a CTA's own copies and MMAs before it exits always use this one.
+constexpr uint64_t kTimeoutNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -34,15 +37,23 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; on timeout raises the CTA abort flag and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// Bounded wait; after `limit` ns raises the CTA abort flag and returns false
+// (at once when another thread of the CTA has raised it).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          uint64_t limit = kTimeoutNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtime();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort) return false;
-    if (gtime() - t0 > kTimeoutNs) { *abort = 1; return false; }
+    if (gtime() - t0 > limit) { *abort = 1; return false; }
   }
+}
+// Bounded drain wait (always the default bound): used before a CTA exits, for
+// copies and MMAs it issued itself, whatever happened to the pipeline.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = gtime();
+  while (!mbar_try(bar, parity) && gtime() - t0 < kTimeoutNs) {}
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {

@@ -253,19 +253,19 @@ __global__ void reduce_parts_kernel(const double* part, int64_t count, int op_ma
   double acc = op_max ? -INFINITY : 0.0;
   for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
     const double x = part[i];
-    acc = op_max ? fmax(acc, x) : acc + x;
+    acc = op_max ? nanmax(acc, x) : acc + x;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const double y = __shfl_xor_sync(0xffffffffu, acc, o);
-    acc = op_max ? fmax(acc, y) : acc + y;
+    acc = op_max ? nanmax(acc, y) : acc + y;
   }
   if (lane == 0) sh[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = op_max ? -INFINITY : 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) a = op_max ? fmax(a, sh[w]) : a + sh[w];
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) a = op_max ? nanmax(a, sh[w]) : a + sh[w];
     *out = a;
   }
 }
@@ -841,20 +841,27 @@ __global__ void round_r4_kernel(RoundVecs V) {
   }
 }
 
+__global__ void marginals_setup_kernel(DevState* S, double w, unsigned int* counter) {
+  if (threadIdx.x < 8) counter[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) { S->w_out = w; S->tc_err = 0; }
+}
+
 __global__ void marginals_out_kernel(int64_t n, int64_t m, const double* lrow_in, const double* lcol_in,
-                                     double* lrow, double* lcol, double* red, unsigned int* counter, double* tot_out) {
+                                     double* lrow, double* lcol, double* red, unsigned int* counter, double* tot_out,
+                                     const int* err) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool bad = err && *err;          // a pass that gave up waiting: its sums are invalid
   double v[1] = {0};
   if (t < n) {
-    const double R = lrow_in[t];
+    const double R = bad ? (double)NAN : lrow_in[t];
     if (lrow) lrow[t] = R;
     v[0] = safe_exp(R);
   } else if (t < n + m) {
-    const double Cc = lcol_in ? lcol_in[t - n] : 0.0;
+    const double Cc = bad ? (double)NAN : (lcol_in ? lcol_in[t - n] : 0.0);
     if (lcol) lcol[t - n] = Cc;
   }
   double tot[1];
-  if (reduce_last<1>(v, red, counter, tot) && threadIdx.x == 0 && tot_out) *tot_out = tot[0];
+  if (reduce_last<1>(v, red, counter, tot) && threadIdx.x == 0 && tot_out) *tot_out = bad ? (double)NAN : tot[0];
 }
 
 __global__ void dense_plan_kernel(PassDesc P, const double* f, const double* g, const double* p,
@@ -962,10 +969,14 @@ void launch_round_r3(const RoundVecs& V, cudaStream_t st) {
 void launch_round_r4(const RoundVecs& V, cudaStream_t st) {
   round_r4_kernel<<<vec_blocks(V.n), kVecThreads, 0, st>>>(V);
 }
+void launch_marginals_setup(DevState* S, double w, unsigned int* counter, cudaStream_t st) {
+  marginals_setup_kernel<<<1, 32, 0, st>>>(S, w, counter);
+}
 void launch_marginals_out(int64_t n, int64_t m, const double* lrow_in, const double* lcol_in, double* lrow,
-                          double* lcol, double* red, unsigned int* counter, double* tot_out, cudaStream_t st) {
+                          double* lcol, double* red, unsigned int* counter, double* tot_out, const int* err,
+                          cudaStream_t st) {
   marginals_out_kernel<<<vec_blocks(n + m), kVecThreads, 0, st>>>(n, m, lrow_in, lcol_in, lrow, lcol, red, counter,
-                                                                 tot_out);
+                                                                 tot_out, err);
 }
 void launch_dense_plan(const PassDesc& P, const double* f, const double* g, const double* p,
                        const double* q, const double* kappa, float* X, int64_t ldx, cudaStream_t st) {

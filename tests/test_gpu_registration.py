@@ -71,23 +71,34 @@ def test_rigid_apply_matches_formula():
 
 
 def test_batched_registration_recovers_the_motion():
-    """Six misaligned partial clouds (half of a 3-ellipsoid target, rotated by
-    up to 0.25 rad and shifted by up to 0.08) registered at once with
-    alpha = 0.6; each must map back onto the target points it was cut from (to
-    the entropic blur), and end where the oracle's loop ends on a small pair.
-    (Seed 6 of the generator is a near-symmetric shape on which the oracle's
-    loop itself slides to another match; with alpha = 0.4 the partial matching
-    lets most sources slide.  Both are recorded findings, not GPU errors.)"""
-    seeds = [0, 1, 2, 4, 5, 7]
+    """Eight misaligned partial clouds (half of a 3-ellipsoid target, rotated
+    by up to 0.25 rad and shifted by up to 0.08; seeds 0-7) registered at once
+    with alpha = 0.6.  Each must map back onto the target points it was cut
+    from to 0.06 (the entropic blur), or else end where the FP64 oracle's own
+    loop ends: on seed 3 the oracle stops at 0.062 and on seed 6, a
+    near-symmetric shape, its loop slides to another match (0.26), so there
+    the synthetic shape limits the result, not the GPU.  (With alpha = 0.4 the
+    partial matching lets most sources slide; a recorded finding.)"""
+    seeds = list(range(8))
     pairs, truth = [], []
     for seed in seeds:
         X, Y0, Rt, tt = W.registration_3d(seed, n=256, frac=0.5, max_angle=0.25, max_shift=0.08)
         pairs.append((X, Y0))
         truth.append((Rt, tt))
     out = PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=30)
-    for seed, (Rt, tt), r in zip(seeds, truth, out):
+    recovered = 0
+    for seed, (X, Y0), (Rt, tt), r in zip(seeds, pairs, truth, out):
         err = max(np.abs(r.R - Rt).max(), np.abs(r.t - tt).max())
-        assert err < 6e-2, (seed, err)
+        if err < 6e-2:
+            recovered += 1
+            continue
+        s = 0.6 * min(X.shape[0], Y0.shape[0]) / max(X.shape[0], Y0.shape[0])
+        Ro, to, _, _ = RG.register(X, Y0, s, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=30,
+                                   tol=1e-6)
+        err_o = max(np.abs(Ro - Rt).max(), np.abs(to - tt).max())
+        assert err_o >= 5e-2, (seed, err, err_o)                  # the oracle does not recover it either
+        assert max(np.abs(r.R - Ro).max(), np.abs(r.t - to).max()) < 2e-2, (seed, err, err_o)
+    assert recovered >= 6
     # the small pair of the oracle test, on both sides
     X, Y0, Rt, tt = W.registration_3d(0, n=120, frac=0.5, max_angle=0.4, max_shift=0.08)
     s = 0.6 * min(60, 120) / 120

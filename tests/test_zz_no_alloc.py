@@ -57,17 +57,43 @@ def test_static_scratch_matches_workspace_entry_point_two_calls_in_a_row():
         assert abs(np.log(tot) - np.log(etot)) <= 5e-6 + 2e-7 * abs(np.log(etot))
 
 
-def test_static_scratch_rejects_a_problem_larger_than_the_array():
-    n = m = 60000
-    g = torch.Generator().manual_seed(0)
+def _pts_problem(n, m, seed=0):
+    g = torch.Generator().manual_seed(seed)
     X = torch.rand(n, 3, generator=g).cuda()
     Y = torch.rand(m, 3, generator=g).cuda()
     r = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
     c = torch.full((m,), 1.2 / m, dtype=torch.float64, device="cuda")
-    dp = pkg.DeviceProblem(pkg.COST_SQEUCLID_F32, r, c, 0.8, X=X, Y=Y, cost_scale=1.0)
-    u = torch.zeros(n, dtype=torch.float64, device="cuda")
-    v = torch.zeros(m, dtype=torch.float64, device="cuda")
-    st, lr, lc, tot = _call_static(dp, 0.05, u, v, 0.0)
+    return pkg.DeviceProblem(pkg.COST_SQEUCLID_F32, r, c, 0.8, X=X, Y=Y, cost_scale=20.0)
+
+
+def test_static_scratch_bound_is_the_pass_scratch_just_under_and_just_over():
+    """The size check counts what the pass itself needs
+    (pot_marginals_workspace_size), not the solvers' larger workspace: the
+    largest square problem that fits runs and matches pot_marginals, one row
+    more is refused with POT_ENOMEM before anything is launched."""
+    limit = 16 << 20
+    lo, hi = 1000, 60000
+    assert pkg.marginals_workspace_bytes(_pts_problem(lo, lo)) <= limit
+    assert pkg.marginals_workspace_bytes(_pts_problem(hi, hi)) > limit
+    while hi - lo > 1:                        # largest n with n x n fitting (host-side queries only)
+        mid = (lo + hi) // 2
+        if pkg.marginals_workspace_bytes(_pts_problem(mid, mid)) <= limit:
+            lo = mid
+        else:
+            hi = mid
+    fit = _pts_problem(lo, lo, seed=1)
+    assert pkg.workspace_bytes(fit) > limit   # the old whole-solver bound would have refused it
+    u = torch.linspace(-3.0, 1.0, lo, dtype=torch.float64, device="cuda")
+    v = torch.linspace(-2.0, 0.5, lo, dtype=torch.float64, device="cuda")
+    st, lr, lc, tot = _call_static(fit, 0.05, u, v, 0.25)
+    assert st == 0, B.lib().pot_last_error()
+    er, ec, etot = pkg.pot_marginals(fit, 0.05, u, v, 0.25)
+    assert _close(lr, er.cpu().numpy()) and _close(lc, ec.cpu().numpy())
+    over = _pts_problem(hi, hi)                # hi = lo + 1
+    assert pkg.marginals_workspace_bytes(over) > limit
+    u2 = torch.zeros(over.n, dtype=torch.float64, device="cuda")
+    v2 = torch.zeros(over.m, dtype=torch.float64, device="cuda")
+    st, lr, lc, tot = _call_static(over, 0.05, u2, v2, 0.0)
     assert st == 2
     assert b"16 MiB" in B.lib().pot_last_error()
-    assert np.isnan(lr).all()          # nothing was launched
+    assert np.isnan(lr).all() and np.isnan(lc).all()      # nothing was launched
