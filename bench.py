@@ -15,9 +15,20 @@ Algorithm 1 as printed (t mod 3) unless ``--block-rule greedy``, and the
 greedy rule's solves measured beside the headline at N = 1.  Multi-GPU runs
 are independent replicas (one instance per rank, seed = rank): weak scaling.
 
+At N = 1 the line also carries, under ``workloads``, the other measured
+configurations, each with its own warm-up, CUDA-event timing on the solve
+stream, clocks sampled over its timed region and, where one applies, its
+roofline: the 256-point dense configuration against the oracle (d1), the
+dense 4096 gamma sweep and the 16384 HBM point (d2), the 512-instance
+batched solve (d4), the learned warm start on 2000 training / 200 held-out
+instances (d5), the appendix's runtime-vs-n study (d6) and the 64-pair
+registration loop (f4).  ``--workload <name>`` runs one of them alone.
+
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm):
-each step is a bounded sample, ASPOT iterations of the oracle on the same
-generator at n = m = 4096, scaled to n = 32768 by the number of cost entries.
+each step is a bounded sample, ASPOT iterations of the unmodified oracle in
+one process per host core, each on its own seeded instance of the same
+generator at n = m = 2048, the aggregate rate scaled to n = 32768 by the
+number of cost entries.
 """
 import argparse
 import json
@@ -32,8 +43,6 @@ sys.path.insert(0, ROOT)
 
 N_FULL = 32768
 D_FULL = 128
-CPU_SAMPLE_N = 4096
-CPU_SAMPLE_ITERS = 8        # about 10 s of single-core FP64 work on the GPU host
 # ncu DRAM bytes per launch of the current kernels (null once a kernel changes):
 # dense_pass_kernel<0>, n = m = 16384 FP32 cost: 1.075126 GB read + 11.26 MB written
 DENSE_16K_TRAFFIC = 1.075126e9 + 11.25888e6
@@ -70,8 +79,12 @@ def _args():
     ap.add_argument("--ws-train", type=int, default=20000, help="warmstart: training instances")
     ap.add_argument("--ws-eval", type=int, default=1000, help="warmstart: held-out seeds")
     ap.add_argument("--ws-epochs", type=int, default=12, help="warmstart: training epochs")
-    ap.add_argument("--ws-small", type=int, default=1024,
-                    help="training instances of the small warm-start study in the headline line (0: skip)")
+    ap.add_argument("--ws-small", type=int, default=2000,
+                    help="training instances of the warm-start study in the headline line (0: skip)")
+    ap.add_argument("--ws-small-eval", type=int, default=200,
+                    help="held-out seeds of the warm-start study in the headline line")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="headline only: skip the other workloads' sub-objects (d1, d2, d4, d5, d6, f4)")
     return ap.parse_args()
 
 
@@ -162,27 +175,101 @@ def _oracle_iters_per_s(n_sample, iters, seed=0, rule="cyclic"):
     return iters / dt, dt
 
 
+def _oracle_worker(job):
+    """One pool worker: `iters` oracle iterations on its own instance (seed),
+    after one untimed warm-up iteration.  Pins numpy's threads to one core so
+    that the workers together use each host core once."""
+    n_sample, iters, seed, rule = job
+    _oracle_iters_per_s(n_sample, 1, seed=seed, rule=rule)
+    return _oracle_iters_per_s(n_sample, iters, seed=seed, rule=rule)
+
+
+class OraclePool:
+    """The oracle on every host core: one spawned process per core, each
+    running the unmodified FP64 oracle on its own seeded instance of the
+    sampled workload (independent replicas, like the GPU arm's ranks).  The
+    aggregate rate is the sum over workers of its iterations over the time
+    of its own timed region (the regions run at the same time).  'spawn'
+    keeps the workers clear of the parent's CUDA state."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+        finally:
+            for k, v in env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def rate(self, n_sample, iters, rule="cyclic"):
+        t0 = time.perf_counter()
+        outs = self.pool.map(_oracle_worker, [(n_sample, iters, 100 + k, rule) for k in range(self.cores)])
+        wall = time.perf_counter() - t0
+        return sum(r for r, _ in outs), wall, max(dt for _, dt in outs)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+CPU_POOL_N = 2048
+CPU_POOL_ITERS = 6
+
+
+def cpu_baseline(n_full, rule="cyclic"):
+    """The oracle as it stands on every host core (see OraclePool) at
+    n = m = 2048 of the 32k generator, scaled to n_full by the number of cost
+    entries; the single-core rate beside it."""
+    pool = OraclePool()
+    try:
+        rate, wall, busy = pool.rate(CPU_POOL_N, CPU_POOL_ITERS, rule)
+    finally:
+        pool.close()
+    scale = (CPU_POOL_N / n_full) ** 2
+    single, dt1 = _oracle_iters_per_s(CPU_POOL_N, 2, rule=rule)
+    return {"value": rate * scale, "unit": "it/s", "cores": pool.cores, "kind": "oracle",
+            "sample": f"{pool.cores} concurrent processes (one per host core), each running {CPU_POOL_ITERS} FP64 "
+                      f"oracle ASPOT iterations on its own seeded instance of the same generator at n=m={CPU_POOL_N} "
+                      f"({wall:.1f} s wall); aggregate rate scaled by ({CPU_POOL_N}/{n_full})^2 to n={n_full}",
+            "single_core_value": single * scale,
+            "time_to_eps_note": ("a full oracle solve of this generator is out of reach at bench time: at n=512 it "
+                                 "has not reached eps~ after 3000 iterations (82 s on one core); the GPU's "
+                                 "time to eps at 32k divided by this rate's iteration time is the labelled "
+                                 "extrapolation in time_to_eps_extrapolated_s")}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    scale = (CPU_SAMPLE_N / args.n) ** 2
-    for _ in range(args.warmup):
-        _oracle_iters_per_s(CPU_SAMPLE_N, 1, rule=args.block_rule)
-    rates, secs = [], 0.0
-    for _ in range(args.steps):
-        r, dt = _oracle_iters_per_s(CPU_SAMPLE_N, 2, rule=args.block_rule)
-        rates.append(r * scale)
-        secs += dt
+    scale = (CPU_POOL_N / args.n) ** 2
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.rate(CPU_POOL_N, 1, args.block_rule)
+        rates, secs = [], 0.0
+        for _ in range(args.steps):
+            r, wall, _ = pool.rate(CPU_POOL_N, 2, args.block_rule)
+            rates.append(r * scale)
+            secs += wall
+    finally:
+        pool.close()
     value = statistics.mean(rates)
-    sample = (f"2 FP64 oracle ASPOT iterations per step at n=m={CPU_SAMPLE_N} (same generator, seed 0), "
-              f"rate scaled by ({CPU_SAMPLE_N}/{args.n})^2 to n={args.n}")
+    sample = (f"{pool.cores} concurrent processes (one per host core), 2 FP64 oracle ASPOT iterations each per step, "
+              f"each on its own seeded instance of the same generator at n=m={CPU_POOL_N}; aggregate rate scaled by "
+              f"({CPU_POOL_N}/{args.n})^2 to n={args.n}")
     line = {"metric": "ASPOT iterations/s at n=32k (time-to-epsilon alongside)", "value": value, "unit": "it/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": _workload_desc(args.n),
                        "parallelism": "single (rank 0 of the launch runs the oracle)", "block_rule": args.block_rule},
-            "cpu_baseline": {"value": value, "unit": "it/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "it/s", "cores": pool.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -339,6 +426,7 @@ def run_ours(args, rank, world, local_rank):
 
     burst, sustained, hbm, src = _peaks()
     n = args.n
+    kernel_name = pkg.pass_kernel(dp, flags)          # the kernel the hot loop's passes ran
     flop_per_pass = 2.0 * n * n * D_FULL
     avg_pass_ms = pass_ms / max(pass_n, 1)
     achieved = flop_per_pass / (avg_pass_ms * 1e-3) / 1e12 if pass_n else None
@@ -361,7 +449,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h, "time_to_eps_ms": e2e_ms / args.steps},
         "gpu_launches": launches,
         "clocks": clocks,
-        "roofline": {"kernel": "tc_pass_kernel (tcgen05 on-the-fly log-sum-exp pass)", "bound": "tensor",
+        "roofline": {"kernel": kernel_name, "bound": "tensor",
                      "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                      "frac": (achieved / sustained) if achieved else None,
                      "traffic": TC2_32K_TRAFFIC if n == N_FULL else None,
@@ -372,19 +460,28 @@ def run_ours(args, rank, world, local_rank):
     if greedy is not None:
         greedy["time_to_eps_vs_cyclic"] = greedy["time_to_eps_ms"] / (ms / args.steps)
         line["greedy_rule"] = greedy
-    if world == 1 and args.ws_small > 0:
-        # learned warm start vs cold start, small configuration (the full one: --workload warmstart)
-        line["warm_vs_cold"] = warm_start_study(args.ws_small, 64, epochs=max(1, 100 * 1024 // args.ws_small),
-                                                device=dev)
-        line["warm_vs_cold"]["note"] = ("small study run inside the headline bench; --workload warmstart runs "
-                                        "the 20000-instance / 1000-seed configuration")
+    if world == 1 and not args.no_workloads:
+        # the other measured workloads, each timed the same way (warm-up, CUDA events on the solve stream,
+        # clocks sampled over its own timed region); --workload <name> runs each one alone at full length
+        wl = {}
+        wl["d1_small_dense_256"] = small_study(args, quick=True, dev=dev)
+        wl["d2_dense_4096"] = dense_study(args, quick=True, dev=dev)
+        wl["d4_batch_3d_512"] = batched_study(args, quick=True, dev=dev)
+        if args.ws_small > 0:
+            ws = warm_start_study(args.ws_small, args.ws_small_eval, epochs=max(1, 80000 // args.ws_small),
+                                  device=dev, greedy=not args.no_greedy)
+            ws["note"] = (f"{args.ws_small} training instances / {args.ws_small_eval} held-out seeds inside the "
+                          f"headline bench; --workload warmstart runs the 20000 / 1000 configuration")
+            wl["d5_warm_start"] = ws
+        wl["d6_scaling_e4"] = scaling_study(args, dev=dev)
+        wl["f4_registration_64"] = registration_study(args, quick=True, dev=dev)
+        line["workloads"] = wl
     if world == 1 and not args.no_cpu_baseline:
-        rate, dt = _oracle_iters_per_s(CPU_SAMPLE_N, CPU_SAMPLE_ITERS, rule=args.block_rule)
-        line["cpu_baseline"] = {"value": rate * (CPU_SAMPLE_N / n) ** 2, "unit": "it/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"{CPU_SAMPLE_ITERS} FP64 oracle ASPOT iterations at n=m={CPU_SAMPLE_N} "
-                                          f"(same generator), "
-                                          f"{dt:.1f} s, rate scaled by ({CPU_SAMPLE_N}/{n})^2"}
+        cb = cpu_baseline(n, rule=args.block_rule)
+        cb["time_to_eps_extrapolated_s"] = (iters / (args.steps * world)) / cb["single_core_value"]
+        cb["time_to_eps_extrapolated_note"] = ("labelled extrapolation: the GPU solve's iteration count times the "
+                                               "oracle's single-core time per iteration at this n")
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
 
 
@@ -423,66 +520,138 @@ def run_pass_only(args):
                       "tflops": 2.0 * args.n * args.n * D_FULL / (ms * 1e-3) / 1e12}), flush=True)
 
 
-def run_dense(args):
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def _timed(stream, fn, warmup, steps, min_s=0.6, flush=None, gpu_index=0):
+    """`warmup` untimed calls of fn, then at least `steps` timed calls, more
+    until `min_s` seconds have passed (so that the clock sampler sees the
+    region).  CUDA events on `stream` around each call; with `flush`, a
+    buffer larger than L2 is written before each timed call.  Returns (last
+    result, list of ms per call, clocks over the timed calls)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        clk = Clocks(gpu_index)
+        clk.start()
+        ev, out, t0 = [], None, time.perf_counter()
+        while len(ev) < steps or time.perf_counter() - t0 < min_s:
+            if flush is not None:
+                flush.zero_()
+            e0, e1 = _ev(), _ev()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            ev.append((e0, e1))
+            if len(ev) >= steps:
+                e1.synchronize()
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+    return out, [a.elapsed_time(b) for a, b in ev], clocks
+
+
+_FLUSH = {}
+
+
+def _flush_buf(dev):
+    import torch
+    if dev not in _FLUSH:
+        _FLUSH[dev] = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    return _FLUSH[dev]
+
+
+def l2_copy_gbs(dev="cuda"):
+    """Measured L2-resident copy bandwidth: b.copy_(a) on two 32 MiB buffers
+    (both stay in the 129 MB L2), read + write bytes over CUDA-event time,
+    best of 5 rounds of 50 copies.  The denominator of the passes whose
+    operand sits in L2 (the 64 MiB cost of the 4096-point dense workload)."""
+    import torch
+    a = torch.empty(32 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    b = torch.empty_like(a)
+    a.fill_(1)
+    best = 0.0
+    for _ in range(5):
+        b.copy_(a)
+        e0, e1 = _ev(), _ev()
+        e0.record()
+        for _ in range(50):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 50 * 2 * a.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
+def dense_study(args, quick=False, dev="cuda"):
     """Dense FP32 cost, n = m = 4096 (and a 16384 point, 1 GiB of cost, for the
     HBM claim): ASPOT to eps at gamma in {0.1, 0.03, 0.01}; achieved bytes of
-    the CUDA-core pass = 4 n m per launch over its CUDA-event time."""
+    the CUDA-core pass = 4 n m per launch over its CUDA-event time (in-loop
+    passes, POT_FLAG_PROFILE), against the measured HBM copy bandwidth (1 GiB
+    cost) or the measured L2 copy bandwidth (64 MiB cost, L2-resident during
+    the solve).  Per iteration: the algorithmic bytes of three full passes
+    (4 n m each) over the iteration's time."""
     import torch
     import paper_2601_17196_gb300 as pkg
     import pot_workloads as W
     burst, sustained, hbm, src = _peaks()
-    out = {"workload": "dense_4096", "rows": []}
-    stream = torch.cuda.Stream()
+    l2 = l2_copy_gbs(dev)
+    out = {"workload": "dense_4096: 64-D X~N(0,I), Y 90% N(0,I) + 10% N(4*1,I), FP32 cost / max, masses 1.0 / 1.3, "
+                       "s=0.9, eps=1e-2; plus n=16384 (1 GiB cost) for the HBM point",
+           "hbm_peak_gbs": hbm, "hbm_peak_source": src, "l2_copy_gbs_measured": l2, "rows": []}
+    stream = torch.cuda.Stream(device=dev)
+    warm, steps = (3, 5) if quick else (args.warmup, args.steps)
+    flush = _flush_buf(dev)
     for n, gammas in ((4096, (0.1, 0.03, 0.01)), (16384, (0.03,))):
         for gam in gammas:
             pb = W.dense_4096(0, n=n, gamma=gam)
-            dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+            dp = pkg.DeviceProblem.from_workload(pb, device=dev)
+            res, ms, clocks = _timed(stream, lambda: pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter),
+                                     warm, steps, flush=flush)
+            t = sum(ms) / len(ms)
+            it = res.iters
+            # one more solve with every main-loop pass timed by CUDA events (kept out of the timed solves)
             with torch.cuda.stream(stream):
-                for _ in range(args.warmup):
-                    pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_PROFILE)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                res = [pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_PROFILE)
-                       for _ in range(args.steps)]
-                e1.record(stream)
-                torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
-            it = sum(r.iters for r in res) / args.steps
-            pms = sum(r.pass_ms for r in res) / max(sum(r.pass_launches for r in res), 1)
+                prof = pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_PROFILE)
+            pms = prof.pass_ms / max(prof.pass_launches, 1)
             gbs = 4.0 * n * n / (pms * 1e-3) / 1e9
-            row = {"n": n, "gamma": gam, "iters": it, "time_to_eps_ms": ms, "it_per_s": it / (ms / 1e3),
-                   "pass_ms": pms, "pass_GBps": gbs, "hbm_frac": gbs / hbm, "hbm_peak": hbm,
-                   "l2_note": "64 MiB cost fits in L2" if n == 4096 else "1 GiB cost > L2",
-                   "objective": res[-1].objective, "converged": all(r.status == 0 for r in res)}
-            if not args.no_greedy:
-                with torch.cuda.stream(stream):
-                    for _ in range(args.warmup):
-                        pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, block_rule=pkg.BLOCK_GREEDY)
-                    torch.cuda.synchronize()
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    rg = [pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter, block_rule=pkg.BLOCK_GREEDY)
-                          for _ in range(args.steps)]
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                gms = e0.elapsed_time(e1) / args.steps
-                git = sum(r.iters for r in rg) / args.steps
-                row["greedy_rule"] = {"iters": git, "time_to_eps_ms": gms, "it_per_s": git / (gms / 1e3),
-                                      "objective": rg[-1].objective, "converged": all(r.status == 0 for r in rg),
-                                      "time_to_eps_vs_cyclic": gms / ms}
+            peak = hbm if n == 16384 else l2
+            iter_us = 1e3 * t / it
+            row = {"n": n, "gamma": gam, "iters": it, "time_to_eps_ms": t, "it_per_s": it / (t / 1e3),
+                   "kernel": pkg.pass_kernel(dp, pkg.FLAG_PROFILE), "clocks": clocks,
+                   "pass_ms": pms, "passes_per_iter": prof.pass_launches / max(prof.iters, 1),
+                   "launches_per_iter": res.kernel_launches / max(it, 1),
+                   "roofline": {"bound": "hbm" if n == 16384 else "l2", "achieved": gbs, "peak": peak,
+                                "unit": "GB/s", "frac": gbs / peak,
+                                "peak_source": (f"{src} HBM copy" if n == 16384 else
+                                                "measured L2-resident copy (64 MiB cost stays in L2)"),
+                                "bytes_per_launch": 4.0 * n * n},
+                   "per_iteration": {"us": iter_us, "algorithmic_bytes_3_passes": 12.0 * n * n,
+                                     "achieved_GBps": 12.0 * n * n / (iter_us * 1e-6) / 1e9,
+                                     "frac_of_peak": 12.0 * n * n / (iter_us * 1e-6) / 1e9 / peak},
+                   "objective": res.objective, "converged": res.status == 0}
             if n == 16384:
                 # DRAM bytes of one two-sided dense_pass_kernel launch at this size, from one ncu
                 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-                row["traffic_bytes_per_launch"] = DENSE_16K_TRAFFIC
-                row["algorithmic_bytes_per_launch"] = 4.0 * n * n
+                row["roofline"]["traffic"] = DENSE_16K_TRAFFIC
+            if not args.no_greedy:
+                rg, gms, gclk = _timed(stream, lambda: pkg.aspot_solve(dp, gam, pb.eps, max_iter=args.max_iter,
+                                                                        block_rule=pkg.BLOCK_GREEDY),
+                                       warm, steps, flush=flush)
+                gt = sum(gms) / len(gms)
+                row["greedy_rule"] = {"iters": rg.iters, "time_to_eps_ms": gt, "it_per_s": rg.iters / (gt / 1e3),
+                                      "objective": rg.objective, "converged": rg.status == 0,
+                                      "time_to_eps_vs_cyclic": gt / t, "clocks": gclk}
             out["rows"].append(row)
             del dp
             torch.cuda.empty_cache()
-    print(json.dumps(out), flush=True)
+    return out
 
 
-def run_scaling(args):
+def scaling_study(args, dev="cuda"):
     """Runtime of 1500 fixed ASPOT iterations vs n (appendix scalability study):
     masses 5 / 3, s = 0.6, gamma = 1e-3, 2-D points, dense FP32 cost; the
     log-log slope is compared with the paper's ~2.27 (its hardware unstated)."""
@@ -492,149 +661,138 @@ def run_scaling(args):
     import pot_workloads as W
     ns = [200, 300, 500, 1000, 1500, 2000, 2500, 3000, 3500, 4000]
     rows = []
-    stream = torch.cuda.Stream()
+    stream = torch.cuda.Stream(device=dev)
+    clk = Clocks(0)
+    clk.start()
     for n in ns:
         pb = W.scaling_e4(0, n=n)
-        dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
-        with torch.cuda.stream(stream):
-            pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=1500, flags=pkg.FLAG_NO_STOP)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=1500, flags=pkg.FLAG_NO_STOP)
-            e1.record(stream)
-            torch.cuda.synchronize()
-        rows.append({"n": n, "ms": e0.elapsed_time(e1), "iters": r.iters, "E": r.err_final})
+        dp = pkg.DeviceProblem.from_workload(pb, device=dev)
+        r, ms, _ = _timed(stream, lambda: pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=1500,
+                                                           flags=pkg.FLAG_NO_STOP),
+                          1, 1, min_s=0.0)
+        rows.append({"n": n, "ms": ms[0], "us_per_iter": 1e3 * ms[0] / 1500, "iters": r.iters,
+                     "launches_per_iter": r.kernel_launches / 1500.0, "E": r.err_final})
+    clocks = clk.stop()
     x = np.log([q["n"] for q in rows])
     y = np.log([q["ms"] for q in rows])
     slope = float(np.polyfit(x, y, 1)[0])
     big = [q for q in rows if q["n"] >= 1500]
     slope_big = float(np.polyfit(np.log([q["n"] for q in big]), np.log([q["ms"] for q in big]), 1)[0])
-    print(json.dumps({"workload": "scaling_e4", "rows": rows, "loglog_slope": slope,
-                      "loglog_slope_n_ge_1500": slope_big, "paper_slope": 2.27}), flush=True)
+    return {"workload": "scaling_e4: 2-D U[0,1]^2 points, masses 5/3, s=0.6, gamma=1e-3, 1500 fixed iterations",
+            "rows": rows, "loglog_slope": slope, "loglog_slope_n_ge_1500": slope_big, "paper_slope": 2.27,
+            "paper_slope_note": "the paper's slope is CPU-side context (hardware unstated), not a target",
+            "clocks": clocks}
 
 
-def run_batched(args):
+def batched_study(args, quick=False, dev="cuda"):
     """512 independent 3-D instances (n_k, m_k ~ U{64..2048}), solved in
-    lockstep by aspot_solve_batched to each one's own threshold."""
+    lockstep by aspot_solve_batched to each one's own threshold: default
+    tiles, the autotuner (first call times the candidates, later calls hit
+    the cache) and the greedy block rule."""
     import torch
     import paper_2601_17196_gb300 as pkg
     import pot_workloads as W
     insts = W.batch_3d(seed=0, count=512)
-    probs = [pkg.DeviceProblem.from_workload(pb, device="cuda") for pb in insts]
+    probs = [pkg.DeviceProblem.from_workload(pb, device=dev) for pb in insts]
     elems = sum(p.n * p.m for p in probs)
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            res = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    stream = torch.cuda.Stream(device=dev)
+    warm, steps = (2, 3) if quick else (args.warmup, args.steps)
+    flush = _flush_buf(dev)
+    res, ms, clocks = _timed(stream, lambda: pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter),
+                             warm, steps, flush=flush)
+    t = sum(ms) / len(ms)
     its = [r.iters for r in res]
-    out = {"workload": "batch_3d", "instances": len(probs), "cost_entries": elems,
-           "ms_all_to_eps": ms, "instances_per_s": len(probs) / (ms / 1e3),
+    out = {"workload": "batch_3d: 512 instances, n_k,m_k~U{64..2048}, U[0,1]^3 FP32 points, |r|=1, "
+                       "|c|~U[1,1.5], s_k~U[0.5,0.95], gamma=0.05, eps=1e-3",
+           "instances": len(probs), "cost_entries": elems,
+           "ms_all_to_eps": t, "instances_per_s": len(probs) / (t / 1e3),
            "iters_max": max(its), "iters_mean": sum(its) / len(its),
+           "launches_per_iter": res[0].kernel_launches / max(max(its), 1),
            "converged": sum(r.status == 0 for r in res), "kernel_launches": res[0].kernel_launches,
-           "tile": [res[0].tile_rows, res[0].tile_cols]}
-    # the autotuner: first call times the candidate tile shapes, later calls hit the cache
+           "tile": [res[0].tile_rows, res[0].tile_cols], "clocks": clocks,
+           "entry_sweeps_per_s": elems * max(its) / (t / 1e3)}
     pkg.autotune_clear()
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
         first = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter, flags=pkg.FLAG_AUTOTUNE)
         torch.cuda.synchronize()
         first_ms = (time.perf_counter() - t0) * 1e3
-        for _ in range(args.warmup):
-            pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter, flags=pkg.FLAG_AUTOTUNE)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            rt = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter, flags=pkg.FLAG_AUTOTUNE)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    tms = e0.elapsed_time(e1) / args.steps
+    rt, tms, tclk = _timed(stream, lambda: pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter,
+                                                                    flags=pkg.FLAG_AUTOTUNE),
+                           warm, steps, flush=flush)
+    tt = sum(tms) / len(tms)
     out["autotuned"] = {"tile": [rt[0].tile_rows, rt[0].tile_cols], "tune_ms": first[0].tune_ms,
-                        "first_call_ms": first_ms, "ms_all_to_eps": tms,
-                        "instances_per_s": len(probs) / (tms / 1e3), "vs_default_tile": tms / ms,
-                        "converged": sum(r.status == 0 for r in rt)}
+                        "first_call_ms": first_ms, "ms_all_to_eps": tt,
+                        "instances_per_s": len(probs) / (tt / 1e3), "vs_default_tile": tt / t,
+                        "converged": sum(r.status == 0 for r in rt), "clocks": tclk}
     if not args.no_greedy:
-        # greedy block rule with the autotuned tiles
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter, flags=pkg.FLAG_AUTOTUNE,
-                                        block_rule=pkg.BLOCK_GREEDY)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                rg = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter, flags=pkg.FLAG_AUTOTUNE,
-                                             block_rule=pkg.BLOCK_GREEDY)
-            e1.record(stream)
-            torch.cuda.synchronize()
-        gms = e0.elapsed_time(e1) / args.steps
+        rg, gms, gclk = _timed(stream, lambda: pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=args.max_iter,
+                                                                        flags=pkg.FLAG_AUTOTUNE,
+                                                                        block_rule=pkg.BLOCK_GREEDY),
+                               warm, steps, flush=flush)
+        gt = sum(gms) / len(gms)
         gits = [r.iters for r in rg]
-        out["greedy_rule_autotuned"] = {"ms_all_to_eps": gms, "instances_per_s": len(probs) / (gms / 1e3),
+        out["greedy_rule_autotuned"] = {"ms_all_to_eps": gt, "instances_per_s": len(probs) / (gt / 1e3),
                                         "iters_max": max(gits), "iters_mean": sum(gits) / len(gits),
-                                        "converged": sum(r.status == 0 for r in rg), "vs_default": gms / ms}
-    print(json.dumps(out), flush=True)
+                                        "converged": sum(r.status == 0 for r in rg), "vs_default": gt / t,
+                                        "clocks": gclk}
+    return out
 
 
-def run_small(args):
+def small_study(args, quick=False, dev="cuda"):
     """The 256-point configuration (X ~ U[0,1]^2, Y ~ N((.5,.5), 0.1^2 I),
     masses 1.0 / 1.2, s = 0.8, gamma = 0.05, eps = 1e-3, dense FP32 cost):
     ASPOT and the feasible Sinkhorn baseline to their thresholds, and the
     tuned-gamma Sinkhorn of Theorem 2 for p in {1, 1.5, 2, 3, 4} (gamma =
-    (2 eps / (49 H_min))^(1/p), eps' = H_min gamma^p), iterations, time to
-    epsilon and <C, X>; the FP64 oracle's ASPOT on the same instance beside it."""
+    (2 eps / (49 H_min))^(1/p), eps' = H_min gamma^p; p = 1 only outside
+    `quick`, it takes ~1e5 iterations), iterations, time to epsilon and
+    <C, X>; the FP64 oracle's ASPOT on the same instance beside it."""
     import torch
     import paper_2601_17196_gb300 as pkg
     import pot_workloads as W
     from oracle import pot as O
     pb = W.small_dense(0)
-    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
-    stream = torch.cuda.Stream()
+    dp = pkg.DeviceProblem.from_workload(pb, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    warm, steps = (3, 10) if quick else (args.warmup, args.steps)
     rows = []
-
-    def timed(fn):
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                fn()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                r = fn()
-            e1.record(stream)
-            torch.cuda.synchronize()
-        return r, e0.elapsed_time(e1) / args.steps
-
-    r, ms = timed(lambda: pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter))
-    rows.append({"solver": "aspot", "gamma": r.gamma, "iters": r.iters, "time_to_eps_ms": ms,
-                 "objective": r.objective, "converged": r.status == 0})
-    r, ms = timed(lambda: pkg.sinkhorn_pot_solve(dp, pb.gamma, pb.eps, max_iter=200000))
-    rows.append({"solver": "sinkhorn", "gamma": r.gamma, "iters": r.iters, "time_to_eps_ms": ms,
-                 "objective": r.objective, "converged": r.status == 0})
-    for p in (1.0, 1.5, 2.0, 3.0, 4.0):
-        r, ms = timed(lambda: pkg.sinkhorn_pot_solve(dp, 0.0, pb.eps, max_iter=200000, p_tune=p))
+    r, ms, clocks = _timed(stream, lambda: pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter),
+                           warm, steps)
+    t = sum(ms) / len(ms)
+    with torch.cuda.stream(stream):        # pass times from one extra, profiled solve
+        prof = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_PROFILE)
+    pms = prof.pass_ms / max(prof.pass_launches, 1)
+    aspot = {"solver": "aspot", "gamma": r.gamma, "iters": r.iters, "time_to_eps_ms": t, "objective": r.objective,
+             "converged": r.status == 0, "us_per_iter": 1e3 * t / r.iters, "clocks": clocks,
+             "kernel": pkg.pass_kernel(dp, pkg.FLAG_PROFILE), "pass_us": 1e3 * pms,
+             "launches_per_iter": r.kernel_launches / r.iters,
+             "roofline": {"bound": "latency", "note": "0.25 MiB cost: a pass is a few microseconds of launch and "
+                                                     "reduction latency; the HBM roofline of 3 passes (0.75 MiB) "
+                                                     "is 0.1 us",
+                          "achieved_pass_GBps": 4.0 * 256 * 256 / (pms * 1e-3) / 1e9}}
+    rows.append(aspot)
+    r, ms, clocks = _timed(stream, lambda: pkg.sinkhorn_pot_solve(dp, pb.gamma, pb.eps, max_iter=200000),
+                           warm, steps)
+    t = sum(ms) / len(ms)
+    rows.append({"solver": "sinkhorn", "gamma": r.gamma, "iters": r.iters, "time_to_eps_ms": t,
+                 "objective": r.objective, "converged": r.status == 0, "clocks": clocks})
+    for p in ((1.5, 2.0, 3.0, 4.0) if quick else (1.0, 1.5, 2.0, 3.0, 4.0)):
+        r, ms, clocks = _timed(stream, lambda: pkg.sinkhorn_pot_solve(dp, 0.0, pb.eps, max_iter=200000, p_tune=p),
+                               1, 1, min_s=0.0)
         rows.append({"solver": f"tuned sinkhorn p={p}", "gamma": r.gamma, "eps_prime": r.eps_stop, "iters": r.iters,
-                     "time_to_eps_ms": ms, "objective": r.objective, "converged": r.status == 0})
+                     "time_to_eps_ms": ms[0], "objective": r.objective, "converged": r.status == 0})
     t0 = time.time()
     C = O.sqeuclid_cost(pb.X, pb.Y, pb.cost_scale) if pb.C is None else pb.C.astype("float64")
     ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma)
     cpu_ms = (time.time() - t0) * 1e3
-    print(json.dumps({"workload": "small_dense n=m=256 gamma=0.05 eps=1e-3 (masses 1.0/1.2, s=0.8)", "rows": rows,
-                      "oracle_aspot": {"iters": ora.iters, "ms": cpu_ms, "objective": ora.objective, "cores": 1,
-                                       "kind": "oracle"},
-                      "objective_rel_diff_gpu_vs_oracle": abs(rows[0]["objective"] - ora.objective) / ora.objective}),
-          flush=True)
+    return {"workload": "small_dense n=m=256 gamma=0.05 eps=1e-3 (masses 1.0/1.2, s=0.8)", "rows": rows,
+            "oracle_aspot": {"iters": ora.iters, "ms": cpu_ms, "objective": ora.objective, "cores": 1,
+                             "kind": "oracle"},
+            "objective_rel_diff_gpu_vs_oracle": abs(aspot["objective"] - ora.objective) / ora.objective,
+            "time_to_eps_gpu_over_oracle": aspot["time_to_eps_ms"] / cpu_ms}
 
 
-def run_registration(args):
+def registration_study(args, quick=False, dev="cuda"):
     """Batched rigid registration (appendix, point cloud registration) of 64
     synthetic partial clouds: target n = 1024 points on three ellipsoid
     surfaces, source = half of it moved by up to 0.25 rad and 0.08, alpha =
@@ -653,33 +811,38 @@ def run_registration(args):
         truth.append((Rt, tt))
     PR.register_batched(pairs[:2], alpha=0.6, max_reg=2, autotune=False)          # warm-up (build, caches)
     torch.cuda.synchronize()
+    clk = Clocks(0)
+    clk.start()
     t0 = time.time()
     out = PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=40,
                               autotune=False)
     torch.cuda.synchronize()
     wall = time.time() - t0
+    clocks = clk.stop()
     err = np.array([max(np.abs(r.R - Rt).max(), np.abs(r.t - tt).max()) for r, (Rt, tt) in zip(out, truth)])
     regs = np.array([r.registrations for r in out])
     inner = np.array([r.inner_iterations for r in out])
-    # autotuned tiles: the first run times each new set of active pairs, the second hits the cache
-    import paper_2601_17196_gb300 as pkg
-    pkg.autotune_clear()
-    tune = {}
-    for leg in ("first_call_s", "wall_s"):
-        torch.cuda.synchronize()
-        t0 = time.time()
-        PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=40,
-                            autotune=True)
-        torch.cuda.synchronize()
-        tune[leg] = time.time() - t0
-    tune["vs_default_tile"] = tune["wall_s"] / wall
-    print(json.dumps({"workload": "registration: 64 pairs, target n=1024 (3 ellipsoid surfaces), source = half, "
-                                  "<=0.25 rad, <=0.08 shift, alpha=0.6, gamma 0.02*0.83^k >= 0.002, eps=1e-3",
-                      "wall_s": wall, "autotuned": tune, "pairs": K, "registrations_mean": float(regs.mean()),
-                      "registrations_max": int(regs.max()), "aspot_iters_per_registration": float(inner.sum() / regs.sum()),
-                      "converged_pairs": int(sum(r.converged for r in out)),
-                      "motion_error_median": float(np.median(err)), "motion_error_p90": float(np.quantile(err, 0.9)),
-                      "pairs_within_0.06": int((err < 0.06).sum())}), flush=True)
+    res = {"workload": "registration: 64 pairs, target n=1024 (3 ellipsoid surfaces), source = half, "
+                       "<=0.25 rad, <=0.08 shift, alpha=0.6, gamma 0.02*0.83^k >= 0.002, eps=1e-3",
+           "wall_s": wall, "pairs": K, "registrations_mean": float(regs.mean()),
+           "registrations_max": int(regs.max()), "aspot_iters_per_registration": float(inner.sum() / regs.sum()),
+           "converged_pairs": int(sum(r.converged for r in out)),
+           "motion_error_median": float(np.median(err)), "motion_error_p90": float(np.quantile(err, 0.9)),
+           "pairs_within_0.06": int((err < 0.06).sum()), "clocks": clocks}
+    if not quick:
+        import paper_2601_17196_gb300 as pkg
+        pkg.autotune_clear()
+        tune = {}
+        for leg in ("first_call_s", "wall_s"):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            PR.register_batched(pairs, alpha=0.6, gamma0=0.02, anneal=0.83, gamma_min=0.002, eps=1e-3, max_reg=40,
+                                autotune=True)
+            torch.cuda.synchronize()
+            tune[leg] = time.time() - t0
+        tune["vs_default_tile"] = tune["wall_s"] / wall
+        res["autotuned"] = tune
+    return res
 
 
 def run_ws_train(args):
@@ -761,6 +924,8 @@ def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batc
         steps = net.step
         del fs
         cold_it, warm_it, cold_ms, warm_ms, used, gap, g_rows = [], [], [], [], [], [], []
+        clk = Clocks(0)
+        clk.start()
         for k in range(n_eval):
             dp = pkg.DeviceProblem.from_workload(W.mix_2d(k), device=device, kind=pkg.COST_SQEUCLID_F32)
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -785,6 +950,7 @@ def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batc
                 h1.record(stream)
                 torch.cuda.synchronize()
                 g_rows.append((gc.iters, gw.iters, g0.elapsed_time(g1), h0.elapsed_time(h1), gw.warm_used))
+        clocks = clk.stop()
     ci, wi = np.array(cold_it, dtype=float), np.array(warm_it, dtype=float)
     cm, wm = np.array(cold_ms), np.array(warm_ms)
     greedy_out = None
@@ -806,7 +972,8 @@ def warm_start_study(n_train: int, n_eval: int, epochs: int, mode: int = 1, batc
             "cold_iters_mean": float(ci.mean()), "warm_iters_mean": float(wi.mean()),
             "iters_ratio_warm_over_cold": float(wi.mean() / ci.mean()),
             "median_per_seed_iters_ratio": float(np.median(wi / ci)),
-            "fallback_fraction": float(1.0 - np.mean(used)), "max_objective_gap": float(max(gap))}
+            "fallback_fraction": float(1.0 - np.mean(used)), "max_objective_gap": float(max(gap)),
+            "clocks": clocks}
 
 
 def run_warmstart(args):
@@ -823,10 +990,10 @@ def main():
         run_warmstart(args)
         return
     if args.workload == "small_dense":
-        run_small(args)
+        print(json.dumps(small_study(args)), flush=True)
         return
     if args.workload == "registration":
-        run_registration(args)
+        print(json.dumps(registration_study(args)), flush=True)
         return
     if args.workload == "ws_train":
         run_ws_train(args)
@@ -835,13 +1002,13 @@ def main():
         run_pass_only(args)
         return
     if args.workload == "batch_3d":
-        run_batched(args)
+        print(json.dumps(batched_study(args)), flush=True)
         return
     if args.workload == "dense_4096":
-        run_dense(args)
+        print(json.dumps(dense_study(args)), flush=True)
         return
     if args.workload == "scaling_e4":
-        run_scaling(args)
+        print(json.dumps(scaling_study(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -289,6 +289,13 @@ POT_API pot_status aspot_state_export(const pot_problem* prob, const pot_params*
  * step at z^t).  Keeps the last 4096 iterations. */
 POT_API pot_status pot_trace(void* workspace, int32_t iters, double* out /* host */, void* stream);
 
+/* Name of the CUDA kernel that runs the O(nm) passes of a solver's main loop
+ * for this problem and these flags: "tc2_pass_kernel" (tcgen05, d = 64 or
+ * 128), "tc_pass_kernel" (tcgen05, other d), "dense_pass_kernel" (dense FP32
+ * cost, 16-byte aligned rows) or "pass_simt_kernel" (every other case);
+ * "" for an invalid problem.  A static string; host only, launches nothing. */
+POT_API const char* pot_pass_kernel(const pot_problem* prob, int32_t flags);
+
 /* Thread-local message of the last failure ("" if none). */
 POT_API const char* pot_last_error(void);
 

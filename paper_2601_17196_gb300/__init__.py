@@ -24,6 +24,7 @@ from .binding import (  # noqa: F401
     pot_plan_dense,
     workspace_bytes,
     marginals_workspace_bytes,
+    pass_kernel,
     lib,
     exported_symbols,
     FLAG_STOP_RAW_EPS,

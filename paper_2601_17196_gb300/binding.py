@@ -43,7 +43,7 @@ EXPORTED = ["pot_workspace_size", "aspot_solve", "sinkhorn_pot_solve", "pot_roun
             "pot_ws_train_step", "pot_ws_warm_workspace_size", "pot_ws_warm_start", "pot_rigid_workspace_size",
             "pot_rigid_fit", "pot_rigid_apply", "pot_trace_batched", "pot_autotune_set", "pot_autotune_lookup",
             "pot_autotune_clear",
-            "pot_autotune_save", "pot_autotune_load", "pot_last_error"]
+            "pot_autotune_save", "pot_autotune_load", "pot_pass_kernel", "pot_last_error"]
 
 
 class PotError(RuntimeError):
@@ -145,9 +145,11 @@ def lib() -> ct.CDLL:
         L.pot_autotune_clear.argtypes = []
         L.pot_autotune_save.argtypes = [ct.c_char_p]
         L.pot_autotune_load.argtypes = [ct.c_char_p]
-        L.pot_last_error.restype = ct.c_char_p
-        for name in EXPORTED[:-1]:
+        L.pot_pass_kernel.argtypes = [P, i32]
+        for name in EXPORTED[:-2]:
             getattr(L, name).restype = ct.c_int
+        L.pot_pass_kernel.restype = ct.c_char_p
+        L.pot_last_error.restype = ct.c_char_p
         _lib_handle = L
     return _lib_handle
 
@@ -305,6 +307,11 @@ def workspace_bytes(prob: DeviceProblem, flags: int = 0) -> int:
     pa.flags = flags
     _check(lib().pot_workspace_size(ct.byref(prob.struct()), ct.byref(pa), ct.byref(b)))
     return int(b.value)
+
+
+def pass_kernel(prob: DeviceProblem, flags: int = 0) -> str:
+    """Name of the kernel the solvers' main-loop passes run for this problem."""
+    return lib().pot_pass_kernel(ct.byref(prob.struct()), int(flags)).decode()
 
 
 def marginals_workspace_bytes(prob: DeviceProblem) -> int:

@@ -984,6 +984,14 @@ pot_status pot_plan_dense(const pot_problem* prob, const pot_plan* plan, double 
   return POT_OK;
 }
 
+const char* pot_pass_kernel(const pot_problem* prob, int32_t flags) {
+  if (check_problem(prob) != POT_OK) return "";
+  const Layout L = make_layout(prob, flags);
+  if (L.use_tc) return L.tl.v3 ? "tc3_pass_kernel" : (L.tl.v2 ? "tc2_pass_kernel" : "tc_pass_kernel");
+  if (prob->kind == POT_COST_DENSE_F32 && L.sl.dense_fast) return "dense_pass_kernel";
+  return "pass_simt_kernel";
+}
+
 pot_status pot_pass_status(void* workspace, void* stream) {
   g_err.clear();
   if (!workspace) return fail(POT_EINVAL, "workspace is NULL");

@@ -37,6 +37,8 @@ constexpr int NEPI = 4 * NGRP;                    // epilogue warps (4 TMEM lane
 constexpr int NTHREADS2 = 64 + 32 * NEPI;         // + TMA warp + MMA warp
 constexpr uint32_t TMEM2_COLS = 512;              // 2 buffers x 2 accumulators, each at a 128-column boundary
 constexpr int NCA = 8;                            // column-term ring depth
+constexpr int kMaxStages = 8;                     // Y ring depth bound (barrier slots)
+constexpr int kBarSlots = 2 + 2 * kMaxStages + 4 + 2 * NCA + 1;
 constexpr double kL2E2 = 1.4426950408889634;
 
 enum { V_RC = 0, V_R = 1, V_C = 2 };
@@ -58,7 +60,7 @@ __host__ __device__ inline Tc2Smem tc2_smem(int d) {
   L.cs_off = o; o += 2 * NGRP * 4 * 32 * 4;      // [buf][group][quad][32] float
   L.cm_off = o; o += 2 * NGRP * 4 * 4;           // [buf][group][quad] float
   L.rb_off = o; o += NGRP * 256 * 8;             // [group][256 rows] float2
-  L.bar_off = (o + 7) & ~7u; o = L.bar_off + 64 * 8;
+  L.bar_off = (o + 7) & ~7u; o = L.bar_off + kBarSlots * 8;
   L.misc_off = o; o += 16;
   L.total = o;
   return L;
@@ -77,13 +79,13 @@ tc2_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
   uint64_t* bars = (uint64_t*)(smem + SL.bar_off);
   uint64_t* fullA = bars + 0;
   uint64_t* aempty = bars + 1;
-  uint64_t* fullB = bars + 2;                  // [nst]
-  uint64_t* emptyB = bars + 6;                 // [nst]
-  uint64_t* tfull = bars + 10;                 // [2]
-  uint64_t* tempty = bars + 12;                // [2]
-  uint64_t* cfull = bars + 14;                 // [NCA]
-  uint64_t* cempty = bars + 14 + NCA;          // [NCA]
-  uint64_t* spare = bars + 14 + 2 * NCA;       // stall test hook: receives the withheld hand-off
+  uint64_t* fullB = bars + 2;                  // [nst <= kMaxStages]
+  uint64_t* emptyB = bars + 2 + kMaxStages;    // [nst]
+  uint64_t* tfull = bars + 2 + 2 * kMaxStages; // [2]
+  uint64_t* tempty = tfull + 2;                // [2]
+  uint64_t* cfull = tfull + 4;                 // [NCA]
+  uint64_t* cempty = cfull + NCA;              // [NCA]
+  uint64_t* spare = cempty + NCA;              // stall test hook: receives the withheld hand-off
   uint32_t* s_tmem = (uint32_t*)(smem + SL.misc_off);
   volatile int* s_abort = (volatile int*)(smem + SL.misc_off + 4);
   float4* sCA = (float4*)(smem + SL.ca_off);
