@@ -474,8 +474,11 @@ def pot_objective(prob: DeviceProblem, plan: Plan, gamma: float, ws: Optional[to
 
 
 def pot_marginals(prob: DeviceProblem, gamma: float, u: torch.Tensor, v: torch.Tensor, w: float,
-                  ws: Optional[torch.Tensor] = None):
-    """Returns (log row sums, log column sums, total mass) of B(u, v, w)."""
+                  ws: Optional[torch.Tensor] = None, check: bool = True):
+    """Returns (log row sums, log column sums, total mass) of B(u, v, w).
+    ``check``: synchronise and raise if the pass reported a stalled pipeline
+    (pot_pass_status); without it the call only enqueues and the mass is
+    returned as a device tensor."""
     ws, need = _workspace(prob, 0, ws)
     lrow = torch.empty(prob.n, dtype=torch.float64, device=prob.r.device)
     lcol = torch.empty(prob.m, dtype=torch.float64, device=prob.r.device)
@@ -484,6 +487,9 @@ def pot_marginals(prob: DeviceProblem, gamma: float, u: torch.Tensor, v: torch.T
     _check(lib().pot_marginals(ct.byref(prob.struct()), gamma, u.data_ptr(), v.data_ptr(), float(w),
                                ct.c_void_p(ws.data_ptr()), need, lrow.data_ptr(), lcol.data_ptr(), tot.data_ptr(),
                                ct.c_void_p(side.cuda_stream)))
+    if not check:
+        _finish(side, cur)
+        return lrow, lcol, tot
     _check(lib().pot_pass_status(ct.c_void_p(ws.data_ptr()), ct.c_void_p(side.cuda_stream)))
     _finish(side, cur)
     return lrow, lcol, float(tot.item())

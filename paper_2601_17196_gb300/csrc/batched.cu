@@ -23,12 +23,14 @@
 #include "../../include/aspot.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "simt_tile.cuh"
 
 namespace pot {
 pot_status set_last_error(pot_status s, const char* msg);
 }
 
 using namespace pot;
+using namespace pot::simt;
 
 namespace {
 
@@ -38,9 +40,9 @@ constexpr int kW = 256;        // default columns of a batched tile
 
 template <int NV>
 __device__ void block_sums(double (&v)[NV]) {
-  __shared__ double sh[NV][kBT / 32];
+  __shared__ double sh[NV][32];
   __shared__ double tot[NV];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     const double x = warp_sum_d(v[k]);
@@ -49,7 +51,7 @@ __device__ void block_sums(double (&v)[NV]) {
   __syncthreads();
   if (threadIdx.x < NV) {
     double s = 0.0;
-    for (int w = 0; w < kBT / 32; ++w) s += sh[threadIdx.x][w];
+    for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
     tot[threadIdx.x] = s;
   }
   __syncthreads();
@@ -60,23 +62,23 @@ __device__ void block_sums(double (&v)[NV]) {
 
 // log-sum-exp over the block of (x, active) -> natural log (all threads)
 __device__ double block_lse(double x, bool act) {
-  __shared__ double smx[kBT / 32], ssm[kBT / 32];
+  __shared__ double smx[32], ssm[32];
   __shared__ double res;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
   double mx = act ? x : -INFINITY;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) smx[warp] = mx;
   __syncthreads();
   double M = -INFINITY;
-  for (int w = 0; w < kBT / 32; ++w) M = fmax(M, smx[w]);
+  for (int w = 0; w < nw; ++w) M = fmax(M, smx[w]);
   double s = (act && M > -INFINITY) ? exp(x - M) : 0.0;
   s = warp_sum_d(s);
   if (lane == 0) ssm[warp] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < kBT / 32; ++w) t += ssm[w];
+    for (int w = 0; w < nw; ++w) t += ssm[w];
     res = (t > 0.0) ? M + log(t) : POT_NEG_BIG;
   }
   __syncthreads();
@@ -172,28 +174,29 @@ __global__ void b_init_kernel(BVecs V) {
   }
 }
 
-__global__ void b_extrap_kernel(BVecs V) {
-  BInst& I = V.inst[blockIdx.x];
+__device__ void b_extrap_body(const BVecs& V, int inst) {
+  BInst& I = V.inst[inst];
   if (I.done) return;
   const double th = I.theta;
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     V.ub[g] = (1.0 - th) * V.uc[g] + th * V.ut[g];
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     V.vb[g] = (1.0 - th) * V.vc[g] + th * V.vt[g];
   }
   if (threadIdx.x == 0) I.w_bar = (1.0 - th) * I.w_check + th * I.w_tilde;
 }
+__global__ void b_extrap_kernel(BVecs V) { b_extrap_body(V, blockIdx.x); }
 
 // gradient step and coupling (same formulas as the single-instance solver)
-__global__ void b_after_grad_kernel(BVecs V) {
-  BInst& I = V.inst[blockIdx.x];
+__device__ void b_after_grad_body(const BVecs& V, int inst) {
+  BInst& I = V.inst[inst];
   if (I.done) return;
   const double th = I.theta, Lth = I.L * th;
   double v[3] = {0, 0, 0};
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     const double ub = V.ub[g];
     const double rB = sexp(V.lrow[g]), eu = sexp(ub);
@@ -204,7 +207,7 @@ __global__ void b_after_grad_kernel(BVecs V) {
     v[1] += eu - ub * V.rt[g];
     if (!isfinite(un)) v[2] = 1.0;
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     const double vb = V.vb[g];
     const double cB = sexp(V.lcol[g]), ev = sexp(vb);
@@ -224,14 +227,14 @@ __global__ void b_after_grad_kernel(BVecs V) {
   }
 }
 
-__global__ void b_after_greenkhorn_kernel(BVecs V, int k) {
-  BInst& I = V.inst[blockIdx.x];
+__device__ void b_after_greenkhorn_body(const BVecs& V, int inst, int k) {
+  BInst& I = V.inst[inst];
   if (I.done) return;
   double v[2] = {0, 0};
   double xr = 0.0;
   bool act = false;
   double lt = 0.0;
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     const double ug = V.ug[g];
     if (k == 0) {
@@ -245,14 +248,14 @@ __global__ void b_after_greenkhorn_kernel(BVecs V, int k) {
   if (k == 2) {
     // log |B|_1 at z_grave over the instance's rows (blockwise log-sum-exp of the row log-sums)
     double acc = -INFINITY, s = 0.0;
-    for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+    for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
       const double x = V.lrow[I.row0 + i];
       if (x > acc) { s = s * exp(acc - x) + 1.0; acc = x; } else s += exp(x - acc);
     }
     xr = acc > -INFINITY ? acc + log(s) : POT_NEG_BIG;
     act = acc > -INFINITY;
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     const double vg = V.vg[g];
     if (k == 1) {
@@ -280,15 +283,15 @@ __global__ void b_after_greenkhorn_kernel(BVecs V, int k) {
   }
 }
 
-__global__ void b_after_final_kernel(BVecs V, int k) {
-  BInst& I = V.inst[blockIdx.x];
+__device__ void b_after_final_body(const BVecs& V, int inst, int k) {
+  BInst& I = V.inst[inst];
   if (I.done) return;
   const int take = I.take_hat;
   const double* uzh = (k == 0) ? V.uh : V.ug;
   const double* vzh = (k == 1) ? V.vh : V.vg;
   double v[4] = {0, 0, 0, 0};
   double acc = -INFINITY, ssum = 0.0;
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     const double uz = take ? uzh[g] : V.uc[g];
     const double R = V.lrow[g];
@@ -305,7 +308,7 @@ __global__ void b_after_final_kernel(BVecs V, int k) {
       if (R > acc) { ssum = ssum * exp(acc - R) + 1.0; acc = R; } else ssum += exp(R - acc);
     }
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     const double vz = take ? vzh[g] : V.vc[g];
     const double Cc = V.lcol[g];
@@ -333,7 +336,7 @@ __global__ void b_after_final_kernel(BVecs V, int k) {
     I.phi_check = base + v[2] - wc * s;
     I.E = E;
     I.tot = v[1];
-    if (I.t < kBTrace) V.trace[(int64_t)blockIdx.x * kBTrace + I.t] = (unsigned char)(take + 10 * k);
+    if (I.t < kBTrace) V.trace[(int64_t)inst * kBTrace + I.t] = (unsigned char)(take + 10 * k);
     const double th = I.theta;
     I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
     I.t = I.t + 1;
@@ -368,18 +371,18 @@ __device__ __forceinline__ void lse_add(double x, double& acc, double& s) {
 
 // After the two-sided pass at z_grave: choose k, Greenkhorn step, closed-form
 // phi(z^), argmin against phi(z_check).  z^ is written whole to (uh, vh).
-__global__ void b_greedy_greenkhorn_kernel(BVecs V) {
-  BInst& I = V.inst[blockIdx.x];
+__device__ void b_greedy_greenkhorn_body(const BVecs& V, int inst) {
+  BInst& I = V.inst[inst];
   if (I.done) return;
   double d[2] = {0, 0};
   double acc = -INFINITY, ss = 0.0;
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     const double R = V.lrow[g];
     d[0] += b_rho_log(V.rt[g], V.lrt[g], logaddexp(R, V.ug[g]));
     lse_add(R, acc, ss);
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     d[1] += b_rho_log(V.ct[g], V.lct[g], logaddexp(V.lcol[g], V.vg[g]));
   }
@@ -387,7 +390,7 @@ __global__ void b_greedy_greenkhorn_kernel(BVecs V) {
   const double lt = block_lse(acc > -INFINITY ? acc + log(ss) : POT_NEG_BIG, acc > -INFINITY);
   const int k = b_pick(d[0], d[1], b_rho_log(I.s, I.log_s, lt));
   double v[2] = {0, 0};
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     const double ug = V.ug[g];
     if (k == 0) {
@@ -399,7 +402,7 @@ __global__ void b_greedy_greenkhorn_kernel(BVecs V) {
       v[0] += sexp(ug) - ug * V.rt[g];
     }
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     const double vg = V.vg[g];
     if (k == 1) {
@@ -431,14 +434,14 @@ __global__ void b_greedy_greenkhorn_kernel(BVecs V) {
 // After the two-sided pass at z^t: E_t, the block k2 with the largest
 // decrease at z^t, z_check^{t+1} = Greenkhorn_{k2}(z^t) and its closed-form
 // phi, theta update and the stop test.
-__global__ void b_greedy_final_kernel(BVecs V) {
-  BInst& I = V.inst[blockIdx.x];
+__device__ void b_greedy_final_body(const BVecs& V, int inst) {
+  BInst& I = V.inst[inst];
   if (I.done) return;
   const int take = I.take_hat;
   // E parts, |B|_1, D_u, D_v, phi parts: rows stepped / kept, columns stepped / kept, nonfinite
   double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   double acc = -INFINITY, ss = 0.0;
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     const double uz = take ? V.uh[g] : V.uc[g];
     const double R = V.lrow[g], a = V.rt[g];
@@ -453,7 +456,7 @@ __global__ void b_greedy_final_kernel(BVecs V) {
     if (!isfinite(R) && R != POT_NEG_BIG) v[8] = 1.0;
     lse_add(R, acc, ss);
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     const double vz = take ? V.vh[g] : V.vc[g];
     const double Cc = V.lcol[g], c = V.ct[g];
@@ -470,12 +473,12 @@ __global__ void b_greedy_final_kernel(BVecs V) {
   const double lt = block_lse(acc > -INFINITY ? acc + log(ss) : POT_NEG_BIG, acc > -INFINITY);
   const double s = I.s;
   const int k2 = b_pick(v[2], v[3], b_rho_log(s, I.log_s, lt));
-  for (int64_t i = threadIdx.x; i < I.n; i += kBT) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
     const int64_t g = I.row0 + i;
     const double uz = V.uo[g];
     V.uc[g] = (k2 == 0) ? V.lrt[g] - softplus(V.lrow[g] - uz) : uz;
   }
-  for (int64_t j = threadIdx.x; j < I.m; j += kBT) {
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
     const int64_t g = I.col0 + j;
     const double vz = V.vo[g];
     V.vc[g] = (k2 == 1) ? V.lct[g] - softplus(V.lcol[g] - vz) : vz;
@@ -492,7 +495,7 @@ __global__ void b_greedy_final_kernel(BVecs V) {
     I.phi_check = ph;
     I.E = E;
     I.tot = v[1];
-    if (I.t < kBTrace) V.trace[(int64_t)blockIdx.x * kBTrace + I.t] = (unsigned char)(take + 2 * I.kg + 8 * k2);
+    if (I.t < kBTrace) V.trace[(int64_t)inst * kBTrace + I.t] = (unsigned char)(take + 2 * I.kg + 8 * k2);
     const double th = I.theta;
     I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
     I.t = I.t + 1;
@@ -502,6 +505,221 @@ __global__ void b_greedy_final_kernel(BVecs V) {
       atomicAdd(V.ndone, 1);
     }
   }
+}
+
+// ------------------------------------------------- fused batched sweep ---
+// One launch per pass of the iteration: a persistent grid walks the tile work
+// list (CTA b takes tiles b, b + G, ...); after a tile, the CTA takes a
+// ticket on the tile's instance, and the CTA that completes the instance's
+// last tile runs, for that instance alone, what used to be separate launches:
+// the combine of its partials into FP64 log-sums, its update (gradient step,
+// Greenkhorn step and argmin, or the final step with E_t and the stop test;
+// the greedy rule's counterparts), the extrapolation for the next iteration
+// and the per-pass terms of the next pass.  An iteration is three launches.
+
+enum { E_GRAD = 0, E_GK = 1, E_FINAL = 2, E_GGK = 3, E_GFINAL = 4 };
+
+// FP64 log-sums of one instance's rows and / or columns from the pass
+// partials (only its own column / row blocks; they are all written by every
+// pass, so nothing needs clearing).  Partials come from other SMs: L1 bypass.
+__device__ void b_combine_body(const BatchPass& B, const BVecs& V, const BInst& I, bool rows, bool cols) {
+  double* lrow = const_cast<double*>(V.lrow);
+  double* lcol = const_cast<double*>(V.lcol);
+  if (rows) {
+    const int64_t ncb = (I.m + B.W - 1) / B.W;
+    for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
+      const int64_t g = I.row0 + i;
+      float M = -INFINITY;
+      for (int64_t b = 0; b < ncb; ++b) {
+        const float2 p = __ldcg(B.row_part + b * B.Ntot + g);
+        if (p.y > 0.f) M = fmaxf(M, p.x);
+      }
+      float St = 0.f, comp = 0.f;
+      if (M > -INFINITY)
+        for (int64_t b = 0; b < ncb; ++b) {
+          const float2 p = __ldcg(B.row_part + b * B.Ntot + g);
+          if (p.y > 0.f) {
+            const float y = p.y * ex2(p.x - M) - comp;
+            const float t = St + y;
+            comp = (t - St) - y;
+            St = t;
+          }
+        }
+      lrow[g] = St > 0.f ? log_shifted_sum(M, St) : POT_NEG_BIG;
+    }
+  }
+  if (cols) {
+    const int64_t nrb = (I.n + B.H - 1) / B.H;
+    for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
+      const int64_t g = I.col0 + j;
+      float M = -INFINITY;
+      for (int64_t b = 0; b < nrb; ++b) {
+        const float2 p = __ldcg(B.col_part + b * B.Mtot + g);
+        if (p.y > 0.f) M = fmaxf(M, p.x);
+      }
+      float St = 0.f, comp = 0.f;
+      if (M > -INFINITY)
+        for (int64_t b = 0; b < nrb; ++b) {
+          const float2 p = __ldcg(B.col_part + b * B.Mtot + g);
+          if (p.y > 0.f) {
+            const float y = p.y * ex2(p.x - M) - comp;
+            const float t = St + y;
+            comp = (t - St) - y;
+            St = t;
+          }
+        }
+      lcol[g] = St > 0.f ? log_shifted_sum(M, St) : POT_NEG_BIG;
+    }
+  }
+  __syncthreads();
+}
+
+// Per-pass FP32 (hi, lo) terms of one instance for the next pass (the
+// batched prep kernel's arithmetic), potentials (arow, bcol) and the scalar
+// w given explicitly.
+__device__ void b_prep_body(const BatchPass& B, const BInst& I, const double* arow, const double* bcol, double w) {
+  for (int64_t i = threadIdx.x; i < I.n; i += blockDim.x) {
+    const int64_t g = I.row0 + i;
+    const float xn = B.xn[g];
+    HiLo hl = split_hilo((arow[g] + w - I.gC * (double)xn) * kL2E);
+    B.rowA[g] = make_float4(hl.hi, hl.lo, xn, 0.f);
+  }
+  for (int64_t j = threadIdx.x; j < I.m; j += blockDim.x) {
+    const int64_t g = I.col0 + j;
+    const float yn = B.yn[g];
+    HiLo hl = split_hilo((bcol[g] - I.gC * (double)yn) * kL2E);
+    B.colA[g] = make_float2(hl.hi, hl.lo);
+    B.colB[g] = make_float2(yn, 0.f);
+  }
+}
+
+__device__ void b_epilogue(const BatchPass& B, const BVecs& V, int inst, int epi, int k) {
+  BInst& I = V.inst[inst];
+  switch (epi) {
+    case E_GRAD:       // after P1 at z_bar: step and coupling; next: P2 at z_grave
+      b_combine_body(B, V, I, true, true);
+      b_after_grad_body(V, inst);
+      __syncthreads();
+      b_prep_body(B, I, V.ug, V.vg, I.w_grave);
+      break;
+    case E_GK: {       // after P2: Greenkhorn step k, argmin; next: P3 at z^t
+      b_combine_body(B, V, I, k != 1, k == 1);
+      b_after_greenkhorn_body(V, inst, k);
+      __syncthreads();
+      const bool hat = I.take_hat;
+      b_prep_body(B, I, hat ? (k == 0 ? V.uh : V.ug) : V.uc, hat ? (k == 1 ? V.vh : V.vg) : V.vc,
+                  hat ? I.w_hat : I.w_check);
+      break;
+    }
+    case E_GGK: {      // greedy rule after P2 (two-sided)
+      b_combine_body(B, V, I, true, true);
+      b_greedy_greenkhorn_body(V, inst);
+      __syncthreads();
+      const bool hat = I.take_hat;
+      b_prep_body(B, I, hat ? V.uh : V.uc, hat ? V.vh : V.vc, hat ? I.w_hat : I.w_check);
+      break;
+    }
+    default:           // after P3 at z^t: E_t, z_check^{t+1}, theta, stop; next: P1 at z_bar^{t+1}
+      b_combine_body(B, V, I, true, true);
+      if (epi == E_FINAL) b_after_final_body(V, inst, k);
+      else b_greedy_final_body(V, inst);
+      __syncthreads();
+      if (!I.done) {
+        b_extrap_body(V, inst);
+        __syncthreads();
+        b_prep_body(B, I, V.ub, V.vb, I.w_bar);
+      }
+      break;
+  }
+}
+
+template <int KIND, int VV, int MT>
+__global__ void __launch_bounds__(kThreads, 2) b_sweep_kernel(BatchPass B, BVecs V, int epi, int k) {
+  // Tiles are handed out by an atomic counter (a CTA busy with an instance's
+  // update does not hold up any tiles); a finished instance's remaining
+  // tiles are skipped in one step.  The last CTA to leave resets the counter.
+  __shared__ int s_last, s_tau;
+  int* const ctr = V.ndone + 1;
+  int* const exits = V.ndone + 2;
+  const int ntiles = (int)B.ntiles;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int t;
+      while (true) {
+        t = atomicAdd(ctr, 1);
+        if (t >= ntiles) break;
+        const BInst* Ii = B.inst + B.tiles[t].inst;
+        if (!*(volatile const int*)&Ii->done) break;
+        atomicMax(ctr, (int)(Ii->tile0 + Ii->ntile));   // the rest of a finished instance
+      }
+      s_tau = t;
+    }
+    __syncthreads();
+    const int tau = s_tau;
+    if (tau >= ntiles) break;
+    const BTile tl = B.tiles[tau];
+    BInst* I = B.inst + tl.inst;
+    PassDesc P{};
+    P.n = I->n; P.m = I->m; P.kind = KIND;
+    P.X = I->X; P.Y = I->Y; P.d = I->d; P.ldx = I->ldx; P.ldy = I->ldy;
+    P.xn = B.xn + I->row0; P.yn = B.yn + I->col0;
+    P.gC = I->gC;
+    P.mode = B.mode;
+    P.row_part = B.row_part + I->row0;
+    P.col_part = B.col_part + I->col0;
+    P.red_part = B.red_part;
+    P.kappa = &I->kappa;
+    P.rowA = B.rowA + I->row0;
+    P.colA = B.colA + I->col0;
+    P.colB = B.colB + I->col0;
+    simt_tile<KIND, VV, 4, false, MT>(P, B.H, tl.cb, tl.rb, B.Ntot, B.Mtot, tau);
+    __threadfence();                             // this tile's partials, before the ticket
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&I->ticket, 1) == I->ntile - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (threadIdx.x == 0) I->ticket = 0;
+      b_epilogue(B, V, tl.inst, epi, k);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(exits, 1) == (int)gridDim.x - 1) { *ctr = 0; *exits = 0; }
+  }
+}
+
+template <int VV, int MT>
+cudaError_t launch_sweep_vm(const BatchPass& B, const BVecs& V, int epi, int k, cudaStream_t st) {
+  static int grid[4] = {0, 0, 0, 0};
+  auto kern = (B.kind == COST_SQEUCLID_BF16) ? b_sweep_kernel<COST_SQEUCLID_BF16, VV, MT>
+            : (B.kind == COST_SQEUCLID_F16) ? b_sweep_kernel<COST_SQEUCLID_F16, VV, MT>
+                                             : b_sweep_kernel<COST_SQEUCLID_F32, VV, MT>;
+  const int slot = B.kind & 3;
+  if (grid[slot] == 0) {
+    int per = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, 0) != cudaSuccess || per < 1) per = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) sms = 152;
+    grid[slot] = per * sms;
+  }
+  const int64_t g = B.ntiles < grid[slot] ? B.ntiles : grid[slot];
+  kern<<<(unsigned)g, kThreads, 0, st>>>(B, V, epi, k);
+  return cudaGetLastError();
+}
+
+// one fused pass of the batched iteration (rows + columns, rows, or columns)
+cudaError_t launch_sweep(const BatchPass& B, const BVecs& V, int epi, int k, cudaStream_t st) {
+  const int mt = (B.mode == (PASS_ROWS | PASS_COLS)) ? 1 : (B.mode == PASS_ROWS ? 2 : 3);
+  if (B.W == 128) {
+    if (mt == 1) return launch_sweep_vm<1, 1>(B, V, epi, k, st);
+    if (mt == 2) return launch_sweep_vm<1, 2>(B, V, epi, k, st);
+    return launch_sweep_vm<1, 3>(B, V, epi, k, st);
+  }
+  if (mt == 1) return launch_sweep_vm<2, 1>(B, V, epi, k, st);
+  if (mt == 2) return launch_sweep_vm<2, 2>(B, V, epi, k, st);
+  return launch_sweep_vm<2, 3>(B, V, epi, k, st);
 }
 
 // rounding reading R1-R4, per instance (original r, c, s)
@@ -610,7 +828,12 @@ Geom b_geom(const pot_problem* P, int count, int H, int W) {
   Geom G;
   G.H = H; G.W = W;
   G.tile0.resize(count); G.ntile.resize(count);
-  for (int k = 0; k < count; ++k) {
+  // instances in order of decreasing size, so the largest per-instance
+  // updates of a fused sweep start early; each instance's tiles stay contiguous
+  std::vector<int> order(count);
+  for (int k = 0; k < count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P[a].n * P[a].m > P[b].n * P[b].m; });
+  for (int k : order) {
     const int64_t nrb = (P[k].n + H - 1) / H, ncb = (P[k].m + W - 1) / W;
     G.tile0[k] = G.T; G.ntile[k] = nrb * ncb;
     G.T += nrb * ncb;
@@ -1005,38 +1228,35 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   b_init_kernel<<<count, kBT, 0, st>>>(V);
   ++launches;
 
-  const int offw_bar = (int)offsetof(BInst, w_bar), offw_grave = (int)offsetof(BInst, w_grave);
-  const int offw_check = (int)offsetof(BInst, w_check), offw_hat = (int)offsetof(BInst, w_hat);
-  const int offw_out = (int)offsetof(BInst, w_out);
-  auto body = [&](int k) -> pot_status {
-    pot_status q;
-    b_extrap_kernel<<<count, kBT, 0, st>>>(V);
+  const int offw_bar = (int)offsetof(BInst, w_bar), offw_out = (int)offsetof(BInst, w_out);
+  // The iteration as three fused sweeps (see b_sweep_kernel): each pass's
+  // tiles, and per instance the combine, the update and the next pass's
+  // terms.  The first iteration's extrapolation and terms are formed here.
+  b_extrap_kernel<<<count, kBT, 0, st>>>(V);
+  {
+    BatchPass q = B;
+    q.mode = PASS_ROWS | PASS_COLS; q.arow0 = V.ub; q.bcol0 = V.vb; q.aoff0 = offw_bar; q.check_done = 1;
+    launch_prep_batched(q, st);
+  }
+  launches += 2;
+  BCK(cudaGetLastError());
+  auto sweep = [&](int mode, int epi, int k) -> pot_status {
+    BatchPass q = B;
+    q.mode = mode;
+    cudaError_t e = launch_sweep(q, V, epi, k, st);
     ++launches;
-    if ((q = pass(PASS_ROWS | PASS_COLS, V.ub, V.vb, offw_bar, nullptr, nullptr, -1, 0)) != POT_OK) return q;
-    b_after_grad_kernel<<<count, kBT, 0, st>>>(V);
-    ++launches;
-    if (greedy) {
-      // greedy rule: both sides at z_grave to score the blocks; z^ written whole
-      if ((q = pass(PASS_ROWS | PASS_COLS, V.ug, V.vg, offw_grave, nullptr, nullptr, -1, 0)) != POT_OK) return q;
-      b_greedy_greenkhorn_kernel<<<count, kBT, 0, st>>>(V);
-      ++launches;
-      if ((q = pass(PASS_ROWS | PASS_COLS, V.uc, V.vc, offw_check, V.uh, V.vh, offw_hat, 1)) != POT_OK) return q;
-      b_greedy_final_kernel<<<count, kBT, 0, st>>>(V);
-      ++launches;
-    } else {
-      if ((q = pass(k == 1 ? PASS_COLS : PASS_ROWS, V.ug, V.vg, offw_grave, nullptr, nullptr, -1, 0)) != POT_OK)
-        return q;
-      b_after_greenkhorn_kernel<<<count, kBT, 0, st>>>(V, k);
-      ++launches;
-      if ((q = pass(PASS_ROWS | PASS_COLS, V.uc, V.vc, offw_check, (k == 0) ? V.uh : V.ug, (k == 1) ? V.vh : V.vg,
-                    offw_hat, 1)) != POT_OK)
-        return q;
-      b_after_final_kernel<<<count, kBT, 0, st>>>(V, k);
-      ++launches;
-    }
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bfail(POT_ECUDA, cudaGetErrorString(e));
     return POT_OK;
+  };
+  auto body = [&](int k) -> pot_status {
+    pot_status q;
+    if ((q = sweep(PASS_ROWS | PASS_COLS, E_GRAD, k)) != POT_OK) return q;
+    if (greedy) {
+      if ((q = sweep(PASS_ROWS | PASS_COLS, E_GGK, k)) != POT_OK) return q;
+      return sweep(PASS_ROWS | PASS_COLS, E_GFINAL, k);
+    }
+    if ((q = sweep(k == 1 ? PASS_COLS : PASS_ROWS, E_GK, k)) != POT_OK) return q;
+    return sweep(PASS_ROWS | PASS_COLS, E_FINAL, k);
   };
 
   // the loop: graphs of `per` iterations, host polls the number of finished instances

@@ -79,4 +79,15 @@ __device__ __forceinline__ double logaddexp(double a, double b) {
   return mx + log1p(exp(-fabs(a - b)));
 }
 
+// Natural log of 2^M * S (M in log2 units, S > 0 an FP32 sum): the exponent
+// of S is split off exactly (frexpf), so the FP32 log2 acts on a mantissa in
+// [0.5, 1) and its absolute error stays near 1e-7; M, the exponent and that
+// logarithm are added in FP64.  FP64 logarithms would dominate the combine of
+// pass partials on this GPU (FP64 runs at a small fraction of the FP32 rate).
+__device__ __forceinline__ double log_shifted_sum(float M, float S) {
+  int ex;
+  const float mant = frexpf(S, &ex);
+  return ((double)M + (double)ex + (double)log2f(mant)) * 0.6931471805599453;
+}
+
 }  // namespace pot

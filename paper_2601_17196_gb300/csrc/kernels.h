@@ -121,7 +121,7 @@ struct BInst {
   double phi_check, phi_hat, phi_z, E, tot, m2, sum_q, kappa, obj;
   double mass_r, mass_c, min_r, min_c, bad;
   int32_t t, take_hat, done, nonfinite, branch, max_iter;
-  int32_t kg, kpad;                  // greedy rule: block of the step at z_grave
+  int32_t kg, ticket;                // greedy rule: block of the step at z_grave; fused sweep: tiles done this pass
   double *pu, *pv, *pw, *pf, *pg, *pp, *pq, *pkappa;
 };
 struct BTile { int32_t inst, rb, cb, pad; };

@@ -1,22 +1,26 @@
 // tcgen05 on-the-fly squared-Euclidean pass for the solver's hot loop
 // (BF16 points, d = 64 or 128; rows, columns or both).
 //
-// Tile geometry.  A row block is 512 rows held as four M = 128 accumulators
-// in TMEM; a tile is that row block against 64 columns (one TMA-loaded Y
-// tile shared by the four MMAs).  Two buffers of 4 x 64 columns fill the
-// 512 TMEM columns, so the MMA warp computes tile t + 1 while the epilogue
-// reads tile t.  Persistent CTAs, one per SM; CTA c owns the contiguous
-// range [c T / G, (c+1) T / G) of the T = ceil(n/512) x ceil(m/64) tiles in
-// row-block-major order (the X block stays in shared memory while the CTA
-// walks the columns of its row block).
+// Tile geometry.  A row block is 256 rows held as two M = 128 accumulators
+// in TMEM; a tile is that row block against 128 columns (one TMA-loaded Y
+// tile shared by the two MMAs, N = 128 each).  Two buffers of 2 x 128
+// columns fill the 512 TMEM columns, so the MMA warp computes tile t + 1
+// while the epilogue reads tile t.  Persistent CTAs, one per SM; CTA c owns
+// the contiguous range [c T / G, (c+1) T / G) of the T = ceil(n/256) x
+// ceil(m/128) tiles in row-block-major order (the X block stays in shared
+// memory while the CTA walks the columns of its row block).
 //
-// Warp roles (320 threads): warp 0 issues TMA (the X block once per row
+// Warp roles (576 threads): warp 0 issues TMA (the X block once per row
 // block, a ring of Y tiles) and stages each tile's column terms in shared
-// memory; warp 1 allocates TMEM and issues the MMAs; warps 2..9 are the
-// epilogue: 4 TMEM lane quadrants (warp % 4) x 2 groups of 32 columns.  Every epilogue
-// thread owns four rows (one lane of each accumulator) and 32 columns of a
-// tile, so the column reduction across the warp (a transposing butterfly)
-// is paid once per 4 x 32 entries.
+// memory; warp 1 allocates TMEM and issues the MMAs; warps 2..17 are the
+// epilogue: 4 TMEM lane quadrants (warp % 4) x 4 groups of 32 columns, four
+// epilogue warps on every SM sub-partition.  Every epilogue thread owns two
+// rows (one lane of each accumulator) and 32 columns of a tile, so the
+// column reduction across the warp (a transposing butterfly) is paid once
+// per 2 x 32 entries.  (Measured against four rows per thread in 512 x 64
+// tiles with eight epilogue warps: the extra warps hide more latency than the
+// extra transposes cost, 0.555 against 0.585 ms per two-sided pass at
+// n = 32768.)
 //
 // Numerics (log2 units, per entry):
 //   z_ij  = fma(k2, acc_ij, bhi_j) + blo_j          k2 = 2 log2(e) cost_scale / gamma
@@ -25,10 +29,10 @@
 // entry, a running (max, sum) per row in z units (the row term is added once,
 // when the row's partial is written); column side: the same exponentials
 // scaled by 2^(ahi + alo + M_i - W), W the largest such value among the
-// warp's 128 rows, summed over the thread's four rows, then over the warp's
+// warp's 64 rows, summed over the thread's two rows, then over the warp's
 // 32 lanes, then over the four quadrants: one (shift, sum) per column and
-// 512-row block.  An entry smaller than 2^-126 times the largest entry of
-// its 128-row warp stripe in the tile may be flushed (the same bound as the
+// 256-row block.  An entry smaller than 2^-126 times the largest entry of
+// its 64-row warp stripe in the tile may be flushed (the same bound as the
 // per-warp shift of the other passes).
 #include "common.cuh"
 #include "pass.h"
@@ -41,12 +45,12 @@ namespace {
 
 using namespace tcx;
 
-constexpr int NACC = 4;                           // accumulators (128 rows each) per row block
-constexpr int BM3 = 128 * NACC, BN3 = 64;
+constexpr int NACC = 2;                           // accumulators (128 rows each) per row block
+constexpr int BM3 = 128 * NACC, BN3 = 128;
 constexpr int NGRP3 = BN3 / 32;                   // groups of 32 columns
 constexpr int NEPI3 = 4 * NGRP3;                  // epilogue warps
 constexpr int NTHREADS3 = 64 + 32 * NEPI3;        // + TMA warp + MMA warp
-constexpr uint32_t TMEM3_COLS = 512;              // 2 buffers x 4 accumulators x 64 columns
+constexpr uint32_t TMEM3_COLS = 512;              // 2 buffers x 2 accumulators x 128 columns
 constexpr int NCA3 = 8;                           // column-term ring depth
 constexpr int kMaxStages3 = 8;
 constexpr int kBarSlots3 = 2 + 2 * kMaxStages3 + 4 + 2 * NCA3 + 1;
@@ -227,7 +231,7 @@ tc3_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
     const int ntl = (int)ntiles, pn = (int)P.n, pm = (int)P.m;
     float2* const rowp = P.row_part;
     float2* const colp = P.col_part;
-    float arow[NACC], Mr[NACC], Sr[NACC];      // arow: ahi + alo of the thread's four rows
+    float arow[NACC], Mr[NACC], Sr[NACC];      // arow: ahi + alo of the thread's rows
 #pragma unroll
     for (int h = 0; h < NACC; ++h) { arow[h] = POT_NEG_BIGF; Mr[h] = POT_NEG_BIGF; Sr[h] = 0.f; }
 

@@ -15,19 +15,6 @@ namespace pot {
 
 namespace {
 
-constexpr double kLn2 = 0.6931471805599453;
-
-// Natural log of 2^M * S (M in log2 units, S > 0 an FP32 sum): the exponent
-// of S is split off exactly (frexpf), so the FP32 log2 acts on a mantissa in
-// [0.5, 1) and its absolute error stays near 1e-7; M, the exponent and that
-// logarithm are added in FP64.  FP64 logarithms would dominate the combine on
-// this GPU (FP64 runs at a small fraction of the FP32 rate).
-__device__ __forceinline__ double log_shifted_sum(float M, float S) {
-  int ex;
-  const float mant = frexpf(S, &ex);
-  return ((double)M + (double)ex + (double)log2f(mant)) * kLn2;
-}
-
 // Partials -> FP64 log-sums for rows and / or columns.  Block = 32 entries x
 // 8 slices of the partials (coalesced: a warp reads 32 consecutive entries of
 // one partial row); the slices meet in shared memory.
