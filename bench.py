@@ -46,9 +46,9 @@ D_FULL = 128
 # ncu DRAM bytes per launch of the current kernels (null once a kernel changes):
 # dense_pass_kernel<0>, n = m = 16384 FP32 cost: 1.075126 GB read + 11.26 MB written
 DENSE_16K_TRAFFIC = 1.075126e9 + 11.25888e6
-# tc2_pass_kernel<0> (rows + columns), n = m = 32768, d = 128: 17.62 MB read (the BF16
-# points) + 5 KB written; the column partials (33.5 MB) stay in L2
-TC2_32K_TRAFFIC = 17618944.0 + 5120.0
+# tc3_pass_kernel<0> (rows + columns), n = m = 32768, d = 128: 17.62 MB read (the BF16
+# points) + 7.7 KB written per launch; the column partials (16.8 MB) stay in L2
+TC3_32K_TRAFFIC = 17617152.0 + 7680.0
 
 
 def _args():
@@ -452,7 +452,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"kernel": kernel_name, "bound": "tensor",
                      "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                      "frac": (achieved / sustained) if achieved else None,
-                     "traffic": TC2_32K_TRAFFIC if n == N_FULL else None,
+                     "traffic": TC3_32K_TRAFFIC if n == N_FULL else None,
                      "traffic_note": "ncu dram bytes of one two-sided launch at n=32768 (read + write)",
                      "peak_source": f"{src} bf16 dense, sustained (kernel timed inside a long step)",
                      "flop_per_launch": flop_per_pass, "avg_launch_ms": avg_pass_ms, "launches": pass_n},

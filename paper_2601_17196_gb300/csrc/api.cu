@@ -260,7 +260,9 @@ pot_status check_tc(Ctx& X) {
   return e ? tc_timeout() : POT_OK;
 }
 
-pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true) {
+// combine: launch the combine of the partials into lrow / lcol (the solvers'
+// loop kernels combine them themselves and pass false)
+pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true, bool combine = true) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (X.prof && X.in_loop && profile) {
     const size_t need = 2 * (size_t)(X.pass_ord + 1);
@@ -287,7 +289,7 @@ pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true) {
     X.launches += 1;
   }
   if (e1) CK(cudaEventRecordWithFlags(e1, X.st, cudaEventRecordExternal));
-  if (d.mode & (PASS_ROWS | PASS_COLS)) {
+  if (combine && (d.mode & (PASS_ROWS | PASS_COLS))) {
     launch_combine(X.rowp, X.L.ncolblk, d.n, (d.mode & PASS_ROWS) ? X.lrow : nullptr, X.colp, X.L.nrowblk, d.m,
                    (d.mode & PASS_COLS) ? X.lcol : nullptr, d.done, X.st, d.skip, d.skip_if);
     X.launches += 1;
@@ -295,6 +297,11 @@ pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true) {
   CKL();
   return POT_OK;
 }
+
+// Whether the solver loops' update kernels combine the pass partials inline
+// (one thread per row / column) instead of a combine launch: when every entry
+// has at most 32 partials.
+int fuse_combine(const Ctx& X) { return (X.L.ncolblk <= 32 && X.L.nrowblk <= 32) ? 1 : 0; }
 
 int64_t pass_ctas(const Ctx& X) {  // one partial per CTA of a max / objective pass
   return X.L.use_tc ? X.L.tl.v1_units : X.L.sl.ncolblk * X.L.sl.nrowblk;
@@ -611,6 +618,7 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
   V.lrow = X.lrow; V.lcol = X.lcol;
   V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
+  V.fused = 0;                             // the warm-start check below uses combined passes
   launch_aspot_init(V, prob->r, prob->c, so.eps_s, params->u0, params->v0, params->w0, X.st); X.launches += 1;
   CKL();
   const pot_aspot_state* RS = params->resume;
@@ -650,10 +658,9 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   }
   auto body = [&](int k) -> pot_status {
     pot_status q;
-    launch_aspot_extrap(V, X.st); X.launches += 1;
     PassDesc p1 = d;                       // gradient pass at z_bar (both sides)
     p1.mode = PASS_ROWS | PASS_COLS; p1.arow0 = V.ub; p1.bcol0 = V.vb; p1.aoff0 = &X.S->w_bar; p1.done = &X.S->done;
-    if ((q = run_pass(X, p1)) != POT_OK) return q;
+    if ((q = run_pass(X, p1, true, !V.fused)) != POT_OK) return q;
     launch_aspot_after_grad(V, X.st); X.launches += 1;
     // Greenkhorn pass at z_grave: the side of block k (both sides for the w-step,
     // whose column sums give those of z^ in closed form)
@@ -661,7 +668,7 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
     p2.mode = (k == 1) ? PASS_COLS : (k == 2 ? (PASS_ROWS | PASS_COLS) : PASS_ROWS);
     p2.arow0 = V.ug; p2.bcol0 = V.vg; p2.aoff0 = &X.S->w_grave;
     p2.done = &X.S->done;
-    if ((q = run_pass(X, p2)) != POT_OK) return q;
+    if ((q = run_pass(X, p2, true, !V.fused)) != POT_OK) return q;
     launch_aspot_after_greenkhorn(V, k, X.st); X.launches += 1;
     // pass at z^t = argmin.  When the argmin keeps z^ (take_hat), the sums of
     // the side block k just updated follow from the Greenkhorn pass in closed
@@ -675,12 +682,12 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
     if (k != 2) {
       PassDesc p3a = p3;
       p3a.mode = (k == 0) ? PASS_COLS : PASS_ROWS;
-      if ((q = run_pass(X, p3a)) != POT_OK) return q;
+      if ((q = run_pass(X, p3a, true, !V.fused)) != POT_OK) return q;
     }
     PassDesc p3b = p3;
     p3b.mode = (k == 0) ? PASS_ROWS : (k == 1 ? PASS_COLS : (PASS_ROWS | PASS_COLS));
     p3b.skip = &X.S->take_hat; p3b.skip_if = 1;
-    if ((q = run_pass(X, p3b, false)) != POT_OK) return q;
+    if ((q = run_pass(X, p3b, false, !V.fused)) != POT_OK) return q;
     launch_aspot_after_final(V, k, X.st); X.launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
@@ -692,15 +699,14 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   // (nothing after a w-step, whose sums follow in closed form).
   auto body_greedy = [&](int) -> pot_status {
     pot_status q;
-    launch_aspot_extrap(V, X.st); X.launches += 1;
     PassDesc p1 = d;
     p1.mode = PASS_ROWS | PASS_COLS; p1.arow0 = V.ub; p1.bcol0 = V.vb; p1.aoff0 = &X.S->w_bar; p1.done = &X.S->done;
-    if ((q = run_pass(X, p1)) != POT_OK) return q;
+    if ((q = run_pass(X, p1, true, !V.fused)) != POT_OK) return q;
     launch_aspot_after_grad(V, X.st); X.launches += 1;
     PassDesc p2 = d;
     p2.mode = PASS_ROWS | PASS_COLS; p2.arow0 = V.ug; p2.bcol0 = V.vg; p2.aoff0 = &X.S->w_grave;
     p2.done = &X.S->done;
-    if ((q = run_pass(X, p2)) != POT_OK) return q;
+    if ((q = run_pass(X, p2, true, !V.fused)) != POT_OK) return q;
     launch_aspot_greedy_pick(V, X.st);
     launch_aspot_after_greenkhorn(V, -1, X.st); X.launches += 2;
     PassDesc p3 = d;
@@ -709,13 +715,13 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
     p3.sel = &X.S->take_hat; p3.done = &X.S->done;
     PassDesc p3z = p3;                     // z^t = z_check: both sides
     p3z.mode = PASS_ROWS | PASS_COLS; p3z.skip = &X.S->take_hat; p3z.skip_if = 1;
-    if ((q = run_pass(X, p3z, false)) != POT_OK) return q;
+    if ((q = run_pass(X, p3z, false, !V.fused)) != POT_OK) return q;
     PassDesc p3r = p3;                     // z^t = z^ after a v-step: rows
     p3r.mode = PASS_ROWS; p3r.skip = &X.S->run_r3; p3r.skip_if = 0;
-    if ((q = run_pass(X, p3r, false)) != POT_OK) return q;
+    if ((q = run_pass(X, p3r, false, !V.fused)) != POT_OK) return q;
     PassDesc p3c = p3;                     // z^t = z^ after a u-step: columns
     p3c.mode = PASS_COLS; p3c.skip = &X.S->run_c3; p3c.skip_if = 0;
-    if ((q = run_pass(X, p3c, false)) != POT_OK) return q;
+    if ((q = run_pass(X, p3c, false, !V.fused)) != POT_OK) return q;
     launch_aspot_greedy_final(V, X.st);
     launch_aspot_greedy_apply(V, X.st); X.launches += 2;
     cudaError_t e = cudaGetLastError();
@@ -725,6 +731,14 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   const int per = params->check_every > 0 ? params->check_every : 24;
   auto aspot_passes = [](int k) { return k == 2 ? 2 : 3; };      // P1, P2 (, P3a); P3b is not timed
   auto greedy_passes = [](int) { return 2; };                     // P1, P2; the passes at z^t are not timed
+  // z_bar of the first iteration; later ones are formed by the iteration's last kernel
+  launch_aspot_extrap(V, X.st); X.launches += 1;
+  // from here the loop kernels combine the partials themselves when there are
+  // few per entry (small problems, where a launch costs more than the work);
+  // with many (the tcgen05 pass at large n: one per 256-row block) the wide
+  // combine kernel, eight threads per entry, is faster
+  V.fused = fuse_combine(X);
+  CKL();
   {
     Nvtx range("aspot: iterations");
     const int k0 = RS ? RS->t % 3 : 0;      // the cyclic rule goes on with block t mod 3
@@ -842,6 +856,7 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
   V.row_part = X.rowp; V.col_part = X.colp; V.ncolblk = X.L.ncolblk; V.nrowblk = X.L.nrowblk;
   V.lrow = X.lrow; V.lcol = X.lcol;
   V.red = X.red; V.counter = X.cnt; V.S = X.S; V.trace = (params->flags & POT_FLAG_TRACE) ? 1 : 0;
+  V.fused = fuse_combine(X);               // the update kernels combine the pass partials themselves
   launch_sink_init(V, prob->r, prob->c, so.eps_s, prob->s, X.st); X.launches += 1;
   CKL();
   PassDesc d = base_desc(X, gamma);
@@ -849,11 +864,11 @@ pot_status sinkhorn_pot_solve(const pot_problem* prob, const pot_params* params,
     pot_status q;
     PassDesc pr = d;
     pr.mode = PASS_ROWS; pr.arow0 = V.u; pr.bcol0 = V.v; pr.aoff0 = nullptr; pr.done = &X.S->done;
-    if ((q = run_pass(X, pr)) != POT_OK) return q;
+    if ((q = run_pass(X, pr, true, !V.fused)) != POT_OK) return q;
     launch_sink_after_rows(V, X.st); X.launches += 2;
     PassDesc pc = d;
     pc.mode = PASS_COLS; pc.arow0 = V.u; pc.bcol0 = V.v; pc.aoff0 = nullptr; pc.done = &X.S->done;
-    if ((q = run_pass(X, pc)) != POT_OK) return q;
+    if ((q = run_pass(X, pc, true, !V.fused)) != POT_OK) return q;
     launch_sink_after_cols(V, X.st); X.launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(POT_ECUDA, "iteration launch: %s", cudaGetErrorString(e));
@@ -987,7 +1002,7 @@ pot_status pot_plan_dense(const pot_problem* prob, const pot_plan* plan, double 
 const char* pot_pass_kernel(const pot_problem* prob, int32_t flags) {
   if (check_problem(prob) != POT_OK) return "";
   const Layout L = make_layout(prob, flags);
-  if (L.use_tc) return L.tl.v3 ? "tc3_pass_kernel" : (L.tl.v2 ? "tc2_pass_kernel" : "tc_pass_kernel");
+  if (L.use_tc) return L.tl.v3 ? "tc3_pass_kernel" : "tc_pass_kernel";
   if (prob->kind == POT_COST_DENSE_F32 && L.sl.dense_fast) return "dense_pass_kernel";
   return "pass_simt_kernel";
 }

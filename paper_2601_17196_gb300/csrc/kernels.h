@@ -27,8 +27,7 @@ struct TcLayout {
   int64_t ncolblk, nrowblk;          // partial counts of the row / column passes (what the combines read)
   int64_t nchunks, tiles_per_chunk;  // general kernel: 128-row units x column chunks
   int64_t v1_nrowblk, v1_units;
-  int v2;                            // hot-loop kernel of pass_tc2.cu serves rows / columns passes
-  int v3;                            // hot-loop kernel of pass_tc3.cu serves them (takes precedence)
+  int v3;                            // hot-loop kernel (pass_tc3.cu) serves rows / columns passes
   int64_t G, T, ntiles2, nrb2, nslots, n_pad2;
   int64_t n_pad, m_pad;              // padding of the per-pass row / column terms
   int ok;
@@ -36,11 +35,6 @@ struct TcLayout {
 TcLayout tc_layout(int64_t n, int64_t m, int d);
 bool tc_supported(const PassDesc& P);
 cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st, cudaEvent_t before_main = nullptr);
-bool tc2_applicable(int d);
-int tc2_tile_cols();
-void tc2_fill_layout(TcLayout& L, int64_t n, int64_t m, int num_sms);
-cudaError_t launch_pass_tc2(const PassDesc& P, const TcLayout& L, const CUtensorMap& mx, const CUtensorMap& my,
-                            cudaStream_t st);
 bool tc3_applicable(int d);
 int tc3_tile_cols();
 void tc3_fill_layout(TcLayout& L, int64_t n, int64_t m, int num_sms);
@@ -79,6 +73,7 @@ struct AspotVecs {
   double* red; unsigned int* counter;
   DevState* S;
   int trace;
+  int fused;                 // the loop kernels combine the pass partials themselves (no combine launch)
 };
 
 struct SinkVecs {
@@ -92,6 +87,7 @@ struct SinkVecs {
   double* red; unsigned int* counter;
   DevState* S;
   int trace;
+  int fused;                 // the loop kernels combine the pass partials themselves (no combine launch)
 };
 
 struct RoundVecs {

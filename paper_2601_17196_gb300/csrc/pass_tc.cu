@@ -391,16 +391,14 @@ TcLayout tc_layout(int64_t n, int64_t m, int d) {
   L.n_pad = L.v1_nrowblk * BM;
   L.m_pad = ntiles * BN;
   L.v3 = tc3_applicable(d) ? 1 : 0;
-  L.v2 = (!L.v3 && tc2_applicable(d)) ? 1 : 0;
-  if (L.v3 || L.v2) {
+  if (L.v3) {
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
       cudaGetLastError();
       sms = 152;
     }
-    if (L.v3) tc3_fill_layout(L, n, m, sms);
-    else tc2_fill_layout(L, n, m, sms);
+    tc3_fill_layout(L, n, m, sms);
     if (L.n_pad2 > L.n_pad) L.n_pad = L.n_pad2;
     L.ncolblk = L.nslots;
     L.nrowblk = L.nrb2;
@@ -432,11 +430,6 @@ cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st
     if (!make_map(&mx, P.X, P.n, P.d, P.ldx, 128) || !make_map(&my, P.Y, P.m, P.d, P.ldy, tc3_tile_cols()))
       return cudaErrorInvalidValue;
     return launch_pass_tc3(P, L, mx, my, st);
-  }
-  if (L.v2 && !(md & (PASS_MAXCOST | PASS_OBJ))) {
-    if (!make_map(&mx, P.X, P.n, P.d, P.ldx, 128) || !make_map(&my, P.Y, P.m, P.d, P.ldy, tc2_tile_cols()))
-      return cudaErrorInvalidValue;
-    return launch_pass_tc2(P, L, mx, my, st);
   }
   if (!make_map(&mx, P.X, P.n, P.d, P.ldx) || !make_map(&my, P.Y, P.m, P.d, P.ldy)) return cudaErrorInvalidValue;
   if (md & PASS_MAXCOST) return launch_mode<M_MAX>(P, L, mx, my, st);

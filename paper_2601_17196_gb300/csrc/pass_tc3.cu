@@ -409,8 +409,10 @@ tc3_pass_kernel(PassDesc P, TcLayout TL, const __grid_constant__ CUtensorMap tmX
   }
 }
 
-// empty row partials (-big, 0) for the slots no CTA writes
-__global__ void tc3_clear_rows_kernel(float2* row_part, int64_t count) {
+// empty row partials (-big, 0) for the slots no CTA writes (nothing when the
+// pass is off: a skipped pass must leave the previous partials in place)
+__global__ void tc3_clear_rows_kernel(PassDesc P, float2* row_part, int64_t count) {
+  if (pass_off(P)) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < count) row_part[t] = make_float2(POT_NEG_BIGF, 0.f);
 }
@@ -455,7 +457,7 @@ cudaError_t launch_pass_tc3(const PassDesc& P, const TcLayout& L, const CUtensor
                             cudaStream_t st) {
   if (P.mode & PASS_ROWS) {
     const int64_t cnt = L.nslots * P.n;
-    tc3_clear_rows_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(P.row_part, cnt);
+    tc3_clear_rows_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(P, P.row_part, cnt);
   }
   const int md = P.mode;
   if ((md & PASS_ROWS) && (md & PASS_COLS)) return launch3<W_RC>(P, L, mx, my, st);

@@ -197,6 +197,43 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
 __device__ __forceinline__ double clamp_log(double x) { return x > POT_NEG_BIG ? x : POT_NEG_BIG; }
 __device__ __forceinline__ double safe_exp(double x) { return x > -700.0 ? exp(x) : 0.0; }
 
+// FP64 log-sum of entry j from the nblk (max, sum) partials of a pass (the
+// arithmetic of combine_kernel, one thread per entry): the loop kernels of the
+// solvers call it instead of a separate combine launch.
+__device__ double comb_part(const float2* part, int64_t nblk, int64_t len, int64_t j) {
+  float M = -INFINITY;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const float2 p = part[b * len + j];
+    if (p.y > 0.f) M = fmaxf(M, p.x);
+  }
+  if (!(M > -INFINITY)) return POT_NEG_BIG;
+  float St = 0.f, comp = 0.f;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const float2 p = part[b * len + j];
+    if (p.y > 0.f) {
+      const float y = p.y * ex2(p.x - M) - comp;
+      const float t = St + y;
+      comp = (t - St) - y;
+      St = t;
+    }
+  }
+  return St > 0.f ? log_shifted_sum(M, St) : POT_NEG_BIG;
+}
+template <class Vecs>
+__device__ __forceinline__ double row_sum_of(const Vecs& V, int64_t i, bool from_parts) {
+  if (!from_parts) return V.lrow[i];
+  const double R = comb_part(V.row_part, V.ncolblk, V.n, i);
+  const_cast<double*>(V.lrow)[i] = R;         // later kernels of the iteration read it
+  return R;
+}
+template <class Vecs>
+__device__ __forceinline__ double col_sum_of(const Vecs& V, int64_t j, bool from_parts) {
+  if (!from_parts) return V.lcol[j];
+  const double C = comb_part(V.col_part, V.nrowblk, V.m, j);
+  const_cast<double*>(V.lcol)[j] = C;
+  return C;
+}
+
 // ----------------------------------------------------------- prologue ---
 
 __global__ void marg_stats_kernel(const double* r, const double* c, int64_t n, int64_t m, double* part,
@@ -309,7 +346,7 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
   double v[3] = {0, 0, 0};   // tot, sum(e^u - u r~) + sum(e^v - v c~), nonfinite
   if (t < V.n) {
     const double ub = V.ub[t];
-    const double R = V.lrow[t];
+    const double R = row_sum_of(V, t, V.fused);
     const double rB = safe_exp(R), eu = safe_exp(ub);
     const double g = rB + eu - V.rt[t];
     const double un = ub - g / Lth;
@@ -321,7 +358,7 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vb = V.vb[j];
-    const double Cc = V.lcol[j];
+    const double Cc = col_sum_of(V, j, V.fused);
     const double cB = safe_exp(Cc), ev = safe_exp(vb);
     const double g = cB + ev - V.ct[j];
     const double vn = vb - g / Lth;
@@ -354,23 +391,25 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
   double v[2] = {0, 0};      // phi parts
   double xr = 0.0;           // log row sum (w step: log |B|_1 = LSE_i of these)
   bool act = false;
+  const bool comb = V.fused && !greedy;     // greedy: the block choice kernel combined them
   if (t < V.n) {
     const double ug = V.ug[t];
     if (k == 0) {
-      const double R = V.lrow[t];
+      const double R = row_sum_of(V, t, comb);
       const double uh = V.lrt[t] - softplus(R - ug);
       V.uh[t] = uh;
       v[0] = -uh * V.rt[t];
     } else {
       v[0] = safe_exp(ug) - ug * V.rt[t];
-      if (k == 2) { xr = V.lrow[t]; act = true; }
+      if (k == 2) { xr = row_sum_of(V, t, comb); act = true; }
       if (greedy) V.uh[t] = ug;
     }
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vg = V.vg[j];
+    if (comb && k == 2) col_sum_of(V, j, true);   // for the closed forms of the final kernel
     if (k == 1) {
-      const double Cc = V.lcol[j];
+      const double Cc = col_sum_of(V, j, comb);
       const double vh = V.lct[j] - softplus(Cc - vg);
       V.vh[j] = vh;
       v[1] = -vh * V.ct[j];
@@ -417,9 +456,14 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   // z^t = z^: the sums of block k's side come from the Greenkhorn pass at
   // z_grave in closed form (the other side was computed at z^ by P3a)
   const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
+  // theta_{t+1} (each block reads theta_t before the last block updates it):
+  // the extrapolation z_bar^{t+1} of the next iteration is formed here
+  const double th0 = S->theta;
+  const double thn = th0 * (sqrt(th0 * th0 + 4.0) - th0) / 2.0;
   if (t < V.n) {
     const double uz = take ? uz_hat[t] : V.uc[t];
-    double R = V.lrow[t];
+    // rows: from the pass at z^t (P3a for k = 1, P3b when z^t = z_check), else closed form
+    double R = row_sum_of(V, t, V.fused && (k == 1 || !take));
     if (take && k == 0) R = clamp_log(R + (V.uh[t] - V.ug[t]));
     else if (take && k == 2) R = clamp_log(R + dw);
     xr = R;
@@ -430,12 +474,13 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     V.uo[t] = uz;
     const double un = (k == 0) ? V.lrt[t] - softplus(R - uz) : uz;
     V.uc[t] = un;
+    V.ub[t] = (1.0 - thn) * un + thn * V.ut[t];
     v[2] = (k == 0) ? -un * V.rt[t] : eu - un * V.rt[t];    // un = uz unless k = 0
     if (!isfinite(R) && R != POT_NEG_BIG) v[3] = 1;
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vz = take ? vz_hat[j] : V.vc[j];
-    double Cc = V.lcol[j];
+    double Cc = col_sum_of(V, j, V.fused && (k == 0 || !take));
     if (take && k == 1) Cc = clamp_log(Cc + (V.vh[j] - V.vg[j]));
     else if (take && k == 2) Cc = clamp_log(Cc + dw);
     const double cB = safe_exp(Cc), ev = safe_exp(vz);
@@ -443,6 +488,7 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     V.vo[j] = vz;
     const double vn = (k == 1) ? V.lct[j] - softplus(Cc - vz) : vz;
     V.vc[j] = vn;
+    V.vb[j] = (1.0 - thn) * vn + thn * V.vt[j];
     v[2] = (k == 1) ? -vn * V.ct[j] : ev - vn * V.ct[j];    // vn = vz unless k = 1
     if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[3] = 1;
   }
@@ -465,8 +511,8 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
       double* tr = S->trace[it & 4095];
       tr[0] = E; tr[1] = S->phi_z; tr[2] = S->phi_check; tr[3] = (double)take;
     }
-    const double th = S->theta;
-    S->theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
+    S->theta = thn;
+    S->w_bar = (1.0 - thn) * wc + thn * S->w_tilde;
     S->t = it + 1;
     if (tot[3] != 0.0 || !isfinite(E)) S->nonfinite = 1;
     if (E <= S->thr || it + 1 >= S->max_iter || S->nonfinite) S->done = 1;
@@ -502,13 +548,13 @@ __global__ void aspot_greedy_pick_kernel(AspotVecs V) {
   double xr = 0.0;
   bool act = false;
   if (t < V.n) {
-    const double R = V.lrow[t];
+    const double R = row_sum_of(V, t, V.fused);
     v[0] = rho_log(V.rt[t], V.lrt[t], logaddexp(R, V.ug[t]));
     xr = R;
     act = true;
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
-    v[1] = rho_log(V.ct[j], V.lct[j], logaddexp(V.lcol[j], V.vg[j]));
+    v[1] = rho_log(V.ct[j], V.lct[j], logaddexp(col_sum_of(V, j, V.fused), V.vg[j]));
   }
   double tot[2], ltot = 0.0;
   if (reduce_last_lse<2>(v, xr, act, V.red, V.counter, tot, &ltot) && threadIdx.x == 0)
@@ -518,14 +564,16 @@ __global__ void aspot_greedy_pick_kernel(AspotVecs V) {
 // Sums of B(z^t) on both sides: from the passes at z^t, or in closed form
 // from the pass at z_grave for the side of the block just stepped (as in
 // aspot_after_final_kernel).
-__device__ __forceinline__ double greedy_row_sum(const AspotVecs& V, int64_t i, int k, int take, double dw) {
-  double R = V.lrow[i];
+__device__ __forceinline__ double greedy_row_sum(const AspotVecs& V, int64_t i, int k, int take, double dw,
+                                                 bool from_parts = false) {
+  double R = row_sum_of(V, i, from_parts);
   if (take && k == 0) R = clamp_log(R + (V.uh[i] - V.ug[i]));
   else if (take && k == 2) R = clamp_log(R + dw);
   return R;
 }
-__device__ __forceinline__ double greedy_col_sum(const AspotVecs& V, int64_t j, int k, int take, double dw) {
-  double Cc = V.lcol[j];
+__device__ __forceinline__ double greedy_col_sum(const AspotVecs& V, int64_t j, int k, int take, double dw,
+                                                 bool from_parts = false) {
+  double Cc = col_sum_of(V, j, from_parts);
   if (take && k == 1) Cc = clamp_log(Cc + (V.vh[j] - V.vg[j]));
   else if (take && k == 2) Cc = clamp_log(Cc + dw);
   return Cc;
@@ -547,7 +595,8 @@ __global__ void aspot_greedy_final_kernel(AspotVecs V) {
   bool act = false;
   if (t < V.n) {
     const double uz = take ? V.uh[t] : V.uc[t];
-    const double R = greedy_row_sum(V, t, k, take, dw);
+    // from the passes at z^t (both sides at z_check, rows after a v-step) or closed form
+    const double R = greedy_row_sum(V, t, k, take, dw, V.fused && (!take || k == 1));
     xr = R;
     act = true;
     const double rB = safe_exp(R), eu = safe_exp(uz), a = V.rt[t];
@@ -561,7 +610,7 @@ __global__ void aspot_greedy_final_kernel(AspotVecs V) {
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vz = take ? V.vh[j] : V.vc[j];
-    const double Cc = greedy_col_sum(V, j, k, take, dw);
+    const double Cc = greedy_col_sum(V, j, k, take, dw, V.fused && (!take || k == 0));
     const double cB = safe_exp(Cc), ev = safe_exp(vz), c = V.ct[j];
     v[0] = fabs(cB + ev - c);
     v[3] = rho_log(c, V.lct[j], logaddexp(Cc, vz));
@@ -608,14 +657,20 @@ __global__ void aspot_greedy_apply_kernel(AspotVecs V) {
   const int k = S->kg, take = S->take_hat, k2 = S->k2;
   const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double th = S->theta;               // theta_{t+1}: the extrapolation of the next iteration
   if (t < V.n) {
     const double uz = V.uo[t];
-    V.uc[t] = (k2 == 0) ? V.lrt[t] - softplus(greedy_row_sum(V, t, k, take, dw) - uz) : uz;
+    const double un = (k2 == 0) ? V.lrt[t] - softplus(greedy_row_sum(V, t, k, take, dw) - uz) : uz;
+    V.uc[t] = un;
+    V.ub[t] = (1.0 - th) * un + th * V.ut[t];
   } else if (t < V.n + V.m) {
     const int64_t j = t - V.n;
     const double vz = V.vo[j];
-    V.vc[j] = (k2 == 1) ? V.lct[j] - softplus(greedy_col_sum(V, j, k, take, dw) - vz) : vz;
+    const double vn = (k2 == 1) ? V.lct[j] - softplus(greedy_col_sum(V, j, k, take, dw) - vz) : vz;
+    V.vc[j] = vn;
+    V.vb[j] = (1.0 - th) * vn + th * V.vt[j];
   }
+  if (t == 0) S->w_bar = (1.0 - th) * S->w_check + th * S->w_tilde;
 }
 
 // Warm-start check.  E(z) = |r(B) + e^u - r~|_1 + |c(B) + e^v - c~|_1 + ||B|_1 - s|
@@ -700,7 +755,7 @@ __global__ void sink_after_rows_kernel(SinkVecs V) {
   bool act = false;
   if (t < V.n) {
     const double u = V.u[t];
-    const double R = V.lrow[t];   // includes u_i
+    const double R = row_sum_of(V, t, V.fused);   // includes u_i
     const double lsum = V.dcol ? logaddexp(R, u + vd) : R;
     v[0] = fabs(safe_exp(lsum) - V.re[t]);
     V.uprev[t] = u;
@@ -743,7 +798,7 @@ __global__ void sink_after_cols_kernel(SinkVecs V) {
   bool act = false;
   if (t < V.m) {
     const double vj = V.v[t];
-    const double Cc = V.lcol[t];   // includes v_j
+    const double Cc = col_sum_of(V, t, V.fused);   // includes v_j
     const double lsum = V.drow ? logaddexp(Cc, vj + ud) : Cc;
     V.v[t] = clamp_log(V.lce[t] - (lsum - vj));
   } else if (t < V.m + V.n) {
