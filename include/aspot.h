@@ -71,6 +71,8 @@ typedef enum {
 #define POT_FLAG_WARM_CHECK 64    /* with u0 / v0: start from zero instead when E(z_warm) > E(0) (res->warm_used) */
 #define POT_FLAG_AUTOTUNE 128     /* aspot_solve_batched: tile shape of the batched pass from the autotune cache,
                                      else the fastest candidate timed on this batch (then cached) */
+#define POT_FLAG_STAGED 256       /* aspot_solve: run the iterations as separate kernels in CUDA graphs even where
+                                     the single-cluster loop applies (see pot_result.cluster_loop) */
 
 typedef struct {
   int64_t n, m;
@@ -153,7 +155,8 @@ typedef struct {            /* host struct filled by the solvers */
   int32_t warm_used;        /* 1 if the iterations started from (u0, v0, w0) */
   int32_t tile_rows;        /* aspot_solve_batched: rows x columns of the batched pass's tiles */
   int32_t tile_cols;
-  int32_t pad;
+  int32_t cluster_loop;     /* aspot_solve: 1 if the iterations ran in the single-cluster loop kernel (small
+                               problems with CUDA-core passes, no TRACE / PROFILE / STAGED flag), else 0 */
   double tune_ms;           /* aspot_solve_batched, POT_FLAG_AUTOTUNE: device time spent timing candidates
                                (0 when the shape came from the cache) */
 } pot_result;
@@ -191,7 +194,8 @@ POT_API pot_status pot_objective(const pot_problem* prob, const pot_plan* plan, 
 
 /* Log row and column sums of B(u, v, w): lrow[i] = log sum_j B_ij,
  * lcol[j] = log sum_i B_ij (device FP64, either may be NULL), and
- * *tot = |B|_1 (device FP64 scalar, may be NULL).  Enqueued only; w is
+ * *tot = |B|_1 (device FP64 scalar, may be NULL).  With lrow NULL and lcol
+ * given, one columns-only pass runs and *tot is the sum over the columns.  Enqueued only; w is
  * passed by value to a kernel, so the call may be captured into a CUDA graph.
  * If the tcgen05 pass gave up waiting on its pipeline, every output is NaN
  * and pot_pass_status reports POT_ETIMEOUT. */

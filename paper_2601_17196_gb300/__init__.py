@@ -35,6 +35,7 @@ from .binding import (  # noqa: F401
     FLAG_PROFILE,
     FLAG_WARM_CHECK,
     FLAG_AUTOTUNE,
+    FLAG_STAGED,
     autotune_set,
     autotune_lookup,
     autotune_clear,

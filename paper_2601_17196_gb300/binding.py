@@ -24,6 +24,7 @@ FLAG_FORCE_SIMT = 16
 FLAG_PROFILE = 32
 FLAG_WARM_CHECK = 64
 FLAG_AUTOTUNE = 128
+FLAG_STAGED = 256
 
 COST_DENSE_F32 = 0
 COST_SQEUCLID_BF16 = 1
@@ -92,7 +93,7 @@ class _Result(ct.Structure):
                 ("rounding_branch", ct.c_int32), ("nonfinite", ct.c_int32),
                 ("pass_ms", ct.c_double), ("pass_launches", ct.c_int64), ("kernel_launches", ct.c_int64),
                 ("err_warm", ct.c_double), ("err_zero", ct.c_double), ("warm_used", ct.c_int32),
-                ("tile_rows", ct.c_int32), ("tile_cols", ct.c_int32), ("pad", ct.c_int32),
+                ("tile_rows", ct.c_int32), ("tile_cols", ct.c_int32), ("cluster_loop", ct.c_int32),
                 ("tune_ms", ct.c_double)]
 
 
@@ -276,6 +277,7 @@ class SolveResult:
     tile_cols: int = 0
     tune_ms: float = 0.0
     decisions: Optional[np.ndarray] = None    # batched: per iteration took + 2 k + 8 k2 (first 1024)
+    cluster_loop: int = 0                      # 1: the iterations ran in the single-cluster loop kernel
 
 
 _side_streams = {}
@@ -426,7 +428,7 @@ def _solve(fn, prob, gamma, eps, max_iter, flags, check_every, p_tune, u0, v0, w
     return SolveResult(st, res.iters, res.objective, res.err_final, res.eps_stop, res.gamma, res.cost_scale,
                        res.mass, res.ms, res.rounding_branch, res.nonfinite, plan, trace,
                        res.pass_ms, res.pass_launches, res.kernel_launches, res.err_warm, res.err_zero,
-                       res.warm_used)
+                       res.warm_used, cluster_loop=res.cluster_loop)
 
 
 def aspot_solve(prob: DeviceProblem, gamma: float, eps: float, max_iter: int = 10000, flags: int = 0,
@@ -474,18 +476,21 @@ def pot_objective(prob: DeviceProblem, plan: Plan, gamma: float, ws: Optional[to
 
 
 def pot_marginals(prob: DeviceProblem, gamma: float, u: torch.Tensor, v: torch.Tensor, w: float,
-                  ws: Optional[torch.Tensor] = None, check: bool = True):
+                  ws: Optional[torch.Tensor] = None, check: bool = True, rows: bool = True, cols: bool = True):
     """Returns (log row sums, log column sums, total mass) of B(u, v, w).
     ``check``: synchronise and raise if the pass reported a stalled pipeline
     (pot_pass_status); without it the call only enqueues and the mass is
-    returned as a device tensor."""
+    returned as a device tensor.  ``rows`` / ``cols`` False: that side is not
+    computed (returned as None); with rows=False the pass is columns-only and
+    the mass is summed over the columns."""
     ws, need = _workspace(prob, 0, ws)
-    lrow = torch.empty(prob.n, dtype=torch.float64, device=prob.r.device)
-    lcol = torch.empty(prob.m, dtype=torch.float64, device=prob.r.device)
+    lrow = torch.empty(prob.n, dtype=torch.float64, device=prob.r.device) if rows else None
+    lcol = torch.empty(prob.m, dtype=torch.float64, device=prob.r.device) if cols else None
     tot = torch.empty(1, dtype=torch.float64, device=prob.r.device)
     side, cur = _stream()
     _check(lib().pot_marginals(ct.byref(prob.struct()), gamma, u.data_ptr(), v.data_ptr(), float(w),
-                               ct.c_void_p(ws.data_ptr()), need, lrow.data_ptr(), lcol.data_ptr(), tot.data_ptr(),
+                               ct.c_void_p(ws.data_ptr()), need, None if lrow is None else lrow.data_ptr(),
+                               None if lcol is None else lcol.data_ptr(), tot.data_ptr(),
                                ct.c_void_p(side.cuda_stream)))
     if not check:
         _finish(side, cur)

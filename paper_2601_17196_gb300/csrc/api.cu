@@ -59,6 +59,7 @@ struct Layout {
   size_t off_state = 0, off_red = 0, off_cnt = 0, off_stats = 0, off_xn = 0, off_yn = 0;
   size_t off_rowp = 0, off_colp = 0, off_u[kSlots] = {}, off_v[kSlots] = {};
   size_t off_rowA = 0, off_colA = 0, off_colB = 0;
+  size_t off_binst = 0;       // the single-cluster loop's instance record and stop counter
   size_t total = 0;
 };
 
@@ -96,7 +97,7 @@ Layout make_layout(const pot_problem* P, int flags, int nslots = kSlots) {
     L.ncolblk = L.sl.ncolblk;
     L.nrowblk = L.sl.dense_fast ? L.sl.nslots : L.sl.nrowblk;
   }
-  const int64_t vblk = vec_blocks(n + m + 2);
+  const int64_t vblk = std::max<int64_t>(vec_blocks(n + m + 2), loop_blocks_max(n + m + 2));
   const int64_t pass_ctas = std::max<int64_t>(L.sl.ncolblk * L.sl.nrowblk, L.use_tc ? L.tl.v1_units : 0);
   L.red_doubles = std::max<int64_t>(vblk * 12, pass_ctas) + 64;   // up to 9 sums + (max, sum) per block
   size_t o = 0;
@@ -106,8 +107,11 @@ Layout make_layout(const pot_problem* P, int flags, int nslots = kSlots) {
   L.off_stats = o; o = align_up(o + sizeof(double) * 8);
   L.off_xn = o; o = align_up(o + sizeof(float) * (n + 1));
   L.off_yn = o; o = align_up(o + sizeof(float) * (m + 1));
+  // column partials: also room for the CUDA-core tiles of the single-cluster
+  // loop, which are never fewer rows than the layout's H
+  const int64_t colblk = L.use_tc ? L.nrowblk : std::max<int64_t>(L.nrowblk, L.sl.nrowblk);
   L.off_rowp = o; o = align_up(o + sizeof(float2) * L.ncolblk * n);
-  L.off_colp = o; o = align_up(o + sizeof(float2) * L.nrowblk * m);
+  L.off_colp = o; o = align_up(o + sizeof(float2) * colblk * m);
   for (int k = kSlots - nslots; k < kSlots; ++k) { L.off_u[k] = o; o = align_up(o + sizeof(double) * (n + 2)); }
   for (int k = kSlots - nslots; k < kSlots; ++k) { L.off_v[k] = o; o = align_up(o + sizeof(double) * (m + 2)); }
   {
@@ -117,6 +121,7 @@ Layout make_layout(const pot_problem* P, int flags, int nslots = kSlots) {
     L.off_colA = o; o = align_up(o + sizeof(float2) * mp);
     L.off_colB = o; o = align_up(o + sizeof(float2) * mp);
   }
+  L.off_binst = o; o = align_up(o + sizeof(BInst) + 64);
   L.total = o;
   return L;
 }
@@ -135,6 +140,8 @@ struct Ctx {
   float4* rowA = nullptr;
   float2 *colA = nullptr, *colB = nullptr;
   double *lrow = nullptr, *lcol = nullptr;     // combined log-sums of the last row / column pass
+  BInst* binst = nullptr;                      // single-cluster loop: instance record
+  int* bndone = nullptr;                       // and its stop counter
   double* U[kSlots];
   double* V[kSlots];
   double cost_scale = 1.0;
@@ -222,6 +229,8 @@ pot_status bind(Ctx& X, const pot_problem* P, int flags, void* ws, size_t ws_byt
   X.rowA = (float4*)(X.ws + X.L.off_rowA);
   X.colA = (float2*)(X.ws + X.L.off_colA);
   X.colB = (float2*)(X.ws + X.L.off_colB);
+  X.binst = (BInst*)(X.ws + X.L.off_binst);
+  X.bndone = (int*)(X.ws + X.L.off_binst + ((sizeof(BInst) + 15) & ~size_t(15)));
   return POT_OK;
 }
 
@@ -278,7 +287,8 @@ pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true, bool combine
   // events inside a captured graph must be external event-record nodes
   if (X.L.use_tc) {
     CK(launch_pass_tc(d, X.L.tl, X.st, e0));
-    X.launches += 2;
+    // terms, (row-partial clear,) pass
+    X.launches += ((d.mode & PASS_ROWS) && X.L.tl.v3) || tc_swaps_cols(X.L.tl, d) ? 3 : 2;
   } else {
     if (d.mode & (PASS_ROWS | PASS_COLS | PASS_OBJ)) {
       launch_prep(d, d.n, d.m, X.st);
@@ -289,9 +299,14 @@ pot_status run_pass(Ctx& X, const PassDesc& d, bool profile = true, bool combine
     X.launches += 1;
   }
   if (e1) CK(cudaEventRecordWithFlags(e1, X.st, cudaEventRecordExternal));
+  // a transposed columns-only pass (large tcgen05 problems) leaves sw_nslots
+  // partials per column; the loop kernels' inline combine never sees one
+  const bool swapped = X.L.use_tc && tc_swaps_cols(X.L.tl, d);
+  if (swapped && !combine) return fail(POT_ECUDA, "internal: a transposed column pass needs the combine launch");
   if (combine && (d.mode & (PASS_ROWS | PASS_COLS))) {
-    launch_combine(X.rowp, X.L.ncolblk, d.n, (d.mode & PASS_ROWS) ? X.lrow : nullptr, X.colp, X.L.nrowblk, d.m,
-                   (d.mode & PASS_COLS) ? X.lcol : nullptr, d.done, X.st, d.skip, d.skip_if);
+    launch_combine(X.rowp, X.L.ncolblk, d.n, (d.mode & PASS_ROWS) ? X.lrow : nullptr, X.colp,
+                   swapped ? X.L.tl.sw_nslots : X.L.nrowblk, d.m, (d.mode & PASS_COLS) ? X.lcol : nullptr, d.done,
+                   X.st, d.skip, d.skip_if);
     X.launches += 1;
   }
   CKL();
@@ -453,6 +468,76 @@ pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, B
   if (graph) cudaGraphDestroy(graph);
   if (st == POT_OK && !done) st = fail(POT_ETIMEOUT, "device stop flag never set");
   return st;
+}
+
+// ------------------------------------------------ single-cluster loop ---
+// Problems up to kClusterEntries cost entries with CUDA-core passes iterate in
+// one thread-block cluster (cluster.cu): one launch per `per` iterations
+// instead of about ten dependent kernels per iteration.  Beyond about 512 x 512
+// the 16 SMs of one cluster do the passes more slowly than the whole GPU
+// (measured: 256^2 49 against 62 us per iteration, 512^2 68 against 72,
+// 1000^2 113 against 86).
+constexpr double kClusterEntries = 262144.0;
+
+// tile rows of the cluster loop: the CUDA-core layout's, raised so that a
+// column has at most 16 row-block partials for the epilogue CTA to combine
+int cluster_rows(int64_t n, int H) {
+  const int64_t h = ((n + 16 * 32 - 1) / (16 * 32)) * 32;
+  return (int)std::max<int64_t>(H, h);
+}
+
+bool use_cluster(const Ctx& X, const pot_params* p, const PassDesc& d) {
+  if (X.L.use_tc) return false;
+  if (p->flags & (POT_FLAG_STAGED | POT_FLAG_TRACE | POT_FLAG_PROFILE)) return false;
+  if ((double)X.P->n * (double)X.P->m > kClusterEntries) return false;
+  return cluster_loop_kind(d) != 0 && cluster_loop_size(d, X.L.sl.V) > 0;
+}
+
+pot_status cluster_drive(Ctx& X, const AspotVecs& V, const PassDesc& d, int per, int max_iter, bool greedy) {
+  cudaStreamCaptureStatus cs;
+  CK(cudaStreamIsCapturing(X.st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(POT_EINVAL, "the stream is being captured");
+  const pot_problem* P = X.P;
+  ClusterLoop A{};
+  A.P = d;
+  A.vecs = V;
+  A.inst = X.binst;
+  A.ndone = X.bndone;
+  A.V = X.L.sl.V;
+  A.H = cluster_rows(P->n, X.L.sl.H);
+  A.ncta = cluster_loop_size(d, A.V);
+  BInst hI;
+  memset(&hI, 0, sizeof(hI));
+  hI.n = P->n; hI.m = P->m;
+  hI.ntile = ((P->n + A.H - 1) / A.H) * ((P->m + 128 * A.V - 1) / (128 * A.V));
+  hI.X = P->X; hI.Y = P->Y; hI.d = P->d; hI.kind = P->kind; hI.ldx = P->ldx; hI.ldy = P->ldy;
+  hI.r = P->r; hI.c = P->c; hI.s = P->s; hI.cost_scale = X.cost_scale; hI.gC = d.gC;
+  hI.pu = V.uo; hI.pv = V.vo;
+  CK(cudaMemcpyAsync(X.binst, &hI, sizeof(BInst), cudaMemcpyHostToDevice, X.st));
+  CK(cudaMemsetAsync(X.bndone, 0, sizeof(int), X.st));
+  if (P->kind == POT_COST_DENSE_F32) {      // the per-pass terms read zero norms
+    CK(cudaMemsetAsync(X.xn, 0, sizeof(float) * (P->n + 1), X.st));
+    CK(cudaMemsetAsync(X.yn, 0, sizeof(float) * (P->m + 1), X.st));
+  }
+  CK(launch_cluster_enter(X.binst, X.S, X.st));
+  X.launches += 1;
+  int done = 0, launched = 0;
+  pot_status st = POT_OK;
+  while (launched < max_iter + per) {
+    cudaError_t e = launch_cluster_loop(A, per, greedy ? 1 : 0, launched == 0 ? 1 : 0, X.st);
+    if (e != cudaSuccess) { st = fail(POT_ECUDA, "cluster loop launch: %s", cudaGetErrorString(e)); break; }
+    X.launches += 1;
+    launched += per;
+    e = cudaMemcpyAsync(&done, &X.binst->done, sizeof(int), cudaMemcpyDeviceToHost, X.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(X.st);
+    if (e != cudaSuccess) { st = fail(POT_ECUDA, "stop flag: %s", cudaGetErrorString(e)); break; }
+    if (done) break;
+  }
+  if (st != POT_OK) return st;
+  CK(launch_cluster_exit(X.binst, X.S, X.st));
+  X.launches += 1;
+  if (!done) return fail(POT_ETIMEOUT, "device stop flag never set");
+  return POT_OK;
 }
 
 pot_status do_round(Ctx& X, double gamma, const double* u, const double* v, pot_plan* plan, int* branch) {
@@ -682,6 +767,12 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
     if (k != 2) {
       PassDesc p3a = p3;
       p3a.mode = (k == 0) ? PASS_COLS : PASS_ROWS;
+      // after a u-step the column sums at z^t enter E_t alone, so this pass may
+      // run transposed.  The v-step's Greenkhorn pass keeps the kernel's own
+      // column side: its sums decide the argmin phi(z^) < phi(z_check), a
+      // near-tie that the other summation order tipped to z_check in two thirds
+      // of the v-steps at n = 32768, each then paying the pass at z_check.
+      p3a.transpose = 1;
       if ((q = run_pass(X, p3a, true, !V.fused)) != POT_OK) return q;
     }
     PassDesc p3b = p3;
@@ -731,21 +822,26 @@ pot_status aspot_solve(const pot_problem* prob, const pot_params* params, void* 
   const int per = params->check_every > 0 ? params->check_every : 24;
   auto aspot_passes = [](int k) { return k == 2 ? 2 : 3; };      // P1, P2 (, P3a); P3b is not timed
   auto greedy_passes = [](int) { return 2; };                     // P1, P2; the passes at z^t are not timed
-  // z_bar of the first iteration; later ones are formed by the iteration's last kernel
-  launch_aspot_extrap(V, X.st); X.launches += 1;
-  // from here the loop kernels combine the partials themselves when there are
-  // few per entry (small problems, where a launch costs more than the work);
-  // with many (the tcgen05 pass at large n: one per 256-row block) the wide
-  // combine kernel, eight threads per entry, is faster
-  V.fused = fuse_combine(X);
-  CKL();
-  {
+  const bool cluster = use_cluster(X, params, d);
+  if (cluster) {
+    Nvtx range("aspot: iterations (cluster loop)");
+    s = cluster_drive(X, V, d, per, params->max_iter, params->block_rule == 1);
+  } else {
+    // z_bar of the first iteration; later ones are formed by the iteration's last kernel
+    launch_aspot_extrap(V, X.st); X.launches += 1;
+    // from here the loop kernels combine the partials themselves when there are
+    // few per entry (small problems, where a launch costs more than the work);
+    // with many (the tcgen05 pass at large n: one per 256-row block) the wide
+    // combine kernel, eight threads per entry, is faster
+    V.fused = fuse_combine(X);
+    CKL();
     Nvtx range("aspot: iterations");
     const int k0 = RS ? RS->t % 3 : 0;      // the cyclic rule goes on with block t mod 3
     if (params->block_rule == 1) s = drive(X, per, params->max_iter, greedy_passes, body_greedy);
     else s = drive(X, per, params->max_iter, aspot_passes, body, k0);
   }
   if (s != POT_OK) return s;
+  res->cluster_loop = cluster ? 1 : 0;
   if ((s = read_state(X, h)) != POT_OK) return s;
   CK(cudaMemcpyAsync(plan->w, &X.S->w_out, sizeof(double), cudaMemcpyDeviceToDevice, X.st));
   res->iters = h.t;
@@ -960,11 +1056,13 @@ pot_status pot_marginals(const pot_problem* prob, double gamma, const double* u,
   // w (by value in a kernel argument), the reduction counters and the stall flag
   launch_marginals_setup(X.S, w, X.cnt, X.st);
   PassDesc d = base_desc(X, gamma);
-  d.mode = PASS_ROWS | (lcol ? PASS_COLS : 0);
+  // rows unless only the columns are asked for (then |B|_1 comes from the columns)
+  d.mode = ((lrow || !lcol) ? PASS_ROWS : 0) | (lcol ? PASS_COLS : 0);
+  d.transpose = 1;
   d.arow0 = u; d.bcol0 = v; d.aoff0 = &X.S->w_out;
   if ((s = run_pass(X, d)) != POT_OK) return s;
-  launch_marginals_out(prob->n, prob->m, X.lrow, lcol ? X.lcol : nullptr, lrow, lcol, X.red, X.cnt, tot,
-                       &X.S->tc_err, X.st);
+  launch_marginals_out(prob->n, prob->m, (d.mode & PASS_ROWS) ? X.lrow : nullptr, lcol ? X.lcol : nullptr, lrow,
+                       lcol, X.red, X.cnt, tot, &X.S->tc_err, X.st);
   CKL();
   return POT_OK;
 }

@@ -70,6 +70,22 @@ struct Lse {
   __device__ __forceinline__ double value() const { return s > 0.0 ? m + log(s) : POT_NEG_BIG; }
 };
 
+// e^R of a log-sum R that comes from FP32 pass partials (whose own error is
+// ~1e-7 relative and more): FP32 accuracy (~2^-22 relative) over the FP64
+// range in a handful of FP64 operations instead of a full FP64 exponential,
+// which costs dozens of instructions on this GPU's narrow FP64 pipe.  With
+// y = R log2 e = k + f (k = floor y, f in [0, 1)): e^R = 2^k 2^f, 2^f from the
+// FP32 hardware ex2, 2^k written into the exponent field.  R <= -700 and NaN
+// give 0 (the log-domain convention for log 0, as for an FP64 exp below it).
+__device__ __forceinline__ double exp_sum(double R) {
+  if (!(R > -700.0)) return 0.0;
+  if (R > 709.7) return INFINITY;
+  const double y = R * 1.4426950408889634;
+  const double k = floor(y);
+  const float p = ex2((float)(y - k));                 // in [1, 2)
+  return (double)p * __hiloint2double(((int)k + 1023) << 20, 0);
+}
+
 __device__ __forceinline__ double softplus(double x) {   // log(1 + e^x)
   return x > 0.0 ? x + log1p(exp(-x)) : log1p(exp(x));
 }

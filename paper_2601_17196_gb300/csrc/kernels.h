@@ -30,16 +30,27 @@ struct TcLayout {
   int v3;                            // hot-loop kernel (pass_tc3.cu) serves rows / columns passes
   int64_t G, T, ntiles2, nrb2, nslots, n_pad2;
   int64_t n_pad, m_pad;              // padding of the per-pass row / column terms
+  // columns-only passes as rows-only passes of the transposed problem (the
+  // point sets swapped): its layout, and sw_nslots partials per column
+  int swap;
+  int64_t sw_G, sw_T, sw_ntiles2, sw_nrb2, sw_nslots, sw_rows_pad, sw_cols_pad;
   int ok;
 };
 TcLayout tc_layout(int64_t n, int64_t m, int d);
 bool tc_supported(const PassDesc& P);
 cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st, cudaEvent_t before_main = nullptr);
+// the pass runs transposed: its column partials number L.sw_nslots
+inline bool tc_swaps_cols(const TcLayout& L, const PassDesc& P) {
+  return L.v3 && L.swap && P.transpose && P.mode == PASS_COLS;
+}
 bool tc3_applicable(int d);
 int tc3_tile_cols();
 void tc3_fill_layout(TcLayout& L, int64_t n, int64_t m, int num_sms);
+void tc3_fill_layout_swap(TcLayout& L, int64_t n, int64_t m, int num_sms);
 cudaError_t launch_pass_tc3(const PassDesc& P, const TcLayout& L, const CUtensorMap& mx, const CUtensorMap& my,
                             cudaStream_t st);
+cudaError_t launch_pass_tc3_cols_swapped(const PassDesc& P, const TcLayout& L, const CUtensorMap& my_rows,
+                                         const CUtensorMap& mx_cols, cudaStream_t st);
 
 // --------------------------------------------------------- device state --
 struct DevState {
@@ -138,8 +149,29 @@ struct BatchPass {
 void launch_pass_simt_batched(const BatchPass& B, cudaStream_t st);
 void launch_prep_batched(const BatchPass& B, cudaStream_t st);
 
+// ------------------------------------------- single-cluster ASPOT loop --
+// One small problem iterated by one thread-block cluster (cluster.cu): the
+// CTAs share each pass's tiles, CTA 0 runs the per-instance update of the
+// batched solver on the single-instance solver's own vectors.
+struct ClusterLoop {
+  PassDesc P;        // base pass: problem, logit multiplier, FP32 terms, partial buffers
+  AspotVecs vecs;    // the solver's vectors
+  BInst* inst;       // device record of the instance (entered from / left to DevState)
+  int* ndone;        // device int the bodies count the instance in when it stops
+  int H, V;          // tile rows (a multiple of 32); 128-column groups per tile (1 or 2)
+  int ncta;          // CTAs of the cluster (8 or 16)
+};
+int cluster_loop_kind(const PassDesc& P);           // 0: not supported; 1 / 3 dense FP32 (aligned / not), 2 FP32 points d <= 4
+int cluster_loop_size(const PassDesc& P, int V);    // largest resident cluster, 0 if none
+cudaError_t launch_cluster_enter(BInst* I, const DevState* S, cudaStream_t st);
+cudaError_t launch_cluster_exit(const BInst* I, DevState* S, cudaStream_t st);
+cudaError_t launch_cluster_loop(const ClusterLoop& A, int iters, int greedy, int first, cudaStream_t st);
+
 constexpr int kVecThreads = 256;
 inline int vec_blocks(int64_t len) { return (int)((len + kVecThreads - 1) / kVecThreads); }
+// the solver loops' O(n + m) kernels run 64-thread blocks up to this length (vec.cu)
+constexpr int64_t kLoopSmallLen = 32768;
+inline int64_t loop_blocks_max(int64_t len) { return (len + 63) / 64; }   // bound for reduction buffers
 
 // prologue: masses, minima, finiteness of r and c -> S (sum_rt/ct reused as raw masses)
 void launch_marg_stats(const double* r, const double* c, int64_t n, int64_t m, double* red,

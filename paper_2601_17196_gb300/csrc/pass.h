@@ -45,6 +45,8 @@ struct PassDesc {
   int* err;              // set to 1 when a bounded pipeline wait of the pass ran out
   uint64_t wait_ns;      // bound of each pipeline wait (ns)
   int stall;             // test hook: the hot-loop tcgen05 pass withholds its first accumulator hand-off
+  int transpose;         // a columns-only tcgen05 pass may run as the rows-only kernel of the transposed
+                         // problem (where the layout allows it, TcLayout::swap)
 };
 
 // True when the pass must not run (the solve has stopped, or its skip

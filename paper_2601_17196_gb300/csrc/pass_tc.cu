@@ -399,7 +399,12 @@ TcLayout tc_layout(int64_t n, int64_t m, int d) {
       sms = 152;
     }
     tc3_fill_layout(L, n, m, sms);
+    tc3_fill_layout_swap(L, n, m, sms);
     if (L.n_pad2 > L.n_pad) L.n_pad = L.n_pad2;
+    if (L.swap) {                   // the transposed pass's terms share the row / column term buffers
+      if (L.sw_rows_pad > L.n_pad) L.n_pad = L.sw_rows_pad;
+      if (L.sw_cols_pad > L.m_pad) L.m_pad = L.sw_cols_pad;
+    }
     L.ncolblk = L.nslots;
     L.nrowblk = L.nrb2;
   } else {
@@ -420,12 +425,20 @@ bool tc_supported(const PassDesc& P) {
 }
 
 cudaError_t launch_pass_tc(const PassDesc& P, const TcLayout& L, cudaStream_t st, cudaEvent_t before_main) {
-  launch_prep(P, L.n_pad, L.m_pad, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (before_main && (e = cudaEventRecordWithFlags(before_main, st, cudaEventRecordExternal)) != cudaSuccess) return e;
   CUtensorMap mx, my;
   const int md = P.mode;
+  cudaError_t e;
+  if (tc_swaps_cols(L, P)) {
+    // rows of the transposed problem: A tiles from Y, B tiles from X
+    if (before_main && (e = cudaEventRecordWithFlags(before_main, st, cudaEventRecordExternal)) != cudaSuccess) return e;
+    if (!make_map(&my, P.Y, P.m, P.d, P.ldy, 128) || !make_map(&mx, P.X, P.n, P.d, P.ldx, tc3_tile_cols()))
+      return cudaErrorInvalidValue;
+    return launch_pass_tc3_cols_swapped(P, L, my, mx, st);
+  }
+  launch_prep(P, L.n_pad, L.m_pad, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (before_main && (e = cudaEventRecordWithFlags(before_main, st, cudaEventRecordExternal)) != cudaSuccess) return e;
   if (L.v3 && !(md & (PASS_MAXCOST | PASS_OBJ))) {
     if (!make_map(&mx, P.X, P.n, P.d, P.ldx, 128) || !make_map(&my, P.Y, P.m, P.d, P.ldy, tc3_tile_cols()))
       return cudaErrorInvalidValue;

@@ -417,6 +417,38 @@ __global__ void tc3_clear_rows_kernel(PassDesc P, float2* row_part, int64_t coun
   if (t < count) row_part[t] = make_float2(POT_NEG_BIGF, 0.f);
 }
 
+// Per-pass terms of the transposed problem (rows = the columns j, columns =
+// the rows i), the arithmetic of prep_kernel with the two sides exchanged:
+//   rowA[j] = (hi, lo of (b_j - gC |y_j|^2) log2 e, |y_j|^2, 0)
+//   colA[i] = (hi, lo of (a_i + aoff - gC |x_i|^2) log2 e)
+// padding entries are log 0.
+__global__ void tc3_prep_swap_kernel(PassDesc P, int64_t rows_pad, int64_t cols_pad) {
+  if (pass_off(P)) return;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool use1 = P.sel && *P.sel;
+  const double* arow = use1 ? P.arow1 : P.arow0;
+  const double* bcol = use1 ? P.bcol1 : P.bcol0;
+  const double* aoffp = use1 ? P.aoff1 : P.aoff0;
+  if (t < rows_pad) {
+    float4 o = make_float4(POT_NEG_BIGF, 0.f, 0.f, 0.f);
+    if (t < P.m) {
+      const float yn = P.yn[t];
+      HiLo hl = split_hilo(((double)bcol[t] - P.gC * (double)yn) * kL2E3);
+      o = make_float4(hl.hi, hl.lo, yn, 0.f);
+    }
+    P.rowA[t] = o;
+  } else if (t < rows_pad + cols_pad) {
+    const int64_t i = t - rows_pad;
+    float2 A = make_float2(POT_NEG_BIGF, 0.f);
+    if (i < P.n) {
+      const float xn = P.xn[i];
+      HiLo hl = split_hilo((arow[i] + (aoffp ? *aoffp : 0.0) - P.gC * (double)xn) * kL2E3);
+      A = make_float2(hl.hi, hl.lo);
+    }
+    P.colA[i] = A;
+  }
+}
+
 template <int MODE>
 cudaError_t launch3(const PassDesc& P, const TcLayout& L, const CUtensorMap& mx, const CUtensorMap& my,
                     cudaStream_t st) {
@@ -437,6 +469,24 @@ cudaError_t launch3(const PassDesc& P, const TcLayout& L, const CUtensorMap& mx,
 bool tc3_applicable(int d) { return d == 64 || d == 128; }
 int tc3_tile_cols() { return BN3; }
 
+// The columns-only pass runs as the rows-only kernel on the transposed
+// problem: a columns-only tile pays the per-tile transposing reduction across
+// the warp, the quadrant merge and a partial per 256 rows, a rows-only tile
+// reduces along its own registers and keeps running sums.  Its layout is the
+// one of (m, n); each column then has sw_nslots partials (the CTAs sharing a
+// row block of the transposed problem) instead of one per 256 rows, so only
+// where the combine kernel reads them (more than 32 row blocks; the loop
+// kernels' inline combine expects one per row block).
+static void tc3_fill_swap(TcLayout& L, int64_t n, int64_t m, int num_sms) {
+  TcLayout S{};
+  S.m_pad = 0;
+  tc3_fill_layout(S, m, n, num_sms);
+  L.sw_G = S.G; L.sw_T = S.T; L.sw_ntiles2 = S.ntiles2; L.sw_nrb2 = S.nrb2; L.sw_nslots = S.nslots;
+  L.sw_rows_pad = S.nrb2 * BM3;
+  L.sw_cols_pad = S.ntiles2 * BN3;
+  L.swap = L.nrb2 > 32 ? 1 : 0;
+}
+
 void tc3_fill_layout(TcLayout& L, int64_t n, int64_t m, int num_sms) {
   L.nrb2 = (n + BM3 - 1) / BM3;
   L.ntiles2 = (m + BN3 - 1) / BN3;
@@ -451,6 +501,27 @@ void tc3_fill_layout(TcLayout& L, int64_t n, int64_t m, int num_sms) {
   L.nslots = slots;
   L.n_pad2 = L.nrb2 * BM3;
   if (L.ntiles2 * BN3 > L.m_pad) L.m_pad = L.ntiles2 * BN3;
+}
+
+void tc3_fill_layout_swap(TcLayout& L, int64_t n, int64_t m, int num_sms) { tc3_fill_swap(L, n, m, num_sms); }
+
+cudaError_t launch_pass_tc3_cols_swapped(const PassDesc& P, const TcLayout& L, const CUtensorMap& my_rows,
+                                         const CUtensorMap& mx_cols, cudaStream_t st) {
+  {
+    const int64_t tot = L.sw_rows_pad + L.sw_cols_pad;
+    tc3_prep_swap_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, L.sw_rows_pad, L.sw_cols_pad);
+  }
+  PassDesc Q = P;
+  Q.n = P.m; Q.m = P.n;
+  Q.X = P.Y; Q.Y = P.X; Q.ldx = P.ldy; Q.ldy = P.ldx; Q.xn = P.yn; Q.yn = P.xn;
+  Q.mode = PASS_ROWS;
+  Q.row_part = P.col_part;            // [sw_nslots][m]: the column partials
+  Q.col_part = nullptr;
+  TcLayout S = L;
+  S.G = L.sw_G; S.T = L.sw_T; S.ntiles2 = L.sw_ntiles2; S.nrb2 = L.sw_nrb2; S.nslots = L.sw_nslots;
+  const int64_t cnt = L.sw_nslots * Q.n;
+  tc3_clear_rows_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(Q, Q.row_part, cnt);
+  return launch3<W_R>(Q, S, my_rows, mx_cols, st);
 }
 
 cudaError_t launch_pass_tc3(const PassDesc& P, const TcLayout& L, const CUtensorMap& mx, const CUtensorMap& my,

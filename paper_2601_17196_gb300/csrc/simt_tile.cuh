@@ -62,6 +62,8 @@ __device__ __forceinline__ void rows4_reduce(float (&v)[4], int lane) {
 // MT: 0 = the pass mode is read at run time (any mode, including the
 // objective and max-cost passes); 1 / 2 / 3 = rows + columns / rows /
 // columns fixed at compile time, which drops the other modes' registers.
+// The per-pass terms (rowA, colA) are read through L2: the single-cluster
+// loop writes them in the same kernel, on another SM, before a barrier.
 template <int KIND, int V, int DMAX, bool VEC, int MT = 0>
 __device__ __forceinline__ void simt_tile(const PassDesc& P, int H, int64_t cb, int64_t rb, int64_t rstride,
                                           int64_t cstride, int64_t red_idx) {
@@ -89,7 +91,7 @@ const bool want_rows = MT == 0 ? (P.mode & PASS_ROWS) != 0 : (MT == 1 || MT == 2
     const int k = q >> 2, e = q & 3;
     const int64_t j = col0 + 128 * k + 4 * lane + e;
     const bool ok = j < P.m;
-    const float2 cb2 = (ok && need_pot) ? P.colA[j] : make_float2(POT_NEG_BIGF, 0.f);
+    const float2 cb2 = (ok && need_pot) ? __ldcg(P.colA + j) : make_float2(POT_NEG_BIGF, 0.f);
     bh[q] = cb2.x; bl[q] = cb2.y;
     colS[q] = 0.f;
     qv[q] = (want_obj && ok) ? P.colB[j].y : 0.f;
@@ -118,7 +120,7 @@ const bool want_rows = MT == 0 ? (P.mode & PASS_ROWS) != 0 : (MT == 1 || MT == 2
       const bool rowv = i < rend;
       HiLo ah;
       if (rowv && need_pot) {
-        const float4 ra = P.rowA[i];
+        const float4 ra = __ldcg(P.rowA + i);
         ah.hi = ra.x; ah.lo = ra.y;
       } else {
         ah.hi = rowv ? 0.f : POT_NEG_BIGF; ah.lo = 0.f;

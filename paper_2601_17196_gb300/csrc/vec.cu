@@ -71,7 +71,7 @@ __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* c
   __shared__ double sh[NV][kVecThreads / 32];
   __shared__ double st[NV];
   __shared__ int amlast;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     const double x = warp_sum_d(v[k]);
@@ -82,7 +82,7 @@ __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* c
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
       double s = 0.0;
-      for (int w = 0; w < kVecThreads / 32; ++w) s += sh[k][w];
+      for (int w = 0; w < nw; ++w) s += sh[k][w];
       part[(int64_t)blockIdx.x * NV + k] = s;
     }
     __threadfence();
@@ -92,7 +92,7 @@ __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* c
   __syncthreads();
   if (!amlast) return false;
   __threadfence();
-  for (int k = warp; k < NV; k += kVecThreads / 32) {
+  for (int k = warp; k < NV; k += nw) {
     double s = 0.0;
     for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (int64_t)b * NV + k);
     s = warp_sum_d(s);
@@ -118,7 +118,7 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   __shared__ double st[NV > 0 ? NV : 1];
   __shared__ double slse;
   __shared__ int amlast;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
     const double y = warp_sum_d(v[k]);
@@ -133,7 +133,7 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   __syncthreads();
   if (warp == 0) {
     // block (max, sum) of the NW warp partials: one exp per lane, not a serial chain
-    const double wm = (lane < NW && ssm[lane] > 0.0) ? smx[lane] : -INFINITY;
+    const double wm = (lane < nw && ssm[lane] > 0.0) ? smx[lane] : -INFINITY;
     double bm = wm;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
@@ -143,7 +143,7 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         double a = 0.0;
-        for (int w = 0; w < NW; ++w) a += sh[k][w];
+        for (int w = 0; w < nw; ++w) a += sh[k][w];
         part[(int64_t)blockIdx.x * NP + k] = a;
       }
       part[(int64_t)blockIdx.x * NP + NV] = bs > 0.0 ? bm : -INFINITY;
@@ -156,7 +156,7 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   __syncthreads();
   if (!amlast) return false;
   __threadfence();
-  for (int k = warp; k < NV; k += NW) {
+  for (int k = warp; k < NV; k += nw) {
     double a = 0.0;
     for (int b2 = lane; b2 < (int)gridDim.x; b2 += 32) a += __ldcg(part + (int64_t)b2 * NP + k);
     a = warp_sum_d(a);
@@ -171,7 +171,7 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   if (lane == 0) smx[warp] = gm;
   __syncthreads();
   gm = -INFINITY;
-  for (int w = 0; w < NW; ++w) gm = fmax(gm, smx[w]);
+  for (int w = 0; w < nw; ++w) gm = fmax(gm, smx[w]);
   double gs = 0.0;
   if (gm > -INFINITY)
     for (int b2 = threadIdx.x; b2 < (int)gridDim.x; b2 += blockDim.x) {
@@ -183,7 +183,7 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0;
-    for (int w = 0; w < NW; ++w) a += ssm[w];
+    for (int w = 0; w < nw; ++w) a += ssm[w];
     slse = (gm > -INFINITY && a > 0.0) ? gm + log(a) : POT_NEG_BIG;
   }
   __syncthreads();
@@ -347,7 +347,7 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
   if (t < V.n) {
     const double ub = V.ub[t];
     const double R = row_sum_of(V, t, V.fused);
-    const double rB = safe_exp(R), eu = safe_exp(ub);
+    const double rB = exp_sum(R), eu = safe_exp(ub);
     const double g = rB + eu - V.rt[t];
     const double un = ub - g / Lth;
     V.ug[t] = ub + th * (un - V.ut[t]);
@@ -359,7 +359,7 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
     const int64_t j = t - V.n;
     const double vb = V.vb[j];
     const double Cc = col_sum_of(V, j, V.fused);
-    const double cB = safe_exp(Cc), ev = safe_exp(vb);
+    const double cB = exp_sum(Cc), ev = safe_exp(vb);
     const double g = cB + ev - V.ct[j];
     const double vn = vb - g / Lth;
     V.vg[j] = vb + th * (vn - V.vt[j]);
@@ -468,7 +468,7 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     else if (take && k == 2) R = clamp_log(R + dw);
     xr = R;
     act = k == 2;                      // log |B|_1 is needed by the w step only
-    const double rB = safe_exp(R), eu = safe_exp(uz);
+    const double rB = exp_sum(R), eu = safe_exp(uz);
     v[0] = fabs(rB + eu - V.rt[t]);
     v[1] = rB;
     V.uo[t] = uz;
@@ -483,7 +483,7 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     double Cc = col_sum_of(V, j, V.fused && (k == 0 || !take));
     if (take && k == 1) Cc = clamp_log(Cc + (V.vh[j] - V.vg[j]));
     else if (take && k == 2) Cc = clamp_log(Cc + dw);
-    const double cB = safe_exp(Cc), ev = safe_exp(vz);
+    const double cB = exp_sum(Cc), ev = safe_exp(vz);
     v[0] = fabs(cB + ev - V.ct[j]);
     V.vo[j] = vz;
     const double vn = (k == 1) ? V.lct[j] - softplus(Cc - vz) : vz;
@@ -894,13 +894,17 @@ __global__ void marginals_out_kernel(int64_t n, int64_t m, const double* lrow_in
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool bad = err && *err;          // a pass that gave up waiting: its sums are invalid
   double v[1] = {0};
+  // |B|_1 from the row sums, or from the column sums of a columns-only pass (lrow_in NULL)
   if (t < n) {
-    const double R = bad ? (double)NAN : lrow_in[t];
-    if (lrow) lrow[t] = R;
-    v[0] = safe_exp(R);
+    if (lrow_in) {
+      const double R = bad ? (double)NAN : lrow_in[t];
+      if (lrow) lrow[t] = R;
+      v[0] = safe_exp(R);
+    }
   } else if (t < n + m) {
     const double Cc = bad ? (double)NAN : (lcol_in ? lcol_in[t - n] : 0.0);
     if (lcol) lcol[t - n] = Cc;
+    if (!lrow_in) v[0] = safe_exp(Cc);
   }
   double tot[1];
   if (reduce_last<1>(v, red, counter, tot) && threadIdx.x == 0 && tot_out) *tot_out = bad ? (double)NAN : tot[0];
@@ -958,26 +962,33 @@ void launch_aspot_init(const AspotVecs& V, const double* r, const double* c, dou
                        const double* u0, const double* v0, double w0, cudaStream_t st) {
   aspot_init_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, r, c, eps_s, u0, v0, w0);
 }
+// Block size of the solver loops' O(n + m) kernels: 64 threads (two warps)
+// while that still gives at most a few blocks per SM, so the FP64 updates,
+// whose instructions each hold an SM sub-partition's narrow FP64 pipe for many
+// cycles, spread over as many SMs as the problem allows; 256 beyond.
+int loop_threads(int64_t len) { return len <= kLoopSmallLen ? 64 : kVecThreads; }
+unsigned loop_blocks(int64_t len) { const int t = loop_threads(len); return (unsigned)((len + t - 1) / t); }
+
 void launch_aspot_extrap(const AspotVecs& V, cudaStream_t st) {
-  aspot_extrap_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  aspot_extrap_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
 }
 void launch_aspot_after_grad(const AspotVecs& V, cudaStream_t st) {
-  aspot_after_grad_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  aspot_after_grad_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
 }
 void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st) {
-  aspot_after_greenkhorn_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, k);
+  aspot_after_greenkhorn_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V, k);
 }
 void launch_aspot_greedy_pick(const AspotVecs& V, cudaStream_t st) {
-  aspot_greedy_pick_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  aspot_greedy_pick_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
 }
 void launch_aspot_greedy_final(const AspotVecs& V, cudaStream_t st) {
-  aspot_greedy_final_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  aspot_greedy_final_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
 }
 void launch_aspot_greedy_apply(const AspotVecs& V, cudaStream_t st) {
-  aspot_greedy_apply_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  aspot_greedy_apply_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
 }
 void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st) {
-  aspot_after_final_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, k);
+  aspot_after_final_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V, k);
 }
 void launch_aspot_start_eval(const AspotVecs& V, const double* u, const double* v, int slot, cudaStream_t st) {
   aspot_start_eval_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, u, v, slot);
@@ -993,11 +1004,11 @@ void launch_sink_init(const SinkVecs& V, const double* r, const double* c, doubl
   sink_init_kernel<<<vec_blocks(V.n + V.m + 1), kVecThreads, 0, st>>>(V, r, c, eps_s, s);
 }
 void launch_sink_after_rows(const SinkVecs& V, cudaStream_t st) {
-  sink_after_rows_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  sink_after_rows_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
   sink_restore_kernel<<<vec_blocks(V.n + 1), kVecThreads, 0, st>>>(V);
 }
 void launch_sink_after_cols(const SinkVecs& V, cudaStream_t st) {
-  sink_after_cols_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V);
+  sink_after_cols_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
 }
 void launch_round_r1(const RoundVecs& V, cudaStream_t st) {
   round_r1_kernel<<<vec_blocks(V.n), kVecThreads, 0, st>>>(V);

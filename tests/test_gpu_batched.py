@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 def test_batched_matches_oracle_and_single_solves():
     insts = W.batch_3d(seed=4, count=6, nmin=64, nmax=520)
     probs = [pkg.DeviceProblem.from_workload(pb, device="cuda") for pb in insts]
-    res = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000)
+    res = pkg.aspot_solve_batched(probs, 0.05, 1e-3, max_iter=5000, decisions=True)
     for pb, dp, r in zip(insts, probs, res):
         C = O.sqeuclid_cost(pb.X, pb.Y, 0.0)
         conv = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=5000)
@@ -21,8 +21,12 @@ def test_batched_matches_oracle_and_single_solves():
         # E_t is not monotone near the threshold: the summation order (tile shape)
         # can move its first crossing by a few iterations
         assert abs(r.iters - conv.iters) <= 4
-        # same number of iterations in the oracle: the iterates (and objectives) agree
-        ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=r.iters, no_stop=True)
+        # same number of iterations in the oracle, with the batched solve's argmin
+        # decisions replayed (a near-tie of phi(z^) against phi(z_check) may go the
+        # other way in FP32, as for the single solve below): the objectives agree
+        assert r.iters <= len(r.decisions)
+        ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=r.iters, no_stop=True,
+                            forced_hat=list((r.decisions & 1) > 0))
         assert abs(r.objective - ora.objective) <= 1e-5 * abs(ora.objective)
         single = pkg.aspot_solve(dp, 0.05, 1e-3, max_iter=5000, flags=pkg.FLAG_TRACE)
         # E_t is not monotone near the threshold: rounding-level differences between

@@ -124,6 +124,45 @@ def _rows_lse(X, Y, rows, cs, gamma, u, v, w):
     return out
 
 
+@pytest.mark.parametrize("n,m,d", [(9000, 8300, 128), (8193, 9001, 64)])
+def test_columns_only_pass_runs_transposed(n, m, d):
+    """Above 32 row blocks of 256 a columns-only pass runs as the rows-only
+    kernel on the transposed problem (Y as the row operand): its column sums
+    against the oracle on sampled columns, against the two-sided pass on all
+    columns, and the mass summed over the columns."""
+    pb = W.cloud_32k(11, n=n, m=m, d=d)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    X, Y = W.from_bf16_bits(pb.X_bf16), W.from_bf16_bits(pb.Y_bf16)
+    g = np.random.default_rng(n)
+    cols = np.sort(g.choice(m, 128, replace=False))
+    cs, gam = 1.0 / 4000.0, 0.02
+    dp.cost_scale = cs
+    for lo, hi in ((-14.0, -10.0), (-60.0, -5.0)):
+        u, v, w = g.uniform(lo, hi, n), g.uniform(lo, hi, m), 3.0
+        none, lcc, totc = pkg.pot_marginals(dp, gam, _t(u), _t(v), w, rows=False)
+        assert none is None
+        lr, lc, tot = pkg.pot_marginals(dp, gam, _t(u), _t(v), w)
+        ec = _rows_lse(Y, X, cols, cs, gam, v, u, w)
+        assert np.abs(_np(lcc)[cols] - ec).max() <= 3e-5 + 2e-7 * np.abs(ec).max()
+        assert np.abs(_np(lcc) - _np(lc)).max() <= 3e-5 + 2e-7 * np.abs(_np(lc)).max()
+        assert totc == pytest.approx(tot, rel=3e-5)
+
+
+def test_transposed_column_passes_in_the_loop_match_simt():
+    """ASPOT at n = 9000 (cyclic rule: the pass at z^t after a u-step is
+    columns-only and runs transposed at this size), 30 fixed iterations
+    against the CUDA-core path: potentials within 2e-4 (1 + |u|)."""
+    pb = W.cloud_32k(12, n=9000, m=8800)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    K = 30
+    a = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP)
+    b = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_FORCE_SIMT)
+    assert a.iters == b.iters == K and a.status == b.status == 0
+    for x, y in ((_np(a.plan.u), _np(b.plan.u)), (_np(a.plan.v), _np(b.plan.v))):
+        np.testing.assert_allclose(x, y, rtol=0, atol=2e-4 * (1 + np.abs(y).max()))
+    assert a.err_final == pytest.approx(b.err_final, rel=2e-2)
+
+
 def test_cloud_32k_full_size_sampled():
     """The bench's workload at its full size (n = m = 32768, d = 128 BF16) in the
     launch configuration the bench times: (1) one fused pass with given
@@ -146,6 +185,9 @@ def test_cloud_32k_full_size_sampled():
     ec = _rows_lse(Y, X, cols, cs, gam, v, u, w)
     assert np.abs(_np(lr)[rows] - er).max() <= 3e-5 + 2e-7 * np.abs(er).max()
     assert np.abs(_np(lc)[cols] - ec).max() <= 3e-5 + 2e-7 * np.abs(ec).max()
+    # the columns-only pass of the solve's loop (transposed at this size)
+    _, lcc, _ = pkg.pot_marginals(dp, gam, _t(u), _t(v), w, rows=False)
+    assert np.abs(_np(lcc)[cols] - ec).max() <= 3e-5 + 2e-7 * np.abs(ec).max()
     # (2) the solve the bench times (cost normalised by its maximum, computed on the GPU)
     dp.cost_scale = 0.0
     res = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=20000)
