@@ -671,7 +671,8 @@ def scaling_study(args, dev="cuda"):
                                                            flags=pkg.FLAG_NO_STOP),
                           1, 1, min_s=0.0)
         rows.append({"n": n, "ms": ms[0], "us_per_iter": 1e3 * ms[0] / 1500, "iters": r.iters,
-                     "launches_per_iter": r.kernel_launches / 1500.0, "E": r.err_final})
+                     "launches_per_iter": r.kernel_launches / 1500.0, "E": r.err_final,
+                     "loop": "single-cluster" if r.cluster_loop else "staged"})
     clocks = clk.stop()
     x = np.log([q["n"] for q in rows])
     y = np.log([q["ms"] for q in rows])
@@ -759,11 +760,20 @@ def small_study(args, quick=False, dev="cuda"):
     r, ms, clocks = _timed(stream, lambda: pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter),
                            warm, steps)
     t = sum(ms) / len(ms)
-    with torch.cuda.stream(stream):        # pass times from one extra, profiled solve
+    # the same solve with the iterations as separate kernels (the single-cluster
+    # loop's alternative), and the pass times from one extra, profiled solve
+    # (profiling times each pass of the staged loop)
+    rs, ms_s, _ = _timed(stream, lambda: pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter,
+                                                         flags=pkg.FLAG_STAGED), warm, steps)
+    t_s = sum(ms_s) / len(ms_s)
+    with torch.cuda.stream(stream):
         prof = pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_PROFILE)
     pms = prof.pass_ms / max(prof.pass_launches, 1)
     aspot = {"solver": "aspot", "gamma": r.gamma, "iters": r.iters, "time_to_eps_ms": t, "objective": r.objective,
              "converged": r.status == 0, "us_per_iter": 1e3 * t / r.iters, "clocks": clocks,
+             "loop": "single-cluster" if r.cluster_loop else "staged",
+             "staged_loop": {"iters": rs.iters, "time_to_eps_ms": t_s, "us_per_iter": 1e3 * t_s / rs.iters,
+                             "launches_per_iter": rs.kernel_launches / rs.iters},
              "kernel": pkg.pass_kernel(dp, pkg.FLAG_PROFILE), "pass_us": 1e3 * pms,
              "launches_per_iter": r.kernel_launches / r.iters,
              "roofline": {"bound": "latency", "note": "0.25 MiB cost: a pass is a few microseconds of launch and "

@@ -62,6 +62,7 @@ struct DevState {
   double sum_rt, sum_ct;
   double m2, sum_p, sum_q, kappa, log_k1, obj;
   double A_over_g;
+  double theta_next;         // theta_{t+1}, formed once per iteration by the gradient kernel
   double e_start[2];         // E(z_warm), E(0) for the warm-start check
   int t, take_hat, done, max_iter, nonfinite, tc_err;
   int warm_used, pad3;

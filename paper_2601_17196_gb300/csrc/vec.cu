@@ -373,6 +373,9 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
     const double wn = S->w_bar - gw / Lth;
     S->w_grave = S->w_bar + th * (wn - S->w_tilde);
     S->w_tilde = wn;
+    // theta_{t+1} once here: the final kernel needs it in every thread (for
+    // z_bar^{t+1}), where an FP64 square root per thread would be costly
+    S->theta_next = th * (sqrt(th * th + 4.0) - th) / 2.0;
     if (S->t == 0) S->phi_check = tot[0] + tot[1] - S->w_bar * S->s;   // phi(z_check^0), z_bar^0 = z_check^0
     if (tot[2] != 0.0 || !isfinite(wn)) S->nonfinite = 1;
   }
@@ -456,10 +459,9 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   // z^t = z^: the sums of block k's side come from the Greenkhorn pass at
   // z_grave in closed form (the other side was computed at z^ by P3a)
   const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
-  // theta_{t+1} (each block reads theta_t before the last block updates it):
-  // the extrapolation z_bar^{t+1} of the next iteration is formed here
-  const double th0 = S->theta;
-  const double thn = th0 * (sqrt(th0 * th0 + 4.0) - th0) / 2.0;
+  // theta_{t+1} (formed by the gradient kernel of this iteration): the
+  // extrapolation z_bar^{t+1} of the next iteration is formed here
+  const double thn = S->theta_next;
   if (t < V.n) {
     const double uz = take ? uz_hat[t] : V.uc[t];
     // rows: from the pass at z^t (P3a for k = 1, P3b when z^t = z_check), else closed form
