@@ -103,13 +103,22 @@ __host__ __device__ __forceinline__ int64_t dense_owner(int64_t u, int64_t G, in
 // Per-warp shared-memory ring of cost chunks filled with cp.async (16 bytes
 // per lane and copy); kDStages chunks of 4 rows x 256 columns per warp, so
 // kDStages - 1 loads are in flight while one chunk is reduced.  Each lane
-// reads back exactly the 16-byte slots it copied, so the ring needs no
-// synchronisation beyond the lane's own cp.async.wait_group.
+// reads back exactly the 16-byte slots it copied.  Beside it, the chunk's four
+// row terms (hi, lo), copied by lanes 0..3 in the same group and read by the
+// whole warp, so the warp synchronises after the wait and before a stage is
+// refilled.  (Loaded from global memory at their use, the row terms were the
+// pass's main long-scoreboard stall.)  2 CTAs per SM: 2 x (16 KB static +
+// 96.75 KB ring + 1 KB reserved) fits the 228 KB of an SM.
 constexpr int kDStages = 3;
-constexpr size_t kDenseRingBytes = (size_t)kWarps * kDStages * 4 * 256 * sizeof(float);
+constexpr size_t kDenseCostRingBytes = (size_t)kWarps * kDStages * 4 * 256 * sizeof(float);
+constexpr size_t kDenseRingBytes = kDenseCostRingBytes + (size_t)kWarps * kDStages * 4 * sizeof(float2);
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -122,8 +131,9 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __shared__ float sS[kWarps][256];
   __shared__ float sM[kWarps][256];
-  extern __shared__ float4 dring[];                      // [kWarps][kDStages][4 rows][64]
+  extern __shared__ float4 dring[];                      // [kWarps][kDStages][4 rows][64], then row terms
   float4* ring = dring + (size_t)warp * kDStages * 4 * 64;
+  float2* aring = reinterpret_cast<float2*>(dring + (size_t)kWarps * kDStages * 4 * 64) + warp * kDStages * 4;
   const float g2 = (float)(P.gC * kL2E);
   const unsigned long long NG = pk2(-g2, -g2);
   // persistent: CTA c owns units [c U / G, (c+1) U / G) of the panel-major
@@ -169,6 +179,11 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
         else *dst = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+    if (lane < 4) {                                      // the row terms (hi, lo) of the chunk
+      float2* dst = aring + st * 4 + lane;
+      if (b + lane < rend) cp_async8(dst, P.rowA + b + lane);
+      else *dst = make_float2(POT_NEG_BIGF, 0.f);
+    }
     cp_commit();
   };
   const int64_t first = row0 + 4 * warp;
@@ -181,9 +196,11 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
   for (int64_t ci = 0; ci < nchunks; ++ci) {
     const int64_t base = first + 32 * ci;
     const int64_t nci = ci + kDStages - 1;
+    __syncwarp();                                        // every lane is done with the stage refilled now
     if (nci < nchunks) issue(first + 32 * nci, (int)(nci % kDStages));
     else cp_commit();
     cp_wait_ring();                                      // chunk ci has landed
+    __syncwarp();                                        // and its row terms, copied by lanes 0..3
     float4 cur[4][2];
     {
       const int st = (int)(ci % kDStages);
@@ -196,9 +213,7 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
     float lg[4][8];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int64_t i = base + r;
-      float4 ra = make_float4(POT_NEG_BIGF, 0.f, 0.f, 0.f);
-      if (i < rend) ra = P.rowA[i];
+      const float2 ra = aring[(int)(ci % kDStages) * 4 + r];
       const unsigned long long AH = pk2(ra.x, ra.x), AL = pk2(ra.y, ra.y);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
