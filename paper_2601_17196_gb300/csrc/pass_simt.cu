@@ -113,9 +113,8 @@ constexpr int kDStages = 3;
 constexpr size_t kDenseCostRingBytes = (size_t)kWarps * kDStages * 4 * 256 * sizeof(float);
 constexpr size_t kDenseRingBytes = kDenseCostRingBytes + (size_t)kWarps * kDStages * 4 * sizeof(float2);
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
+__device__ __forceinline__ void cp_async16s(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -168,16 +167,21 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
   for (int q = 0; q < 8; ++q) { cM[q] = POT_NEG_BIGF; cS[q] = 0.f; }
 
   // chunk ci of this warp: rows row0 + 4 warp + 32 ci + r, in ring stage ci % kDStages
+  // one running row pointer and 32-bit shared addresses per chunk
+  const float* const cbase = P.C + col0 + 4 * lane;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring + lane);
   auto issue = [&](int64_t b, int st) {
+    const float* src = cbase + b * P.ldc;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int64_t i = b + r;
+      const bool rv = b + r < rend;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        float4* dst = ring + (st * 4 + r) * 64 + k * 32 + lane;
-        if (i < rend && gv[k]) cp_async16(dst, P.C + i * P.ldc + col0 + 128 * k + 4 * lane);
-        else *dst = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int slot = (st * 4 + r) * 64 + k * 32;          // in float4, before the lane
+        if (rv && gv[k]) cp_async16s(ring_s + (uint32_t)slot * 16u, src + 128 * k);
+        else ring[slot + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      src += P.ldc;
     }
     if (lane < 4) {                                      // the row terms (hi, lo) of the chunk
       float2* dst = aring + st * 4 + lane;
@@ -237,14 +241,16 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
       for (int r = 0; r < 4; ++r) {
         const bool ok = rm[r] > -1.0e29f;
         const unsigned long long NM = pk2(ok ? -rm[r] : 0.f, ok ? -rm[r] : 0.f);
-        float s = 0.f;
+        unsigned long long sp = 0ull;                    // packed (even, odd) partial sums; bits 0 = 0.0f
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           float a, b;
           upk2(add2(pk2(lg[r][2 * p], lg[r][2 * p + 1]), NM), a, b);
-          s += ex2(a) + ex2(b);
+          sp = add2(sp, pk2(ex2(a), ex2(b)));
         }
-        sm[r] = s;
+        float s0, s1;
+        upk2(sp, s0, s1);
+        sm[r] = s0 + s1;
       }
       rows4_reduce<false>(sm, lane);
       if ((lane & 7) == 0) {
@@ -254,15 +260,28 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
       }
     }
     if (COLS) {
+      // columns q, q + 1 of the lane as FP32x2 pairs (as the logits were
+      // formed): shift, sum over the chunk's 4 rows, rescale of the running sum.
+      // A running max of log 0 (-big) rescales by ex2(-huge) = 0; a column whose
+      // entries are all log 0 keeps its state (ok).
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float cmx = fmaxf(max3f(lg[0][q], lg[1][q], lg[2][q]), lg[3][q]);
-        const float nm = fmaxf(cM[q], cmx);
-        if (nm > -1.0e29f) {
-          const float sc = cM[q] > -1.0e29f ? ex2(cM[q] - nm) : 0.f;
-          cS[q] = cS[q] * sc + ((ex2(lg[0][q] - nm) + ex2(lg[1][q] - nm)) + (ex2(lg[2][q] - nm) + ex2(lg[3][q] - nm)));
-          cM[q] = nm;
+      for (int p = 0; p < 4; ++p) {
+        const int q0 = 2 * p, q1 = 2 * p + 1;
+        const float nm0 = max3f(max3f(lg[0][q0], lg[1][q0], lg[2][q0]), lg[3][q0], cM[q0]);
+        const float nm1 = max3f(max3f(lg[0][q1], lg[1][q1], lg[2][q1]), lg[3][q1], cM[q1]);
+        const unsigned long long NMp = pk2(-nm0, -nm1);
+        unsigned long long e[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float a, b;
+          upk2(add2(pk2(lg[r][q0], lg[r][q1]), NMp), a, b);
+          e[r] = pk2(ex2(a), ex2(b));
         }
+        const unsigned long long sum = add2(add2(e[0], e[1]), add2(e[2], e[3]));
+        float n0, n1;
+        upk2(fma2(pk2(cS[q0], cS[q1]), pk2(ex2(cM[q0] - nm0), ex2(cM[q1] - nm1)), sum), n0, n1);
+        if (nm0 > -1.0e29f) { cS[q0] = n0; cM[q0] = nm0; }
+        if (nm1 > -1.0e29f) { cS[q1] = n1; cM[q1] = nm1; }
       }
     }
   }
