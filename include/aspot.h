@@ -156,7 +156,7 @@ typedef struct {            /* host struct filled by the solvers */
   int32_t tile_rows;        /* aspot_solve_batched: rows x columns of the batched pass's tiles */
   int32_t tile_cols;
   int32_t cluster_loop;     /* aspot_solve: 1 if the iterations ran in the single-cluster loop kernel (small
-                               problems with CUDA-core passes, no TRACE / PROFILE / STAGED flag), else 0 */
+                               problems with CUDA-core passes, no PROFILE / STAGED flag), else 0 */
   double tune_ms;           /* aspot_solve_batched, POT_FLAG_AUTOTUNE: device time spent timing candidates
                                (0 when the shape came from the cache) */
 } pot_result;

@@ -488,7 +488,7 @@ int cluster_rows(int64_t n, int H) {
 
 bool use_cluster(const Ctx& X, const pot_params* p, const PassDesc& d) {
   if (X.L.use_tc) return false;
-  if (p->flags & (POT_FLAG_STAGED | POT_FLAG_TRACE | POT_FLAG_PROFILE)) return false;
+  if (p->flags & (POT_FLAG_STAGED | POT_FLAG_PROFILE)) return false;
   if ((double)X.P->n * (double)X.P->m > kClusterEntries) return false;
   return cluster_loop_kind(d) != 0 && cluster_loop_size(d, X.L.sl.V) > 0;
 }
@@ -506,6 +506,7 @@ pot_status cluster_drive(Ctx& X, const AspotVecs& V, const PassDesc& d, int per,
   A.V = X.L.sl.V;
   A.H = cluster_rows(P->n, X.L.sl.H);
   A.ncta = cluster_loop_size(d, A.V);
+  A.trace4 = V.trace ? &X.S->trace[0][0] : nullptr;
   BInst hI;
   memset(&hI, 0, sizeof(hI));
   hI.n = P->n; hI.m = P->m;

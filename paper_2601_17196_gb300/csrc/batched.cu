@@ -605,6 +605,7 @@ POT_API pot_status aspot_solve_batched(const pot_problem* probs, int32_t count, 
   V.lrow = lrow; V.lcol = lcol; V.ndone = ndone;
   V.uo = U[8]; V.vo = Vv[8]; V.fc = U[9]; V.gc = Vv[9];
   V.trace = (unsigned char*)(ws + L.off_trace);
+  V.trace4 = nullptr;
 
   BatchPass B{};
   B.kind = probs[0].kind; B.H = G.H; B.W = G.W; B.Ntot = L.N; B.Mtot = L.M; B.tiles = dtiles; B.ntiles = G.T;

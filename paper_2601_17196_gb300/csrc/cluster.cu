@@ -345,6 +345,7 @@ cudaError_t launch_cluster_loop(const ClusterLoop& A, int iters, int greedy, int
   V.lrow = W.lrow; V.lcol = W.lcol;
   V.ndone = A.ndone;
   V.trace = nullptr;
+  V.trace4 = A.trace4;
   const int kind = cluster_loop_kind(P);
   if (kind == 1)
     return A.V == 1 ? cl_launch<COST_DENSE_F32, 1, 0, true>(P, B, V, A.ncta, iters, greedy, first, st)

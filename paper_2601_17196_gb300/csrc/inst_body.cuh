@@ -78,6 +78,8 @@ struct BVecs {
   const double *lrow, *lcol;
   int* ndone;
   unsigned char* trace;               // [count][kBTrace]: took + 2 k + 8 k2 per iteration
+  double* trace4;                     // single solve: rows [4096][4] of (E_t, phi(z^t), phi(z_check^{t+1}),
+                                      // took + 2 k + 8 k2), the single-instance solver's trace, or NULL
 };
 
 // The threads that update one instance.  The bodies below are written against
@@ -261,6 +263,10 @@ static __device__ void b_after_final_body(const BVecs& V, int inst, int k, T& tm
     I.E = E;
     I.tot = v[1];
     if (V.trace && tm.writer() && I.t < kBTrace) V.trace[(int64_t)inst * kBTrace + I.t] = (unsigned char)(take + 10 * k);
+    if (V.trace4 && tm.writer()) {
+      double* tr = V.trace4 + (int64_t)(I.t & 4095) * 4;
+      tr[0] = E; tr[1] = I.phi_z; tr[2] = I.phi_check; tr[3] = (double)take;
+    }
     const double th = I.theta;
     I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
     I.t = I.t + 1;
@@ -422,6 +428,10 @@ static __device__ void b_greedy_final_body(const BVecs& V, int inst, T& tm) {
     I.E = E;
     I.tot = v[1];
     if (V.trace && tm.writer() && I.t < kBTrace) V.trace[(int64_t)inst * kBTrace + I.t] = (unsigned char)(take + 2 * I.kg + 8 * k2);
+    if (V.trace4 && tm.writer()) {
+      double* tr = V.trace4 + (int64_t)(I.t & 4095) * 4;
+      tr[0] = E; tr[1] = I.phi_z; tr[2] = ph; tr[3] = (double)(take + 2 * I.kg + 8 * k2);
+    }
     const double th = I.theta;
     I.theta = th * (sqrt(th * th + 4.0) - th) / 2.0;
     I.t = I.t + 1;

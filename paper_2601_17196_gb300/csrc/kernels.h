@@ -161,6 +161,7 @@ struct ClusterLoop {
   int* ndone;        // device int the bodies count the instance in when it stops
   int H, V;          // tile rows (a multiple of 32); 128-column groups per tile (1 or 2)
   int ncta;          // CTAs of the cluster (8 or 16)
+  double* trace4;    // DevState::trace rows to fill (POT_FLAG_TRACE), or NULL
 };
 int cluster_loop_kind(const PassDesc& P);           // 0: not supported; 1 / 3 dense FP32 (aligned / not), 2 FP32 points d <= 4
 int cluster_loop_size(const PassDesc& P, int V);    // largest resident cluster, 0 if none

@@ -13,6 +13,8 @@
 namespace pot {
 namespace simt {
 
+using tcx::pk2; using tcx::upk2; using tcx::add2; using tcx::fma2; using tcx::max3f;
+
 constexpr int kThreads = 256;
 constexpr int kWarps = 8;
 constexpr double kL2E = 1.4426950408889634;
@@ -200,6 +202,10 @@ const bool want_rows = MT == 0 ? (P.mode & PASS_ROWS) != 0 : (MT == 1 || MT == 2
       }
     }
 
+    // Entries of log 0 carry logits near -1e30; shifted by a real maximum
+    // their ex2 is 0, so the sums need no per-entry test; a row or column
+    // whose entries are all log 0 is caught by its maximum.  Adjacent columns
+    // q, q + 1 of a lane go through the shifts and sums as FP32x2 pairs.
     if (want_rows) {
       // the chunk's four rows reduced together by the transposing butterfly
       float mx[R], sm[R], rm[R];
@@ -214,33 +220,44 @@ const bool want_rows = MT == 0 ? (P.mode & PASS_ROWS) != 0 : (MT == 1 || MT == 2
       for (int rr = 0; rr < R; ++rr) rm[rr] = __shfl_sync(0xffffffffu, mx[0], 8 * rr);
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) {
-        float ssum = 0.f;
+        const unsigned long long NM = pk2(-rm[rr], -rm[rr]);
+        unsigned long long sp = 0ull;               // packed partial sums; bits 0 = 0.0f
 #pragma unroll
-        for (int q = 0; q < NC; ++q) ssum += (lg[rr][q] > -1.0e29f) ? ex2(lg[rr][q] - rm[rr]) : 0.f;
-        sm[rr] = ssum;
+        for (int q = 0; q < NC; q += 2) {
+          float a, b;
+          upk2(add2(pk2(lg[rr][q], lg[rr][q + 1]), NM), a, b);
+          sp = add2(sp, pk2(ex2(a), ex2(b)));
+        }
+        float s0, s1;
+        upk2(sp, s0, s1);
+        sm[rr] = s0 + s1;
       }
       rows4_reduce<false>(sm, lane);                // lane 8r: row r's sum in sm[0]
       if ((lane & 7) == 0) {
         const int64_t i = ib + (int64_t)kWarps * (lane >> 3);
-        if (i < rend) P.row_part[cb * rstride + i] = make_float2(mx[0], sm[0]);
+        if (i < rend) P.row_part[cb * rstride + i] = make_float2(mx[0], mx[0] > -1.0e29f ? sm[0] : 0.f);
       }
     }
     if (want_cols) {
-      // exact per-column log-sum-exp: one rescale per chunk, one ex2 per entry
+      // exact per-column log-sum-exp: the running (max, sum) rescaled once per
+      // chunk (by ex2(old max - new max): 0 from log 0, 1 when unchanged)
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        float cmx = colM[q];
+      for (int q = 0; q < NC; q += 2) {
+        const float nm0 = max3f(max3f(lg[0][q], lg[1][q], lg[2][q]), lg[3][q], colM[q]);
+        const float nm1 = max3f(max3f(lg[0][q + 1], lg[1][q + 1], lg[2][q + 1]), lg[3][q + 1], colM[q + 1]);
+        const unsigned long long NMp = pk2(-nm0, -nm1);
+        unsigned long long e[R];
 #pragma unroll
-        for (int rr = 0; rr < R; ++rr) cmx = fmaxf(cmx, lg[rr][q]);
-        if (cmx > -1.0e29f) {
-          if (cmx > colM[q]) {
-            colS[q] = (colM[q] > -1.0e29f) ? colS[q] * ex2(colM[q] - cmx) : 0.f;
-            colM[q] = cmx;
-          }
-#pragma unroll
-          for (int rr = 0; rr < R; ++rr)
-            if (lg[rr][q] > -1.0e29f) colS[q] += ex2(lg[rr][q] - cmx);
+        for (int rr = 0; rr < R; ++rr) {
+          float a, b;
+          upk2(add2(pk2(lg[rr][q], lg[rr][q + 1]), NMp), a, b);
+          e[rr] = pk2(ex2(a), ex2(b));
         }
+        const unsigned long long sum = add2(add2(e[0], e[1]), add2(e[2], e[3]));
+        float n0, n1;
+        upk2(fma2(pk2(colS[q], colS[q + 1]), pk2(ex2(colM[q] - nm0), ex2(colM[q + 1] - nm1)), sum), n0, n1);
+        if (nm0 > -1.0e29f) { colS[q] = n0; colM[q] = nm0; }
+        if (nm1 > -1.0e29f) { colS[q + 1] = n1; colM[q + 1] = nm1; }
       }
     }
   }

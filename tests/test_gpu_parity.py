@@ -116,13 +116,19 @@ def test_marginals_sqeuclid(kind, d):
 
 # ----------------------------------------------------------- solvers ---
 
-def test_aspot_fixed_iterations_match_oracle():
+# the small solves run in the single-cluster loop unless FLAG_STAGED asks for
+# the separate kernels: both loops are held to the same bars
+LOOPS = [pytest.param(0, id="cluster"), pytest.param(pkg.FLAG_STAGED, id="staged")]
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_aspot_fixed_iterations_match_oracle(loop):
     pb = W.small_dense(3, n=200, m=233)
     C = pb.C.astype(np.float64)
     K = 60
-    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_TRACE,
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_TRACE | loop,
                           check_every=9)
-    assert res.iters == K
+    assert res.iters == K and res.cluster_loop == (0 if loop else 1)
     took = res.trace[:, 3] > 0.5
     ora = O.aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=K, no_stop=True, forced_hat=took,
                   record=True)
@@ -156,16 +162,17 @@ def _near_tie(dec, k, mass=1.5, delta=1e-5):
     return dmax - dec[k] <= 1e-12 + 2 * err
 
 
-def test_aspot_greedy_fixed_iterations_match_oracle():
+@pytest.mark.parametrize("loop", LOOPS)
+def test_aspot_greedy_fixed_iterations_match_oracle(loop):
     """Greedy block rule (the choice in Theorem 3's proof): 60 iterations with
     the oracle replaying the GPU's argmin and block decisions; every decision
     the free FP64 run takes differently before the runs part is a near-tie."""
     pb = W.small_dense(3, n=200, m=233)
     C = pb.C.astype(np.float64)
     K = 60
-    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_TRACE,
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=K, flags=pkg.FLAG_NO_STOP | pkg.FLAG_TRACE | loop,
                           check_every=9, block_rule=pkg.BLOCK_GREEDY)
-    assert res.iters == K
+    assert res.iters == K and res.cluster_loop == (0 if loop else 1)
     took, k, k2 = _greedy_codes(res.trace)
     assert set(k.tolist()) <= {0, 1, 2} and set(k2.tolist()) <= {0, 1, 2}
     assert len(set(k.tolist())) >= 2            # the rule is not a fixed block on this instance
@@ -195,7 +202,8 @@ def _first_split_is_near_tie(free, took, k, k2):
     return True
 
 
-def test_aspot_greedy_converged_matches_oracle():
+@pytest.mark.parametrize("loop", LOOPS)
+def test_aspot_greedy_converged_matches_oracle(loop):
     """Greedy rule to the stop threshold on the 256-point workload.  The
     oracle replays the GPU's decisions for the GPU's iteration count: the
     objectives agree to 1e-5 relative, the oracle's E_t is below the
@@ -203,9 +211,9 @@ def test_aspot_greedy_converged_matches_oracle():
     from the GPU's decisions only at a near-tie."""
     pb = W.small_dense(0)
     C = pb.C.astype(np.float64)
-    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=5000, flags=pkg.FLAG_TRACE,
+    res = pkg.aspot_solve(_dev(pb), pb.gamma, pb.eps, max_iter=5000, flags=pkg.FLAG_TRACE | loop,
                           block_rule=pkg.BLOCK_GREEDY)
-    assert res.status == 0
+    assert res.status == 0 and res.cluster_loop == (0 if loop else 1)
     assert res.err_final <= res.eps_stop
     took, k, k2 = _greedy_codes(res.trace)
     ora = O.solve_aspot(C, pb.r, pb.c, pb.s, pb.eps, pb.gamma, max_iter=res.iters, no_stop=True,
