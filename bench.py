@@ -65,8 +65,10 @@ def _args():
                          "prints it; greedy: the block with the largest decrease of phi)")
     ap.add_argument("--no-greedy", action="store_true",
                     help="headline: skip the greedy-block-rule solves measured beside the cyclic ones")
-    ap.add_argument("--mode", default="solve", choices=["solve", "pass"],
-                    help="'pass': time only the fused row+column pass (for ncu captures of that kernel)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "pass", "iters"],
+                    help="'pass': time only the fused row+column pass (for ncu captures of that kernel); "
+                         "'iters': ASPOT solves of exactly --max-iter iterations at size --n (for launch lists "
+                         "of the solver loop)")
     ap.add_argument("--workload", default="cloud_32k",
                     choices=["cloud_32k", "dense_4096", "scaling_e4", "batch_3d", "warmstart", "small_dense",
                              "registration", "ws_train"],
@@ -518,6 +520,37 @@ def run_pass_only(args):
         return
     print(json.dumps({"mode": "pass", "n": args.n, "ms_per_pass_incl_combine": ms,
                       "tflops": 2.0 * args.n * args.n * D_FULL / (ms * 1e-3) / 1e12}), flush=True)
+
+
+def run_iters_only(args):
+    """--warmup untimed and --steps timed ASPOT solves of exactly --max-iter
+    iterations (no stop test) on the cloud workload (or, with --workload
+    dense_4096, the dense FP32 cost at gamma 0.03) at size n."""
+    import torch
+    import paper_2601_17196_gb300 as pkg
+    import pot_workloads as W
+    dense = args.workload == "dense_4096"
+    pb = W.dense_4096(0, n=args.n, gamma=0.03) if dense else W.cloud_32k(0, n=args.n)
+    dp = pkg.DeviceProblem.from_workload(pb, device="cuda")
+    rule = 1 if args.block_rule == "greedy" else 0
+    stream = torch.cuda.Stream()
+    solve = lambda: pkg.aspot_solve(dp, pb.gamma, pb.eps, max_iter=args.max_iter, flags=pkg.FLAG_NO_STOP,
+                                    block_rule=rule)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            solve()
+        torch.cuda.synchronize()
+        e0, e1 = _ev(), _ev()
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"mode": "iters", "workload": "dense" if dense else "cloud", "n": args.n,
+                      "block_rule": args.block_rule, "iters": res.iters, "ms_per_solve": ms,
+                      "us_per_iter": 1e3 * ms / max(res.iters, 1), "launches_per_solve": res.kernel_launches,
+                      "loop": "single-cluster" if res.cluster_loop else "staged"}), flush=True)
 
 
 def _ev():
@@ -1010,6 +1043,9 @@ def main():
         return
     if args.mode == "pass":
         run_pass_only(args)
+        return
+    if args.mode == "iters":
+        run_iters_only(args)
         return
     if args.workload == "batch_3d":
         print(json.dumps(batched_study(args)), flush=True)

@@ -419,7 +419,14 @@ pot_status drive(Ctx& X, int per, int max_iter, PassesPerIter passes_per_iter, B
     X.pass_ord = 0;
     CK(cudaStreamBeginCapture(X.st, cudaStreamCaptureModeThreadLocal));
     pot_status s = POT_OK;
-    for (int it = 0; it < per && s == POT_OK; ++it) s = body((it + k0) % 3);
+    {
+      // kernel-to-kernel edges of the graph become programmatic ones (each
+      // kernel's blocks are scheduled while its predecessor runs and wait for
+      // it on the device), except in profiled solves, whose timing events sit
+      // between the kernels
+      pdl_scope pdl(!X.prof);
+      for (int it = 0; it < per && s == POT_OK; ++it) s = body((it + k0) % 3);
+    }
     per_graph_launches = X.launches - l0;
     X.launches = l0;
     cudaGraph_t g2 = nullptr;

@@ -36,6 +36,18 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
+// Programmatic dependent launch.  A kernel that a solver loop launches with
+// the programmatic-serialisation attribute may be scheduled while its
+// predecessor in the stream still runs: pdl_wait() returns once that
+// predecessor has completed and its writes are visible (at once for a kernel
+// launched without the attribute), and pdl_release() lets the successor's
+// blocks be scheduled.  Such a kernel calls pdl_wait() before its first access
+// to device memory, so every kernel of the chain still sees all earlier ones
+// complete; only the launch latency overlaps.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() { pdl_wait(); pdl_release(); }
+
 // Maxima that keep a NaN (fmaxf / fmax drop it): a NaN anywhere in the cost
 // must reach the prologue's finiteness check through the max-cost pass.
 __device__ __forceinline__ float nanmaxf(float a, float b) { return (a > b || a != a) ? a : b; }

@@ -9,6 +9,34 @@
 
 namespace pot {
 
+// ------------------------------------------------------------- launches --
+// Launches of the staged solver loops.  While pdl_scope is alive on the host
+// thread (set around the capture of a loop's CUDA graph), launch_k adds the
+// programmatic-serialisation attribute: the kernel's blocks may be scheduled
+// as soon as its predecessor's blocks have all called pdl_release(); the
+// kernel itself starts with pdl_enter() (common.cuh), which waits for the
+// predecessor to complete.  Kernels launched through launch_k call it first.
+bool pdl_active();
+struct pdl_scope {
+  bool prev;
+  explicit pdl_scope(bool on);
+  ~pdl_scope();
+};
+template <class... KA, class... A>
+inline void launch_k(void (*kern)(KA...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_active() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // ---------------------------------------------------------------- passes --
 struct SimtLayout {
   int V; int H; int64_t ncolblk, nrowblk;   // generic tiles: ncolblk x nrowblk CTAs of H x 128V

@@ -38,7 +38,14 @@ namespace {
 //   colA[j] = (hi, lo of (b_j - gC |y_j|^2) log2 e),  colB[j] = (|y_j|^2, q_j)
 // (no norm terms for a dense cost).  Entries past n / m (padding) are log 0.
 // In max-cost mode the tensor-core pass reads the norms through the same slots.
-__global__ void prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad) {
+__global__ void prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad, int release_first) {
+  // release_first: the pass that follows is scheduled while this kernel still
+  // waits for the loop kernel before it.  Not before the persistent dense
+  // pass, whose fixed share of the work per CTA wants every CTA placed at once
+  // (CTAs that found an SM still held by the loop kernel would start late).
+  if (release_first) pdl_release();
+  pdl_wait();
+  if (!release_first) pdl_release();
   if (pass_off(P)) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool use1 = P.sel && *P.sel;
@@ -92,12 +99,6 @@ __global__ void prep_kernel(PassDesc P, int64_t n_pad, int64_t m_pad) {
 
 using tcx::pk2; using tcx::upk2; using tcx::add2; using tcx::fma2; using tcx::max3f;
 
-__global__ void clear_parts_kernel(float2* a, int64_t cnt, const int* done, const int* skip, int skip_if) {
-  if ((done && *done) || (skip && *skip == skip_if)) return;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < cnt) a[t] = make_float2(POT_NEG_BIGF, 0.f);
-}
-
 __host__ __device__ __forceinline__ int64_t dense_owner(int64_t u, int64_t G, int64_t U) { return ((u + 1) * G - 1) / U; }
 
 // Per-warp shared-memory ring of cost chunks filled with cp.async (16 bytes
@@ -125,6 +126,10 @@ __device__ __forceinline__ void cp_wait_ring() { asm volatile("cp.async.wait_gro
 
 template <int MODE>   // 0: rows + columns, 1: rows, 2: columns
 __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, SimtLayout DL) {
+  // no early release: the loop kernel that follows spreads its FP64 work one block
+  // per SM, which holds only for blocks placed on an idle GPU, not on the few
+  // SMs a draining pass frees first
+  pdl_wait();
   if (pass_off(P)) return;
   constexpr bool ROWS = MODE != 2, COLS = MODE != 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -304,6 +309,9 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
       for (int w = 0; w < kWarps; ++w)
         if (sM[w][t] > -1.0e29f) S = fmaf(sS[w][t], ex2(sM[w][t] - Km), S);
       P.col_part[slot * P.m + j] = make_float2(Km, S);
+      // the panel's last segment marks the slots no segment of it writes empty
+      if (seg_end == (panel + 1) * DL.nrg)
+        for (int64_t e = slot + 1; e < DL.nslots; ++e) P.col_part[e * P.m + j] = make_float2(POT_NEG_BIGF, 0.f);
     }
     __syncthreads();            // shared memory is reused by the next segment
   }
@@ -312,6 +320,10 @@ __global__ void __launch_bounds__(kThreads, 2) dense_pass_kernel(PassDesc P, Sim
 
 template <int KIND, int V, int DMAX, bool VEC>
 __global__ void __launch_bounds__(kThreads) pass_simt_kernel(PassDesc P, int H) {
+  // no early release: the loop kernel that follows spreads its FP64 work one block
+  // per SM, which holds only for blocks placed on an idle GPU, not on the few
+  // SMs a draining pass frees first
+  pdl_wait();
   if (pass_off(P)) return;
   simt_tile<KIND, V, DMAX, VEC>(P, H, blockIdx.x, blockIdx.y, P.n, P.m, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -320,18 +332,14 @@ template <int KIND, int V, int DMAX>
 void launch_v(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
   dim3 grid((unsigned)L.ncolblk, (unsigned)L.nrowblk);
   const bool vec = KIND == COST_DENSE_F32 && (P.ldc % 4 == 0) && ((uintptr_t)P.C % 16 == 0);
-  if (vec) pass_simt_kernel<KIND, V, DMAX, true><<<grid, kThreads, 0, st>>>(P, L.H);
-  else pass_simt_kernel<KIND, V, DMAX, false><<<grid, kThreads, 0, st>>>(P, L.H);
+  launch_k(vec ? pass_simt_kernel<KIND, V, DMAX, true> : pass_simt_kernel<KIND, V, DMAX, false>, grid, dim3(kThreads), 0,
+           st, P, L.H);
 }
 
 template <int KIND>
 void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
   const bool hot = (P.mode & (PASS_ROWS | PASS_COLS)) && !(P.mode & (PASS_OBJ | PASS_MAXCOST));
   if (KIND == COST_DENSE_F32 && hot && L.dense_fast) {
-    if (P.mode & PASS_COLS) {     // slots no segment writes must read as empty
-      const int64_t cnt = L.nslots * P.m;
-      clear_parts_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(P.col_part, cnt, P.done, P.skip, P.skip_if);
-    }
     const unsigned grid = (unsigned)L.G;
     static bool attr_set = false;
     if (!attr_set) {
@@ -343,9 +351,9 @@ void launch_kind(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {
       cudaFuncSetAttribute(dense_pass_kernel<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       attr_set = true;
     }
-    if ((P.mode & PASS_ROWS) && (P.mode & PASS_COLS)) dense_pass_kernel<0><<<grid, kThreads, kDenseRingBytes, st>>>(P, L);
-    else if (P.mode & PASS_ROWS) dense_pass_kernel<1><<<grid, kThreads, kDenseRingBytes, st>>>(P, L);
-    else dense_pass_kernel<2><<<grid, kThreads, kDenseRingBytes, st>>>(P, L);
+    const int mode = ((P.mode & PASS_ROWS) && (P.mode & PASS_COLS)) ? 0 : ((P.mode & PASS_ROWS) ? 1 : 2);
+    launch_k(mode == 0 ? dense_pass_kernel<0> : (mode == 1 ? dense_pass_kernel<1> : dense_pass_kernel<2>), dim3(grid),
+             dim3(kThreads), kDenseRingBytes, st, P, L);
     return;
   }
   if (KIND == COST_DENSE_F32) {
@@ -483,7 +491,9 @@ void simt_dense_layout(SimtLayout& L, int64_t n, int64_t m, int num_sms) {
 
 void launch_prep(const PassDesc& P, int64_t n_pad, int64_t m_pad, cudaStream_t st) {
   const int64_t tot = n_pad + m_pad;
-  prep_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(P, n_pad, m_pad);
+  const bool dense_next = P.kind == COST_DENSE_F32 && (P.mode & (PASS_ROWS | PASS_COLS)) &&
+                          !(P.mode & (PASS_OBJ | PASS_MAXCOST));
+  launch_k(prep_kernel, dim3((unsigned)((tot + 255) / 256)), dim3(256), 0, st, P, n_pad, m_pad, dense_next ? 0 : 1);
 }
 
 void launch_pass_simt(const PassDesc& P, const SimtLayout& L, cudaStream_t st) {

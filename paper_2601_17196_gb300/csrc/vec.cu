@@ -21,6 +21,9 @@ namespace {
 __global__ void combine_kernel(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow,
                                const float2* col_part, int64_t nrowblk, int64_t m, double* lcol, int64_t nbr,
                                const int* done, const int* skip, int skip_if) {
+  // no early release: the loop kernel that follows spreads its FP64 work one
+  // block per SM, which holds only for blocks placed on an idle GPU
+  pdl_wait();
   if ((done && *done) || (skip && *skip == skip_if)) return;
   __shared__ float sM[8][32], sS[8][32];
   const bool is_row = blockIdx.x < nbr;
@@ -200,7 +203,34 @@ __device__ __forceinline__ double safe_exp(double x) { return x > -700.0 ? exp(x
 // FP64 log-sum of entry j from the nblk (max, sum) partials of a pass (the
 // arithmetic of combine_kernel, one thread per entry): the loop kernels of the
 // solvers call it instead of a separate combine launch.
+// NB >= nblk: every partial is loaded at once (NB independent loads in
+// flight, predicated past nblk) and kept in registers for the two sweeps, the
+// same arithmetic in the same order as the streaming form below, without its
+// chain of dependent loads.
+template <int NB>
+__device__ __forceinline__ double comb_part_regs(const float2* part, int64_t nblk, int64_t len, int64_t j) {
+  float2 p[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) p[b] = (b < nblk) ? part[b * len + j] : make_float2(0.f, 0.f);
+  float M = -INFINITY;
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    if (p[b].y > 0.f) M = fmaxf(M, p[b].x);
+  if (!(M > -INFINITY)) return POT_NEG_BIG;
+  float St = 0.f, comp = 0.f;
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    if (p[b].y > 0.f) {
+      const float y = p[b].y * ex2(p[b].x - M) - comp;
+      const float t = St + y;
+      comp = (t - St) - y;
+      St = t;
+    }
+  return St > 0.f ? log_shifted_sum(M, St) : POT_NEG_BIG;
+}
 __device__ double comb_part(const float2* part, int64_t nblk, int64_t len, int64_t j) {
+  if (nblk <= 16) return comb_part_regs<16>(part, nblk, len, j);
+  if (nblk <= 32) return comb_part_regs<32>(part, nblk, len, j);
   float M = -INFINITY;
   for (int64_t b = 0; b < nblk; ++b) {
     const float2 p = part[b * len + j];
@@ -327,6 +357,7 @@ __global__ void aspot_init_kernel(AspotVecs V, const double* r, const double* c,
 
 // z_bar = (1 - theta) z_check + theta z~
 __global__ void aspot_extrap_kernel(AspotVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const double th = S->theta;
@@ -339,6 +370,7 @@ __global__ void aspot_extrap_kernel(AspotVecs V) {
 // After the fused pass at z_bar: gradient (r(B)+e^u-r~, c(B)+e^v-c~, |B|-s),
 // step z~' = z_bar - grad/(L theta), coupling z_grave = z_bar + theta (z~' - z~).
 __global__ void aspot_after_grad_kernel(AspotVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const double th = S->theta, Lth = S->L * th;
@@ -386,6 +418,7 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
 // rule's block S->kg (the pass was two-sided); z^ is then written whole to
 // (uh, vh), and the flags of the one-sided passes at z^t are set.
 __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const bool greedy = k < 0;
@@ -447,6 +480,7 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
 // After the fused pass at z^t: E_t, z_check^{t+1} = Greenkhorn_k(z^t),
 // closed-form phi(z_check^{t+1}), theta update and the stop test.
 __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const int take = S->take_hat;
@@ -543,6 +577,7 @@ __device__ __forceinline__ int pick_block(double du, double dv, double dw) {
 
 // After the two-sided pass at z_grave: S->kg = argmax of the decreases there.
 __global__ void aspot_greedy_pick_kernel(AspotVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -586,6 +621,7 @@ __device__ __forceinline__ double greedy_col_sum(const AspotVecs& V, int64_t j, 
 // that block, theta update and the stop test.  z^t is written to (uo, vo);
 // aspot_greedy_apply_kernel then forms z_check^{t+1}.
 __global__ void aspot_greedy_final_kernel(AspotVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const int k = S->kg, take = S->take_hat;
@@ -655,6 +691,7 @@ __global__ void aspot_greedy_final_kernel(AspotVecs V) {
 // exported state holds z_check^{t+1}) and after it, where it rewrites the same
 // values: it reads only z^t, the pass sums and scalars that no longer change.
 __global__ void aspot_greedy_apply_kernel(AspotVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   const int k = S->kg, take = S->take_hat, k2 = S->k2;
   const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
@@ -748,6 +785,7 @@ __global__ void sink_init_kernel(SinkVecs V, const double* r, const double* c, d
 // a row pass; the l1 row residual of the current point is the stop test of
 // the previous iteration (columns are exact right after a column update).
 __global__ void sink_after_rows_kernel(SinkVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -785,6 +823,7 @@ __global__ void sink_after_rows_kernel(SinkVecs V) {
 
 // restore the pre-update row potentials when the stop test fired
 __global__ void sink_restore_kernel(SinkVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done != 2) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -792,6 +831,7 @@ __global__ void sink_restore_kernel(SinkVecs V) {
 }
 
 __global__ void sink_after_cols_kernel(SinkVecs V) {
+  pdl_enter();
   DevState* S = V.S;
   if (S->done) return;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -943,14 +983,16 @@ __global__ void dense_plan_kernel(PassDesc P, const double* f, const double* g, 
 
 }  // namespace
 
+static thread_local bool g_pdl = false;   // see pdl_scope
+
 void launch_combine(const float2* row_part, int64_t ncolblk, int64_t n, double* lrow, const float2* col_part,
                     int64_t nrowblk, int64_t m, double* lcol, const int* done, cudaStream_t st, const int* skip,
                     int skip_if) {
   const int64_t nbr = lrow ? (n + 31) / 32 : 0;
   const int64_t nbc = lcol ? (m + 31) / 32 : 0;
   if (nbr + nbc == 0) return;
-  combine_kernel<<<(unsigned)(nbr + nbc), 256, 0, st>>>(row_part, ncolblk, n, lrow, col_part, nrowblk, m, lcol, nbr,
-                                                        done, skip, skip_if);
+  launch_k(combine_kernel, dim3((unsigned)(nbr + nbc)), dim3(256), 0, st, row_part, ncolblk, n, lrow, col_part,
+           nrowblk, m, lcol, nbr, done, skip, skip_if);
 }
 
 void launch_marg_stats(const double* r, const double* c, int64_t n, int64_t m, double* red,
@@ -968,29 +1010,33 @@ void launch_aspot_init(const AspotVecs& V, const double* r, const double* c, dou
 // while that still gives at most a few blocks per SM, so the FP64 updates,
 // whose instructions each hold an SM sub-partition's narrow FP64 pipe for many
 // cycles, spread over as many SMs as the problem allows; 256 beyond.
+bool pdl_active() { return g_pdl; }
+pdl_scope::pdl_scope(bool on) : prev(g_pdl) { g_pdl = on; }
+pdl_scope::~pdl_scope() { g_pdl = prev; }
+
 int loop_threads(int64_t len) { return len <= kLoopSmallLen ? 64 : kVecThreads; }
 unsigned loop_blocks(int64_t len) { const int t = loop_threads(len); return (unsigned)((len + t - 1) / t); }
 
 void launch_aspot_extrap(const AspotVecs& V, cudaStream_t st) {
-  aspot_extrap_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
+  launch_k(aspot_extrap_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V);
 }
 void launch_aspot_after_grad(const AspotVecs& V, cudaStream_t st) {
-  aspot_after_grad_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
+  launch_k(aspot_after_grad_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V);
 }
 void launch_aspot_after_greenkhorn(const AspotVecs& V, int k, cudaStream_t st) {
-  aspot_after_greenkhorn_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V, k);
+  launch_k(aspot_after_greenkhorn_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V, k);
 }
 void launch_aspot_greedy_pick(const AspotVecs& V, cudaStream_t st) {
-  aspot_greedy_pick_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
+  launch_k(aspot_greedy_pick_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V);
 }
 void launch_aspot_greedy_final(const AspotVecs& V, cudaStream_t st) {
-  aspot_greedy_final_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
+  launch_k(aspot_greedy_final_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V);
 }
 void launch_aspot_greedy_apply(const AspotVecs& V, cudaStream_t st) {
-  aspot_greedy_apply_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
+  launch_k(aspot_greedy_apply_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V);
 }
 void launch_aspot_after_final(const AspotVecs& V, int k, cudaStream_t st) {
-  aspot_after_final_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V, k);
+  launch_k(aspot_after_final_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V, k);
 }
 void launch_aspot_start_eval(const AspotVecs& V, const double* u, const double* v, int slot, cudaStream_t st) {
   aspot_start_eval_kernel<<<vec_blocks(V.n + V.m), kVecThreads, 0, st>>>(V, u, v, slot);
@@ -1006,11 +1052,11 @@ void launch_sink_init(const SinkVecs& V, const double* r, const double* c, doubl
   sink_init_kernel<<<vec_blocks(V.n + V.m + 1), kVecThreads, 0, st>>>(V, r, c, eps_s, s);
 }
 void launch_sink_after_rows(const SinkVecs& V, cudaStream_t st) {
-  sink_after_rows_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
-  sink_restore_kernel<<<vec_blocks(V.n + 1), kVecThreads, 0, st>>>(V);
+  launch_k(sink_after_rows_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V);
+  launch_k(sink_restore_kernel, dim3(vec_blocks(V.n + 1)), dim3(kVecThreads), 0, st, V);
 }
 void launch_sink_after_cols(const SinkVecs& V, cudaStream_t st) {
-  sink_after_cols_kernel<<<loop_blocks(V.n + V.m), loop_threads(V.n + V.m), 0, st>>>(V);
+  launch_k(sink_after_cols_kernel, dim3(loop_blocks(V.n + V.m)), dim3(loop_threads(V.n + V.m)), 0, st, V);
 }
 void launch_round_r1(const RoundVecs& V, cudaStream_t st) {
   round_r1_kernel<<<vec_blocks(V.n), kVecThreads, 0, st>>>(V);
