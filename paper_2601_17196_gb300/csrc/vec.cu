@@ -69,17 +69,61 @@ __global__ void combine_kernel(const float2* row_part, int64_t ncolblk, int64_t 
   }
 }
 
+// Warp sums of NV <= 4 values by a transposing butterfly: at the first
+// levels each lane keeps half of its values and adds its partner's copies of
+// them, so the four sums take 6 FP64 additions per lane instead of 20 (a
+// warp-wide FP64 instruction holds an SM sub-partition for dozens of cycles
+// on this GPU).  Value k's total ends in lane sum_lane<NV>(k); other NV use
+// one butterfly per value (total in lane 0).
+template <int NV>
+__device__ __forceinline__ int sum_lane(int k) { return NV <= 1 ? 0 : (NV == 2 ? 16 * k : 8 * k); }
+template <int NV>
+__device__ __forceinline__ void warp_sums(double (&v)[NV], int lane) {
+  if constexpr (NV == 1) {
+    v[0] = warp_sum_d(v[0]);
+  } else if constexpr (NV == 2) {
+    const bool up = lane & 16;
+    double keep = up ? v[1] : v[0];
+    keep += __shfl_xor_sync(0xffffffffu, up ? v[0] : v[1], 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+    v[0] = v[1] = keep;              // lanes 0..15 hold sum 0, lanes 16..31 sum 1
+  } else if constexpr (NV == 3 || NV == 4) {
+    const double v3 = NV == 4 ? v[NV - 1] : 0.0;
+    const bool up = lane & 16;
+    double k0 = up ? v[2] : v[0], k1 = up ? v3 : v[1];
+    k0 += __shfl_xor_sync(0xffffffffu, up ? v[0] : v[2], 16);
+    k1 += __shfl_xor_sync(0xffffffffu, up ? v[1] : v3, 16);
+    const bool up8 = lane & 8;
+    double keep = up8 ? k1 : k0;
+    keep += __shfl_xor_sync(0xffffffffu, up8 ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = keep;   // lanes 8k .. 8k+7 hold sum k
+  } else {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum_d(v[k]);
+  }
+}
+template <int NV>
+__device__ __forceinline__ bool holds_sum(int lane, int k) {
+  return (NV == 1 || NV > 4) ? lane == 0 : lane == sum_lane<NV>(k);
+}
+
 template <int NV>
 __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* counter, double (&tot)[NV]) {
   __shared__ double sh[NV][kVecThreads / 32];
   __shared__ double st[NV];
   __shared__ int amlast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  double w[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const double x = warp_sum_d(v[k]);
-    if (lane == 0) sh[k][warp] = x;
-  }
+  for (int k = 0; k < NV; ++k) w[k] = v[k];
+  warp_sums<NV>(w, lane);
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    if (holds_sum<NV>(lane, k)) sh[k][warp] = w[k];
   __syncthreads();
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -113,7 +157,10 @@ __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* c
 // block order, the log-sum-exp in natural log).
 template <int NV>
 __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, double* part,
-                                unsigned int* counter, double (&tot)[NV], double* lse_out) {
+                                unsigned int* counter, double (&tot)[NV], double* lse_out, bool lse_on = true) {
+  // lse_on (the same in every thread): whether the log-sum-exp is wanted at
+  // all; when not, its FP64 maxima, exponentials and logarithm are skipped
+  // and *lse_out is log 0
   constexpr int NW = kVecThreads / 32;
   constexpr int NP = NV + 2;
   __shared__ double sh[NV > 0 ? NV : 1][NW];
@@ -122,26 +169,34 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   __shared__ double slse;
   __shared__ int amlast;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  double w[NV > 0 ? NV : 1];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    const double y = warp_sum_d(v[k]);
-    if (lane == 0) sh[k][warp] = y;
+  for (int k = 0; k < NV; ++k) w[k] = v[k];
+  if constexpr (NV > 0) warp_sums<NV>(w, lane);
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    if (holds_sum<NV>(lane, k)) sh[k][warp] = w[k];
+  double mx = -INFINITY, sm = 0.0;
+  if (lse_on) {
+    mx = active ? x : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    sm = (active && mx > -INFINITY) ? exp(x - mx) : 0.0;
+    sm = warp_sum_d(sm);
   }
-  double mx = active ? x : -INFINITY;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  double sm = (active && mx > -INFINITY) ? exp(x - mx) : 0.0;
-  sm = warp_sum_d(sm);
   if (lane == 0) { smx[warp] = mx; ssm[warp] = sm; }
   __syncthreads();
   if (warp == 0) {
     // block (max, sum) of the NW warp partials: one exp per lane, not a serial chain
-    const double wm = (lane < nw && ssm[lane] > 0.0) ? smx[lane] : -INFINITY;
-    double bm = wm;
+    double bm = -INFINITY, bs = 0.0;
+    if (lse_on) {
+      const double wm = (lane < nw && ssm[lane] > 0.0) ? smx[lane] : -INFINITY;
+      bm = wm;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-    double bs = (wm > -INFINITY) ? ssm[lane] * exp(wm - bm) : 0.0;
-    bs = warp_sum_d(bs);
+      for (int o = 16; o > 0; o >>= 1) bm = fmax(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+      bs = (wm > -INFINITY) ? ssm[lane] * exp(wm - bm) : 0.0;
+      bs = warp_sum_d(bs);
+    }
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
@@ -165,29 +220,33 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
     a = warp_sum_d(a);
     if (lane == 0) st[k] = a;
   }
-  // grid log-sum-exp of the block partials, in parallel over the block's threads
-  double gm = -INFINITY;
-  for (int b2 = threadIdx.x; b2 < (int)gridDim.x; b2 += blockDim.x)
-    if (__ldcg(part + (int64_t)b2 * NP + NV + 1) > 0.0) gm = fmax(gm, __ldcg(part + (int64_t)b2 * NP + NV));
+  if (lse_on) {
+    // grid log-sum-exp of the block partials, in parallel over the block's threads
+    double gm = -INFINITY;
+    for (int b2 = threadIdx.x; b2 < (int)gridDim.x; b2 += blockDim.x)
+      if (__ldcg(part + (int64_t)b2 * NP + NV + 1) > 0.0) gm = fmax(gm, __ldcg(part + (int64_t)b2 * NP + NV));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
-  if (lane == 0) smx[warp] = gm;
-  __syncthreads();
-  gm = -INFINITY;
-  for (int w = 0; w < nw; ++w) gm = fmax(gm, smx[w]);
-  double gs = 0.0;
-  if (gm > -INFINITY)
-    for (int b2 = threadIdx.x; b2 < (int)gridDim.x; b2 += blockDim.x) {
-      const double ss = __ldcg(part + (int64_t)b2 * NP + NV + 1);
-      if (ss > 0.0) gs += ss * exp(__ldcg(part + (int64_t)b2 * NP + NV) - gm);
+    for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if (lane == 0) smx[warp] = gm;
+    __syncthreads();
+    gm = -INFINITY;
+    for (int w = 0; w < nw; ++w) gm = fmax(gm, smx[w]);
+    double gs = 0.0;
+    if (gm > -INFINITY)
+      for (int b2 = threadIdx.x; b2 < (int)gridDim.x; b2 += blockDim.x) {
+        const double ss = __ldcg(part + (int64_t)b2 * NP + NV + 1);
+        if (ss > 0.0) gs += ss * exp(__ldcg(part + (int64_t)b2 * NP + NV) - gm);
+      }
+    gs = warp_sum_d(gs);
+    if (lane == 0) ssm[warp] = gs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (int w = 0; w < nw; ++w) a += ssm[w];
+      slse = (gm > -INFINITY && a > 0.0) ? gm + log(a) : POT_NEG_BIG;
     }
-  gs = warp_sum_d(gs);
-  if (lane == 0) ssm[warp] = gs;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int w = 0; w < nw; ++w) a += ssm[w];
-    slse = (gm > -INFINITY && a > 0.0) ? gm + log(a) : POT_NEG_BIG;
+  } else if (threadIdx.x == 0) {
+    slse = POT_NEG_BIG;
   }
   __syncthreads();
 #pragma unroll
@@ -455,7 +514,7 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
     }
   }
   double tot[2], ltot = 0.0;
-  if (reduce_last_lse<2>(v, xr, act, V.red, V.counter, tot, &ltot) && threadIdx.x == 0) {
+  if (reduce_last_lse<2>(v, xr, act, V.red, V.counter, tot, &ltot, k == 2) && threadIdx.x == 0) {
     double wh = S->w_grave, base;
     if (k == 0) base = S->sum_rt;                 // |B|_1 + sum e^u = |r~|_1 after the u step
     else if (k == 1) base = S->sum_ct;
@@ -529,7 +588,7 @@ __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
     if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[3] = 1;
   }
   double tot[4], ltot = 0.0;
-  if (reduce_last_lse<4>(v, xr, act, V.red, V.counter, tot, &ltot) && threadIdx.x == 0) {
+  if (reduce_last_lse<4>(v, xr, act, V.red, V.counter, tot, &ltot, k == 2) && threadIdx.x == 0) {
     const double s = S->s;
     const double E = fabs(tot[1] - s) + tot[0];
     const double wz = S->w_z;
