@@ -139,11 +139,17 @@ __device__ bool reduce_last(const double (&v)[NV], double* part, unsigned int* c
   __syncthreads();
   if (!amlast) return false;
   __threadfence();
-  for (int k = warp; k < NV; k += nw) {
-    double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (int64_t)b * NV + k);
-    s = warp_sum_d(s);
-    if (lane == 0) st[k] = s;
+  // value pairs (k, k + nw) per warp, summed together by the transposing butterfly
+  for (int k = warp; k < NV; k += 2 * nw) {
+    const int k2 = k + nw;
+    double s2[2] = {0.0, 0.0};
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      s2[0] += __ldcg(part + (int64_t)b * NV + k);
+      if (k2 < NV) s2[1] += __ldcg(part + (int64_t)b * NV + k2);
+    }
+    warp_sums<2>(s2, lane);
+    if (lane == sum_lane<2>(0)) st[k] = s2[0];
+    if (k2 < NV && lane == sum_lane<2>(1)) st[k2] = s2[1];
   }
   __syncthreads();
 #pragma unroll
@@ -214,11 +220,17 @@ __device__ bool reduce_last_lse(const double (&v)[NV], double x, bool active, do
   __syncthreads();
   if (!amlast) return false;
   __threadfence();
-  for (int k = warp; k < NV; k += nw) {
-    double a = 0.0;
-    for (int b2 = lane; b2 < (int)gridDim.x; b2 += 32) a += __ldcg(part + (int64_t)b2 * NP + k);
-    a = warp_sum_d(a);
-    if (lane == 0) st[k] = a;
+  // value pairs (k, k + nw) per warp, summed together by the transposing butterfly
+  for (int k = warp; k < NV; k += 2 * nw) {
+    const int k2 = k + nw;
+    double a2[2] = {0.0, 0.0};
+    for (int b2 = lane; b2 < (int)gridDim.x; b2 += 32) {
+      a2[0] += __ldcg(part + (int64_t)b2 * NP + k);
+      if (k2 < NV) a2[1] += __ldcg(part + (int64_t)b2 * NP + k2);
+    }
+    warp_sums<2>(a2, lane);
+    if (lane == sum_lane<2>(0)) st[k] = a2[0];
+    if (k2 < NV && lane == sum_lane<2>(1)) st[k2] = a2[1];
   }
   if (lse_on) {
     // grid log-sum-exp of the block partials, in parallel over the block's threads
@@ -431,31 +443,42 @@ __global__ void aspot_extrap_kernel(AspotVecs V) {
 __global__ void aspot_after_grad_kernel(AspotVecs V) {
   pdl_enter();
   DevState* S = V.S;
-  if (S->done) return;
-  const double th = S->theta, Lth = S->L * th;
+  // every operand in one round of loads, the stop flag among them (a loop
+  // kernel's time is a few dependent rounds of loads plus its FP64 chain)
+  const int done = S->done;
+  const double th = S->theta, L = S->L;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool row = t < V.n, col = !row && t < V.n + V.m;
+  const int64_t j = t - V.n;
+  double z = 0.0, zt = 0.0, a = 0.0, R = 0.0;   // potential at z_bar, z~, marginal, log-sum
+  if (row) {
+    z = V.ub[t]; zt = V.ut[t]; a = V.rt[t];
+    R = V.fused ? comb_part(V.row_part, V.ncolblk, V.n, t) : V.lrow[t];
+  } else if (col) {
+    z = V.vb[j]; zt = V.vt[j]; a = V.ct[j];
+    R = V.fused ? comb_part(V.col_part, V.nrowblk, V.m, j) : V.lcol[j];
+  }
+  if (done) return;
+  const double Lth = L * th;
   double v[3] = {0, 0, 0};   // tot, sum(e^u - u r~) + sum(e^v - v c~), nonfinite
-  if (t < V.n) {
-    const double ub = V.ub[t];
-    const double R = row_sum_of(V, t, V.fused);
-    const double rB = exp_sum(R), eu = safe_exp(ub);
-    const double g = rB + eu - V.rt[t];
-    const double un = ub - g / Lth;
-    V.ug[t] = ub + th * (un - V.ut[t]);
+  if (row) {
+    if (V.fused) const_cast<double*>(V.lrow)[t] = R;    // later kernels of the iteration read it
+    const double rB = exp_sum(R), eu = safe_exp(z);
+    const double g = rB + eu - a;
+    const double un = z - g / Lth;
+    V.ug[t] = z + th * (un - zt);
     V.ut[t] = un;
     v[0] = rB;
-    v[1] = eu - ub * V.rt[t];
+    v[1] = eu - z * a;
     if (!isfinite(un)) v[2] = 1;
-  } else if (t < V.n + V.m) {
-    const int64_t j = t - V.n;
-    const double vb = V.vb[j];
-    const double Cc = col_sum_of(V, j, V.fused);
-    const double cB = exp_sum(Cc), ev = safe_exp(vb);
-    const double g = cB + ev - V.ct[j];
-    const double vn = vb - g / Lth;
-    V.vg[j] = vb + th * (vn - V.vt[j]);
+  } else if (col) {
+    if (V.fused) const_cast<double*>(V.lcol)[j] = R;
+    const double cB = exp_sum(R), ev = safe_exp(z);
+    const double g = cB + ev - a;
+    const double vn = z - g / Lth;
+    V.vg[j] = z + th * (vn - zt);
     V.vt[j] = vn;
-    v[1] = ev - vb * V.ct[j];
+    v[1] = ev - z * a;
     if (!isfinite(vn)) v[2] = 1;
   }
   double tot[3];
@@ -479,38 +502,51 @@ __global__ void aspot_after_grad_kernel(AspotVecs V) {
 __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
   pdl_enter();
   DevState* S = V.S;
-  if (S->done) return;
+  // every operand in one round of loads (the greedy rule's block index one
+  // round earlier), the stop flag among them
+  const int done = S->done;
   const bool greedy = k < 0;
   if (greedy) k = S->kg;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool row = t < V.n, col = !row && t < V.n + V.m;
+  const int64_t j = t - V.n;
+  const bool comb = V.fused && !greedy;     // greedy: the block choice kernel combined them
+  // the side's potential at z_grave, marginal and its log; the side's log-sum
+  // where block k needs it (rows: u- and w-steps; columns: v-step, and the
+  // w-step's combine for the closed forms of the final kernel)
+  double zg = 0.0, a = 0.0, la = 0.0, R = 0.0;
+  const bool need = row ? (k == 0 || k == 2) : (col && (k == 1 || (comb && k == 2)));
+  if (row) {
+    zg = V.ug[t]; a = V.rt[t]; la = V.lrt[t];
+    if (need) R = comb ? comb_part(V.row_part, V.ncolblk, V.n, t) : V.lrow[t];
+  } else if (col) {
+    zg = V.vg[j]; a = V.ct[j]; la = V.lct[j];
+    if (need) R = comb ? comb_part(V.col_part, V.nrowblk, V.m, j) : V.lcol[j];
+  }
+  if (done) return;
   double v[2] = {0, 0};      // phi parts
   double xr = 0.0;           // log row sum (w step: log |B|_1 = LSE_i of these)
   bool act = false;
-  const bool comb = V.fused && !greedy;     // greedy: the block choice kernel combined them
-  if (t < V.n) {
-    const double ug = V.ug[t];
+  if (row) {
+    if (need && comb) const_cast<double*>(V.lrow)[t] = R;   // later kernels of the iteration read it
     if (k == 0) {
-      const double R = row_sum_of(V, t, comb);
-      const double uh = V.lrt[t] - softplus(R - ug);
+      const double uh = la - softplus(R - zg);
       V.uh[t] = uh;
-      v[0] = -uh * V.rt[t];
+      v[0] = -uh * a;
     } else {
-      v[0] = safe_exp(ug) - ug * V.rt[t];
-      if (k == 2) { xr = row_sum_of(V, t, comb); act = true; }
-      if (greedy) V.uh[t] = ug;
+      v[0] = safe_exp(zg) - zg * a;
+      if (k == 2) { xr = R; act = true; }
+      if (greedy) V.uh[t] = zg;
     }
-  } else if (t < V.n + V.m) {
-    const int64_t j = t - V.n;
-    const double vg = V.vg[j];
-    if (comb && k == 2) col_sum_of(V, j, true);   // for the closed forms of the final kernel
+  } else if (col) {
+    if (need && comb) const_cast<double*>(V.lcol)[j] = R;
     if (k == 1) {
-      const double Cc = col_sum_of(V, j, comb);
-      const double vh = V.lct[j] - softplus(Cc - vg);
+      const double vh = la - softplus(R - zg);
       V.vh[j] = vh;
-      v[1] = -vh * V.ct[j];
+      v[1] = -vh * a;
     } else {
-      v[1] = safe_exp(vg) - vg * V.ct[j];
-      if (greedy) V.vh[j] = vg;
+      v[1] = safe_exp(zg) - zg * a;
+      if (greedy) V.vh[j] = zg;
     }
   }
   double tot[2], ltot = 0.0;
@@ -541,50 +577,72 @@ __global__ void aspot_after_greenkhorn_kernel(AspotVecs V, int k) {
 __global__ void aspot_after_final_kernel(AspotVecs V, int k) {
   pdl_enter();
   DevState* S = V.S;
-  if (S->done) return;
-  const int take = S->take_hat;
-  const double* uz_hat = (k == 0) ? V.uh : V.ug;
-  const double* vz_hat = (k == 1) ? V.vh : V.vg;
+  // every operand in one round of loads, the stop flag and the argmin among
+  // them: both candidates for z^t and both sources of its sums are read, then
+  // selected
+  const int done = S->done, take = S->take_hat;
+  const double w_hat = S->w_hat, w_grave = S->w_grave;
+  // theta_{t+1} (formed by the gradient kernel of this iteration): the
+  // extrapolation z_bar^{t+1} of the next iteration is formed here
+  const double thn = S->theta_next;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool row = t < V.n, col = !row && t < V.n + V.m;
+  const int64_t j = t - V.n;
+  // side of the entry: potential of z^ (block k's Greenkhorn step or z_grave),
+  // of z_check, z^ and z_grave of block k's side, marginal, its log, z~
+  double zh = 0.0, zc = 0.0, zhk = 0.0, zgk = 0.0, a = 0.0, la = 0.0, zt = 0.0, Rp = 0.0, Rl = 0.0;
+  bool parts = false;        // the sums at z^t come from the pass (else in closed form from P2)
+  if (row) {
+    zh = (k == 0) ? V.uh[t] : V.ug[t]; zc = V.uc[t]; a = V.rt[t]; la = V.lrt[t]; zt = V.ut[t];
+    if (k == 0) { zhk = V.uh[t]; zgk = V.ug[t]; }
+    if (V.fused) Rp = comb_part(V.row_part, V.ncolblk, V.n, t);
+    Rl = V.lrow[t];
+  } else if (col) {
+    zh = (k == 1) ? V.vh[j] : V.vg[j]; zc = V.vc[j]; a = V.ct[j]; la = V.lct[j]; zt = V.vt[j];
+    if (k == 1) { zhk = V.vh[j]; zgk = V.vg[j]; }
+    if (V.fused) Rp = comb_part(V.col_part, V.nrowblk, V.m, j);
+    Rl = V.lcol[j];
+  }
+  if (done) return;
   double v[4] = {0, 0, 0, 0};   // Eu+Ev, tot, phi parts, nonfinite
   double xr = 0.0;
   bool act = false;
   // z^t = z^: the sums of block k's side come from the Greenkhorn pass at
   // z_grave in closed form (the other side was computed at z^ by P3a)
-  const double dw = (take && k == 2) ? S->w_hat - S->w_grave : 0.0;
-  // theta_{t+1} (formed by the gradient kernel of this iteration): the
-  // extrapolation z_bar^{t+1} of the next iteration is formed here
-  const double thn = S->theta_next;
-  if (t < V.n) {
-    const double uz = take ? uz_hat[t] : V.uc[t];
+  const double dw = (take && k == 2) ? w_hat - w_grave : 0.0;
+  if (row) {
+    const double uz = take ? zh : zc;
     // rows: from the pass at z^t (P3a for k = 1, P3b when z^t = z_check), else closed form
-    double R = row_sum_of(V, t, V.fused && (k == 1 || !take));
-    if (take && k == 0) R = clamp_log(R + (V.uh[t] - V.ug[t]));
+    parts = V.fused && (k == 1 || !take);
+    double R = parts ? Rp : Rl;
+    if (parts) const_cast<double*>(V.lrow)[t] = Rp;
+    if (take && k == 0) R = clamp_log(R + (zhk - zgk));
     else if (take && k == 2) R = clamp_log(R + dw);
     xr = R;
     act = k == 2;                      // log |B|_1 is needed by the w step only
     const double rB = exp_sum(R), eu = safe_exp(uz);
-    v[0] = fabs(rB + eu - V.rt[t]);
+    v[0] = fabs(rB + eu - a);
     v[1] = rB;
     V.uo[t] = uz;
-    const double un = (k == 0) ? V.lrt[t] - softplus(R - uz) : uz;
+    const double un = (k == 0) ? la - softplus(R - uz) : uz;
     V.uc[t] = un;
-    V.ub[t] = (1.0 - thn) * un + thn * V.ut[t];
-    v[2] = (k == 0) ? -un * V.rt[t] : eu - un * V.rt[t];    // un = uz unless k = 0
+    V.ub[t] = (1.0 - thn) * un + thn * zt;
+    v[2] = (k == 0) ? -un * a : eu - un * a;    // un = uz unless k = 0
     if (!isfinite(R) && R != POT_NEG_BIG) v[3] = 1;
-  } else if (t < V.n + V.m) {
-    const int64_t j = t - V.n;
-    const double vz = take ? vz_hat[j] : V.vc[j];
-    double Cc = col_sum_of(V, j, V.fused && (k == 0 || !take));
-    if (take && k == 1) Cc = clamp_log(Cc + (V.vh[j] - V.vg[j]));
+  } else if (col) {
+    const double vz = take ? zh : zc;
+    parts = V.fused && (k == 0 || !take);
+    double Cc = parts ? Rp : Rl;
+    if (parts) const_cast<double*>(V.lcol)[j] = Rp;
+    if (take && k == 1) Cc = clamp_log(Cc + (zhk - zgk));
     else if (take && k == 2) Cc = clamp_log(Cc + dw);
     const double cB = exp_sum(Cc), ev = safe_exp(vz);
-    v[0] = fabs(cB + ev - V.ct[j]);
+    v[0] = fabs(cB + ev - a);
     V.vo[j] = vz;
-    const double vn = (k == 1) ? V.lct[j] - softplus(Cc - vz) : vz;
+    const double vn = (k == 1) ? la - softplus(Cc - vz) : vz;
     V.vc[j] = vn;
-    V.vb[j] = (1.0 - thn) * vn + thn * V.vt[j];
-    v[2] = (k == 1) ? -vn * V.ct[j] : ev - vn * V.ct[j];    // vn = vz unless k = 1
+    V.vb[j] = (1.0 - thn) * vn + thn * zt;
+    v[2] = (k == 1) ? -vn * a : ev - vn * a;    // vn = vz unless k = 1
     if (!isfinite(Cc) && Cc != POT_NEG_BIG) v[3] = 1;
   }
   double tot[4], ltot = 0.0;
